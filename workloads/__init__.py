@@ -1,0 +1,128 @@
+"""Seeded synthetic inputs for the truncated-SVD library and its tests.
+
+This module only builds matrices (and nothing of the SVD methods' arithmetic), so
+both the CUDA path and the CPU oracle may take their inputs from it.  Every
+generator is deterministic in its seed (numpy PCG64).
+
+Workloads (sizes as in the paper's experiments and the library's benchmark):
+
+* ``dense_known_spectrum``: A = U0 diag(sigma) V0^T with U0, V0 the sign-fixed
+  Q factors of seeded N(0,1) matrices; the synthetic dense benchmark of Sec. 4.2
+  builds its test matrices this way.  Default spectrum sigma_i = 2^(-i/8).
+* ``csr_uniform``: m x n CSR, exactly d distinct uniformly drawn columns per row
+  (sorted), N(0,1) values: a stand-in for the rectangular SuiteSparse matrices of
+  Sec. 4.1 (Table 2), which are not available here.
+* ``csr_power_law``: rows with Zipf-distributed degrees and Zipf column
+  popularity, U(0,1) values (heavy rows and heavy columns).
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+
+def _orthonormal(rng: np.random.Generator, rows: int, cols: int) -> np.ndarray:
+    """Q factor of a seeded N(0,1) rows x cols matrix, signs fixed so diag(R) > 0."""
+    G = rng.standard_normal((rows, cols))
+    Q, R = np.linalg.qr(G)
+    return Q * np.where(np.diag(R) < 0, -1.0, 1.0)
+
+
+def spectrum_pow2(n: int) -> np.ndarray:
+    """sigma_i = 2^(-i/8), i = 0..n-1 (sigma_1 = 1, gaps of 2^(1/8))."""
+    return 2.0 ** (-np.arange(n) / 8.0)
+
+
+def spectrum_power(n: int, alpha: float = 1.5) -> np.ndarray:
+    """sigma_i = 1 / (1 + i)^alpha, i = 0..n-1."""
+    return 1.0 / (1.0 + np.arange(n)) ** alpha
+
+
+def dense_known_spectrum(m: int, n: int, seed: int = 0, sigma=None):
+    """Dense A = U0 diag(sigma) V0^T (m x n, m >= n is not required).
+
+    Returns (A, sigma, U0, V0) with U0 (m x r), V0 (n x r), r = min(m, n), A C-contiguous FP64.
+    """
+    rng = np.random.default_rng(seed)
+    r = min(m, n)
+    if sigma is None:
+        sigma = spectrum_pow2(r)
+    sigma = np.asarray(sigma, dtype=np.float64)
+    U0 = _orthonormal(rng, m, r)
+    V0 = _orthonormal(rng, n, r)
+    A = np.ascontiguousarray((U0 * sigma) @ V0.T)
+    return A, sigma, U0, V0
+
+
+def csr_uniform(m: int, n: int, d: int, seed: int = 1, dtype=np.float64) -> sp.csr_matrix:
+    """CSR with exactly ``d`` distinct uniformly random columns per row (sorted), N(0,1) values."""
+    if d > n:
+        raise ValueError("d > n")
+    rng = np.random.default_rng(seed)
+    cols = np.sort(rng.integers(0, n, size=(m, d)), axis=1)
+    while True:
+        dup = np.any(cols[:, 1:] == cols[:, :-1], axis=1) if d > 1 else np.zeros(m, bool)
+        bad = np.nonzero(dup)[0]
+        if bad.size == 0:
+            break
+        cols[bad] = np.sort(rng.integers(0, n, size=(bad.size, d)), axis=1)
+    vals = rng.standard_normal(m * d).astype(dtype)
+    indptr = np.arange(0, m * d + 1, d, dtype=np.int32)
+    return sp.csr_matrix((vals, cols.reshape(-1).astype(np.int32), indptr), shape=(m, n))
+
+
+def _zipf_truncated(rng, size, a, lo, hi):
+    """Samples of P(k) proportional to k^-a on the integers lo..hi (inverse CDF on a table)."""
+    ks = np.arange(lo, hi + 1, dtype=np.float64)
+    w = ks ** (-a)
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    return (np.searchsorted(cdf, rng.random(size), side="right") + lo).astype(np.int64)
+
+
+def csr_power_law(m: int, n: int, target_nnz: int, seed: int = 3, deg_exp: float = 2.1,
+                  deg_max: int = 20000, col_exp: float = 1.5, dtype=np.float32) -> sp.csr_matrix:
+    """Power-law CSR: row degrees d_i = min(deg_max, ceil(c z_i)), z_i ~ Zipf(deg_exp) on
+    [1, deg_max], with c set by bisection so that sum d_i is within 0.5% of ``target_nnz``;
+    columns drawn with Zipf(col_exp) popularity over ranks mapped to ids by a seeded
+    permutation, distinct within a row; values U(0, 1).
+    """
+    rng = np.random.default_rng(seed)
+    z = _zipf_truncated(rng, m, deg_exp, 1, deg_max).astype(np.float64)
+    deg_max = min(deg_max, n)
+    lo, hi = 0.0, float(target_nnz)
+    for _ in range(200):
+        c = 0.5 * (lo + hi)
+        tot = np.minimum(deg_max, np.ceil(c * z)).sum()
+        if abs(tot - target_nnz) <= 0.005 * target_nnz:
+            break
+        if tot < target_nnz:
+            lo = c
+        else:
+            hi = c
+    deg = np.minimum(deg_max, np.ceil(c * z)).astype(np.int64)
+    perm = rng.permutation(n)
+    ranks = np.arange(1, n + 1, dtype=np.float64)
+    pop = ranks ** (-col_exp)
+    cdf = np.cumsum(pop)
+    cdf /= cdf[-1]
+    indptr = np.zeros(m + 1, dtype=np.int64)
+    indptr[1:] = np.cumsum(deg)
+    nnz = int(indptr[-1])
+    cols = np.empty(nnz, dtype=np.int32)
+    # draw with replacement, dedupe per row, top up until every row has its degree
+    for i0 in range(0, m, 65536):
+        i1 = min(m, i0 + 65536)
+        for i in range(i0, i1):
+            d = int(deg[i])
+            got = np.empty(0, dtype=np.int64)
+            while got.size < d:
+                need = d - got.size
+                draw = np.searchsorted(cdf, rng.random(need + 8), side="right")
+                got = np.unique(np.concatenate([got, perm[np.minimum(draw, n - 1)]]))
+            if got.size > d:
+                got = np.sort(rng.choice(got, size=d, replace=False))
+            cols[indptr[i]:indptr[i + 1]] = got
+    vals = rng.random(nnz).astype(dtype)
+    return sp.csr_matrix((vals, cols, indptr.astype(np.int64)), shape=(m, n))
