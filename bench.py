@@ -1,0 +1,328 @@
+"""Benchmark: time-to-k-triplets at residual <= 1e-6 on one GB300 (per GPU replica).
+
+One step = one full LancSVD solve (Alg. 2: start block, CSR(A^T) build, every
+restart cycle of SpMM / SpMM^T / CGS-CQR2 / Jacobi SVD, the residual checks and
+the Ritz vectors) on a synthetic 100,000 x 100,000 CSR matrix with exactly 10
+uniformly drawn distinct columns per row and N(0,1) values (seed 1), k = b = 64,
+r = 16 blocks, FP64.  A is resident in HBM before the timed region.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead
+(host cores, bounded sample).  Multi-GPU (torchrun): independent replicas, one
+problem per rank (seed 1 + rank), no collective on the data path.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (matrix, method, params)
+    "sparse100k-lanczos": dict(kind="csr", m=100_000, n=100_000, d=10, seed=1, method="blanczos",
+                               k=64, b=64, r=16, tol=1e-6, max_restarts=50, oracle_cycles=9),
+    "sparse100k-rsvd": dict(kind="csr", m=100_000, n=100_000, d=10, seed=1, method="rsvd",
+                            k=64, p=64, q=3),
+    "dense512-lanczos": dict(kind="dense", m=512, n=256, seed=0, method="blanczos",
+                             k=10, b=16, r=4, tol=1e-6, max_restarts=50, oracle_cycles=2),
+    "dense512-rsvd": dict(kind="dense", m=512, n=256, seed=0, method="rsvd", k=10, p=10, q=2),
+}
+
+METRIC = "time-to-k-triplets at residual <=1e-6 (s); SpMM/GEMM fraction of HBM/tensor roofline"
+SM_COUNT = 152
+FP64_FLOPS_PER_CLK_PER_SM = 4  # 2 DFMA lanes per SM (measured 2.06 DFMA/clk/SM), 2 flops each
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def _make_matrix(cfg, rank):
+    import workloads
+    if cfg["kind"] == "csr":
+        return workloads.csr_uniform(cfg["m"], cfg["n"], cfg["d"], seed=cfg["seed"] + rank)
+    A, _, _, _ = workloads.dense_known_spectrum(cfg["m"], cfg["n"], seed=cfg["seed"] + rank)
+    return A
+
+
+def _solve(tsvd, cfg, A, seed, profile=False, output="device"):
+    if cfg["method"] == "blanczos":
+        return tsvd.blanczos(A, cfg["k"], cfg["b"], cfg["r"], seed=seed, tol=cfg["tol"],
+                             max_restarts=cfg["max_restarts"], profile=profile, output=output)
+    return tsvd.rsvd(A, cfg["k"], cfg["p"], cfg["q"], seed=seed, profile=profile, output=output)
+
+
+def _oracle_solve(cfg, A, seed, cycles=None):
+    import oracle
+    if cfg["method"] == "blanczos":
+        if cycles is None:
+            return oracle.blanczos(A, cfg["k"], cfg["b"], cfg["r"], seed=seed, tol=cfg["tol"],
+                                   max_restarts=cfg["max_restarts"])
+        return oracle.blanczos(A, cfg["k"], cfg["b"], cfg["r"], seed=seed, tol=0.0, max_restarts=cycles - 1)
+    return oracle.rsvd(A, cfg["k"], cfg["p"], cfg["q"], seed=seed)
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.path is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        loaded = [v for v in sm if v > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _flush_l2(torch, buf):
+    buf.add_(1.0)  # writes 256 MiB (> 129 MB L2)
+
+
+def _cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def run_reference(args, cfg):
+    """The FP64 CPU oracle timed on the host cores (bounded sample per step)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    A = _make_matrix(cfg, 0)
+    cores = _cpu_cores()
+    if cfg["method"] == "blanczos":
+        per_step = []
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            _oracle_solve(cfg, A, seed=cfg["seed"], cycles=1)
+            dt = time.perf_counter() - t0
+            if i >= args.warmup:
+                per_step.append(dt)
+        t_cycle = statistics.median(per_step)
+        value = t_cycle * cfg["oracle_cycles"]
+        sample = (f"1 of the {cfg['oracle_cycles']} restart cycles the oracle needs on the full matrix, "
+                  f"per step; value = median cycle time x {cfg['oracle_cycles']}")
+    else:
+        per_step = []
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            _oracle_solve(cfg, A, seed=cfg["seed"])
+            if i >= args.warmup:
+                per_step.append(time.perf_counter() - t0)
+        value = statistics.median(per_step)
+        sample = "the whole solve on the full matrix, per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, **{k: v for k, v in cfg.items() if k != "oracle_cycles"},
+                   "parallelism": f"replicas{args.gpus}"},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--workload", default="sparse100k-lanczos", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    cfg = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+
+    import numpy as np
+    import torch
+    import paper_2403_06218_gb300 as tsvd
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    A_host = _make_matrix(cfg, rank)
+    if cfg["kind"] == "csr":
+        A_dev = tsvd.CsrMatrix.from_scipy(A_host)
+        A_pinned = tsvd.CsrMatrix.from_scipy(A_host, device="cpu", pin_memory=True)
+        h2d = 12 * A_host.nnz + 4 * (A_host.shape[0] + 1)
+    else:
+        A_dev = torch.from_numpy(A_host).cuda()
+        A_pinned = torch.from_numpy(A_host).pin_memory()
+        h2d = 8 * A_host.size
+    m, n = A_host.shape
+    d2h = 8 * (m + n) * cfg["k"] + 8 * cfg["k"]
+    seed = cfg["seed"] + rank
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    for _ in range(args.warmup):
+        res = _solve(tsvd, cfg, A_dev, seed)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K solves, A resident in HBM ----
+    infos = []
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(args.steps):
+            _flush_l2(torch, flush)
+            res = _solve(tsvd, cfg, A_dev, seed, profile=True)
+            infos.append(res.info)
+        e1.record(st)
+        torch.cuda.synchronize()
+        barrier()
+    ms_total = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    clocks = clk.summary()
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e_steps = max(1, min(args.steps, 2))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        r_host = _solve(tsvd, cfg, A_pinned, seed, output="host")
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist is not None:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    # ---- roofline of the dominant kernel class (CUDA events on the launching stream) ----
+    from paper_2403_06218_gb300._capi import KERNEL_CLASSES
+    ms_cls = [sum(i["prof_ms"][c] for i in infos) for c in range(6)]
+    fl_cls = [sum(i["prof_flops"][c] for i in infos) for c in range(6)]
+    by_cls = [sum(i["prof_bytes"][c] for i in infos) for c in range(6)]
+    ln_cls = [sum(i["prof_launches"][c] for i in infos) for c in range(6)]
+    dom = max(range(5), key=lambda c: ms_cls[c])
+    peaks = _measured_peaks()
+    fp64_peak = SM_COUNT * FP64_FLOPS_PER_CLK_PER_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    achieved = fl_cls[dom] / (ms_cls[dom] * 1e-3) / 1e12 if ms_cls[dom] > 0 else 0.0
+    roofline = {
+        "kernel": KERNEL_CLASSES[dom], "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+        "frac": achieved / fp64_peak, "traffic": None,
+        "peak_note": "FP64 pipe: 152 SMs x 4 flop/clk x max SM clock (derived; 1.19 TFLOP/s measured by a DFMA loop)",
+        "launches": ln_cls[dom], "avg_launch_ms": ms_cls[dom] / max(1, ln_cls[dom]),
+        "bytes_per_launch": by_cls[dom] / max(1, ln_cls[dom]),
+        "hbm_frac_of_measured": (by_cls[dom] / (ms_cls[dom] * 1e-3) / 1e9) / float(peaks.get("hbm_gbs", 6790.3))
+        if ms_cls[dom] > 0 else None,
+        "share_of_step": ms_cls[dom] / ms_total,
+        "classes": {KERNEL_CLASSES[c]: {"launches": ln_cls[c], "ms": ms_cls[c], "tflops": (fl_cls[c] / (ms_cls[c] * 1e-3) / 1e12)
+                                        if ms_cls[c] > 0 else None} for c in range(6)},
+    }
+
+    line = {
+        "metric": METRIC, "value": ms_step / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, **{k: v for k, v in cfg.items() if k != "oracle_cycles"},
+                   "parallelism": f"replicas{world}", "l2": "flushed before every step (256 MiB write)"},
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
+        "clocks": clocks,
+        "roofline": roofline,
+        "solve": {"cycles": infos[-1]["iterations"], "restarts": infos[-1]["restarts"],
+                  "resid_max": infos[-1]["resid_max"], "converged": infos[-1]["converged"],
+                  "svd_sweeps": infos[-1]["svd_sweeps"], "ms_transpose": infos[-1]["ms_transpose"]},
+    }
+
+    if rank == 0 and not args.no_cpu_baseline:
+        # the oracle as it stands on the host cores: one restart cycle of the same
+        # solve on the full matrix, scaled by the cycles the solve needed
+        cycles = int(infos[-1]["iterations"]) if cfg["method"] == "blanczos" else 1
+        t0 = time.perf_counter()
+        _oracle_solve(cfg, A_host, seed, cycles=1 if cfg["method"] == "blanczos" else None)
+        t_cyc = time.perf_counter() - t0
+        line["cpu_baseline"] = {
+            "value": t_cyc * cycles, "unit": "s", "cores": _cpu_cores(), "kind": "oracle",
+            "sample": (f"1 restart cycle on the full matrix, x{cycles} cycles" if cfg["method"] == "blanczos"
+                       else "the whole solve"),
+        }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,265 @@
+/*
+ * tsvd.h -- C ABI of a truncated-SVD library for one NVIDIA GB300 (sm_103a).
+ *
+ * Methods (Tomas, Quintana-Orti, Anzt, "Fast Truncated SVD of Sparse and Dense
+ * Matrices on Graphics Processors"):
+ *   - RandSVD, randomized subspace iteration (Sec. 2.1, Alg. 1);
+ *   - LancSVD, block Golub-Kahan-Lanczos bidiagonalisation with full two-sided
+ *     block re-orthogonalisation and basic restart (Sec. 2.2, Alg. 2);
+ * and their building blocks: CGS-QR (Alg. 3), CholeskyQR2 (Alg. 4),
+ * CGS-CQR2 (Alg. 5), the sparse/dense block products with A and A^T (Table 1),
+ * the small SVD of the projected matrix (Alg. 1 S5, Alg. 2 S6) and the
+ * Gaussian start block (Sec. 4).
+ *
+ * Conventions shared by every entry point
+ *   - Dense blocks are ROW-MAJOR: element (i, j) of a block with leading
+ *     dimension ld is at p[i * ld + j].  ld >= number of columns.
+ *   - All arithmetic and all floating-point outputs are FP64.
+ *   - Pointers are CUDA device pointers unless a descriptor field says
+ *     TSVD_HOST.  The caller owns every buffer; the library keeps no pointer
+ *     after a call returns and never allocates device memory: scratch comes
+ *     from the caller's workspace, sized by the matching *_workspace_size call.
+ *     Workspace pointers must be 256-byte aligned.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     enqueued on it; every entry point synchronises that stream before it
+ *     returns (the status words it reports are read back from the device).
+ *   - Return value: TSVD_OK (0), TSVD_NOT_CONVERGED (1, a warning: outputs
+ *     hold the best triplets found), or a negative error code.  On an error the
+ *     outputs are unspecified; no exception or abort crosses the ABI.
+ *   - Integers describing sizes are int64_t; CSR indices are int32_t.
+ */
+#ifndef TSVD_H_
+#define TSVD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define TSVD_OK                 0
+#define TSVD_NOT_CONVERGED      1   /* warning: tolerance not met within max_restarts */
+#define TSVD_ERR_INVALID_ARG   (-1) /* bad size, parameter, pointer, or CSR structure  */
+#define TSVD_ERR_NONFINITE     (-2) /* NaN/Inf met in the data or a Gram diagonal     */
+#define TSVD_ERR_CUDA          (-3) /* a CUDA runtime call failed                       */
+#define TSVD_ERR_WORKSPACE     (-4) /* workspace missing, too small or misaligned       */
+#define TSVD_ERR_TIMEOUT       (-5) /* a bounded device-side wait gave up               */
+#define TSVD_ERR_UNSUPPORTED   (-6) /* a size beyond this build's kernel limits         */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define TSVD_DENSE   0   /* tsvd_matrix.format: row-major dense                    */
+#define TSVD_CSR     1   /* tsvd_matrix.format: compressed sparse row              */
+#define TSVD_F64     0   /* tsvd_matrix.dtype                                      */
+#define TSVD_DEVICE  0   /* memory location of a buffer                            */
+#define TSVD_HOST    1
+
+#define TSVD_METHOD_RSVD      0
+#define TSVD_METHOD_BLANCZOS  1
+
+/* Largest block width of one Cholesky factorisation (CholeskyQR2 / CGS-CQR2);
+ * CGS-QR splits wider blocks (Alg. 3).  Largest small-SVD order. */
+#define TSVD_MAX_BLOCK      128
+#define TSVD_MAX_SMALL_SVD  2048
+
+/* The matrix A (m x n).  Dense: `val` points to m*ld doubles, row-major.
+ * CSR: row_ptr[m+1] (row_ptr[0] = 0, non-decreasing, row_ptr[m] = nnz),
+ * col_idx[nnz] in [0, n), val[nnz]; columns within a row in any order. */
+typedef struct tsvd_matrix {
+    int64_t m, n;
+    int32_t format;          /* TSVD_DENSE or TSVD_CSR                     */
+    int32_t dtype;           /* TSVD_F64                                   */
+    int32_t location;        /* TSVD_DEVICE or TSVD_HOST (copied in)       */
+    int32_t reserved;
+    const void* val;
+    int64_t ld;              /* dense only                                 */
+    const int32_t* row_ptr;  /* CSR only                                   */
+    const int32_t* col_idx;  /* CSR only                                   */
+    int64_t nnz;             /* CSR only                                   */
+} tsvd_matrix;
+
+/* tsvd_opts.flags bits */
+#define TSVD_FLAG_PROFILE  1   /* time every kernel class with CUDA events (tsvd_info.prof_*) */
+
+/* Kernel classes reported by TSVD_FLAG_PROFILE (index into tsvd_info.prof_*). */
+#define TSVD_K_SPMM     0   /* CSR SpMM with A or A^T (Table 1 SpMM)                      */
+#define TSVD_K_GEMM_TN  1   /* X^T Z: Gram matrices and projections P^T Q (Algs. 4, 5)    */
+#define TSVD_K_GEMM_NN  2   /* X M: updates Q - P H, Q L^{-T}, Ritz/restart products      */
+#define TSVD_K_CHOL     3   /* Cholesky + triangular inverse of a Gram matrix             */
+#define TSVD_K_SVD      4   /* small Jacobi SVD                                            */
+#define TSVD_K_OTHER    5   /* start block, transpose build, residuals, copies            */
+#define TSVD_K_COUNT    6
+
+/* Options; fill with tsvd_default_opts() and override fields. */
+typedef struct tsvd_opts {
+    double tol;              /* LancSVD stops when max_j ||A v_j - s_j u_j|| <= tol * s_1 (default 1e-6) */
+    int32_t max_restarts;    /* LancSVD restarts allowed after the first cycle (default 50) */
+    int32_t qr_block;        /* RandSVD CGS-QR block width; 0 = min(k+p, TSVD_MAX_BLOCK) */
+    int32_t output_location; /* TSVD_DEVICE or TSVD_HOST for sigma/U/V (default device) */
+    int32_t flags;           /* TSVD_FLAG_* bits (default 0) */
+    const double* start_block; /* optional device block replacing the Philox draw:
+                                  RandSVD n' x (k+p), LancSVD m' x b, row-major, ld = cols,
+                                  where m' >= n' are the dimensions after the m<n transpose */
+    void* stream;            /* cudaStream_t */
+} tsvd_opts;
+
+/* Per-call report.  Phase times are CUDA-event milliseconds on `stream`. */
+typedef struct tsvd_info {
+    int32_t iterations;      /* RandSVD loop trips (q+1); LancSVD restart cycles run */
+    int32_t restarts;        /* LancSVD restarts taken                              */
+    int32_t breakdowns;      /* Cholesky breakdowns sent to the CGS2 fallback       */
+    int32_t converged;       /* 1 if resid_max <= tol (LancSVD)                      */
+    int32_t transposed;      /* 1 if m < n and the method ran on A^T                 */
+    int32_t svd_sweeps;      /* Jacobi sweeps of the last small SVD                   */
+    double resid_max;        /* max_j ||A v_j - s_j u_j||_2 / s_1 of the returned triplets */
+    double rho_last;         /* last Lanczos residual estimate / s_1                  */
+    double ms_total;         /* whole call, including the CSR transpose build         */
+    double ms_transpose;     /* CSR(A^T) build                                         */
+    int64_t kernel_launches; /* kernels this call enqueued                             */
+    /* With TSVD_FLAG_PROFILE: per kernel class, the launches, their summed
+     * CUDA-event time on `stream`, and the algorithmic flops and compulsory
+     * bytes they were asked to do (Table 1 cost model, symmetric Gram counted
+     * as its upper half).  Zero otherwise. */
+    int64_t prof_launches[TSVD_K_COUNT];
+    double prof_ms[TSVD_K_COUNT];
+    double prof_flops[TSVD_K_COUNT];
+    double prof_bytes[TSVD_K_COUNT];
+} tsvd_info;
+
+typedef struct tsvd_handle tsvd_handle;
+
+/* ---- lifetime ----------------------------------------------------------- */
+
+/* Fills *opts with the defaults listed above. */
+void tsvd_default_opts(tsvd_opts* opts);
+
+/* Creates a handle bound to CUDA device `device` (queries its SM count and
+ * kernel occupancy; allocates only the host-side struct).  *out = NULL on error. */
+int tsvd_create(tsvd_handle** out, int device);
+
+/* Frees the handle (host memory only).  NULL is accepted. */
+int tsvd_destroy(tsvd_handle* h);
+
+/* Static text for a status code. */
+const char* tsvd_status_string(int status);
+
+/* ---- drivers ------------------------------------------------------------ */
+
+/* Workspace bytes for tsvd_rsvd (method TSVD_METHOD_RSVD, a = p, c = q) or
+ * tsvd_blanczos (TSVD_METHOD_BLANCZOS, a = b, c = r) on A with k triplets. */
+int tsvd_workspace_size(const tsvd_matrix* A, int method, int k, int a, int c,
+                        const tsvd_opts* opts, size_t* bytes);
+
+/* RandSVD, Alg. 1 (Sec. 2.1): block width l = k + p, q + 1 trips of S1-S4
+ * (q power steps), then the SVD of R (S5) and the Ritz vectors (S6, S7).
+ * The start block is N(0,1) Philox4x32-10 (key = seed, stream 1) unless
+ * opts->start_block is given.  If m < n the method runs on A^T (Sec. 2).
+ * Outputs: sigma[k] descending; U (m x k), V (n x k) row-major, ld = k; the
+ * largest-magnitude entry of each v_j is positive.
+ * Requires 1 <= k <= k + p <= min(m, n). */
+int tsvd_rsvd(tsvd_handle* h, const tsvd_matrix* A, int k, int p, int q, uint64_t seed,
+              const tsvd_opts* opts, void* ws, size_t ws_bytes,
+              double* sigma, double* U, double* V, tsvd_info* info);
+
+/* LancSVD, Alg. 2 (Sec. 2.2): blocks of width b, r blocks per cycle (Krylov
+ * dimension r*b), full block re-orthogonalisation on both sides (Alg. 5),
+ * basic restart with the b leading Ritz vectors, repeated until
+ * max_j ||A v_j - s_j u_j||_2 <= opts->tol * s_1 or opts->max_restarts.
+ * The start block is N(0,1) Philox4x32-10 (key = seed, stream 2),
+ * orthonormalised by CholeskyQR2 (S1), unless opts->start_block is given.
+ * Outputs as tsvd_rsvd.  Requires 1 <= b <= TSVD_MAX_BLOCK, r >= 1,
+ * 1 <= k <= r*b <= min(m, n), r*b <= TSVD_MAX_SMALL_SVD.
+ * Returns TSVD_NOT_CONVERGED if the tolerance was not met. */
+int tsvd_blanczos(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint64_t seed,
+                  const tsvd_opts* opts, void* ws, size_t ws_bytes,
+                  double* sigma, double* U, double* V, tsvd_info* info);
+
+/* ---- building blocks ---------------------------------------------------- */
+
+/* Start block (Sec. 4: N(0,1) start vectors): out[i*ld + j], i < rows, j < cols.
+ * Element e = i*cols + j uses Philox4x32-10 (Salmon et al., SC'11) at counter
+ * (e/2 mod 2^32, e/2 >> 32, stream_id, 0), key (seed mod 2^32, seed >> 32);
+ * uniforms u = ((w_a >> 5) 2^26 + (w_b >> 6) + 1) 2^-53 from words (w0,w1), (w2,w3);
+ * Box-Muller gives sqrt(-2 ln u1) cos(2 pi u2) (even e) or sin(...) (odd e). */
+int tsvd_gaussian_block(int64_t rows, int64_t cols, uint64_t seed, uint32_t stream_id,
+                        double* out, int64_t ld, void* stream);
+
+/* CSR(A^T) of an m x n CSR matrix (needed by the A^T products, Table 1 S3 of
+ * Alg. 1 and S2 of Alg. 2).  Outputs t_row_ptr[n+1], t_col_idx[nnz],
+ * t_val[nnz]; within each row of A^T the entries are in increasing original
+ * row order, so the output is deterministic.  Validates the input CSR on the
+ * device (TSVD_ERR_INVALID_ARG on a bad structure). */
+int tsvd_csr_transpose_workspace(int64_t m, int64_t n, int64_t nnz, size_t* bytes);
+int tsvd_csr_transpose(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz,
+                       const int32_t* row_ptr, const int32_t* col_idx, const double* val,
+                       int32_t* t_row_ptr, int32_t* t_col_idx, double* t_val,
+                       void* ws, size_t ws_bytes, void* stream);
+
+/* Y = A X for CSR A (m x n): X is n x w (ldx), Y is m x w (ldy), Table 1 SpMM.
+ * Each y_i sums its row's entries in CSR order.  ws holds the status words
+ * (TSVD_SPMM_WORKSPACE bytes); an entry whose column lies outside [0, n) is
+ * skipped and reported as TSVD_ERR_INVALID_ARG. */
+#define TSVD_SPMM_WORKSPACE 256
+int tsvd_spmm(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz,
+              const int32_t* row_ptr, const int32_t* col_idx, const double* val,
+              int w, const double* X, int64_t ldx, double* Y, int64_t ldy,
+              void* ws, size_t ws_bytes, void* stream);
+
+/* Y = op(A) X for dense row-major A (m x n, lda): trans = 0 gives A X
+ * (X n x w, Y m x w); trans = 1 gives A^T X (X m x w, Y n x w).
+ * The dense GEMM of Table 1 (the products marked * there). */
+int tsvd_dense_mm_workspace(int trans, int64_t m, int64_t n, int w, size_t* bytes);
+int tsvd_dense_mm(tsvd_handle* h, int trans, int64_t m, int64_t n, const double* A, int64_t lda,
+                  int w, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                  void* ws, size_t ws_bytes, void* stream);
+
+/* Workspace bytes for the orthogonalisation entry points below on a q-row
+ * block of width b against s earlier columns. */
+int tsvd_orth_workspace(int64_t q, int64_t s, int b, size_t* bytes);
+
+/* CholeskyQR2, Alg. 4 (Sec. 3.2): in place Y (q x b, ldy) <- Q with Q^T Q = I and
+ * R (b x b, row-major, ld = b, upper triangular, positive diagonal) with
+ * Y_in = Q R, R = Lbar^T L^T.  On a Cholesky breakdown (pivot <= b*eps*max W_ii)
+ * the block is redone by column-wise classical Gram-Schmidt with
+ * re-orthogonalisation (Sec. 3.2); columns found numerically dependent are
+ * replaced by Philox columns (key = seed, stream 0x100 + t, t = *replacements,
+ * which is advanced).  *breakdowns (may be NULL) is incremented per fallback.
+ * Requires 1 <= b <= TSVD_MAX_BLOCK, q >= b. */
+int tsvd_cholqr2(tsvd_handle* h, int64_t q, int b, double* Y, int64_t ldy, double* R,
+                 uint64_t seed, int* replacements, int* breakdowns,
+                 void* ws, size_t ws_bytes, void* stream);
+
+/* CGS-CQR2, Alg. 5 (Sec. 3.3): orthogonalises Y (q x b) in place against the
+ * orthonormal columns of P (q x s, ldp), two passes of block classical
+ * Gram-Schmidt each followed by a CholeskyQR step: Y_in = P H + Q R with
+ * P^T Q = 0, Q^T Q = I.  H (s x b, ld = b) may be NULL when not wanted; it is
+ * H + Hbar L^T (the exact sum of the two passes).  R as tsvd_cholqr2.
+ * s = 0 reduces to tsvd_cholqr2. */
+int tsvd_cgs_cqr2(tsvd_handle* h, int64_t q, int64_t s, int b, const double* P, int64_t ldp,
+                  double* Y, int64_t ldy, double* H, double* R,
+                  uint64_t seed, int* replacements, int* breakdowns,
+                  void* ws, size_t ws_bytes, void* stream);
+
+/* CGS-QR, Alg. 3 (Sec. 3.1): QR of Y (q x r) by column blocks of width b
+ * (the last one narrower if b does not divide r): Y <- Q in place, R (r x r,
+ * ld = r) upper triangular assembled from [H_j; R_j].  1 <= b <= TSVD_MAX_BLOCK. */
+int tsvd_cgs_qr(tsvd_handle* h, int64_t q, int r, int b, double* Y, int64_t ldy, double* R,
+                uint64_t seed, int* replacements, int* breakdowns,
+                void* ws, size_t ws_bytes, void* stream);
+
+/* Small SVD (Alg. 1 S5, Alg. 2 S6) of the n x n matrix B (ldb) by one-sided
+ * Jacobi (Hestenes) with parallel round-robin pair ordering:
+ * B = Ubar diag(sigma) Vbar^T, sigma descending, Ubar and Vbar n x n
+ * row-major (ld = n), the largest-magnitude entry of each Vbar column
+ * positive.  *sweeps (may be NULL) receives the sweep count.
+ * Requires 1 <= n <= TSVD_MAX_SMALL_SVD. */
+int tsvd_small_svd_workspace(int n, size_t* bytes);
+int tsvd_small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb,
+                   double* Ubar, double* sigma, double* Vbar, int* sweeps,
+                   void* ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSVD_H_ */

@@ -1,0 +1,369 @@
+"""Python entry points over the C ABI: argument marshalling only.
+
+Every computation runs in ``libtsvd.so``; this module only builds descriptors,
+allocates outputs and workspace with PyTorch (device memory) or numpy (host
+memory), passes the current CUDA stream, and raises ``TsvdError`` on failure.
+Matrices:
+
+* ``CsrMatrix`` (int32 ``row_ptr``/``col_idx`` and float64 ``val`` tensors, on the
+  GPU or in host memory), a ``torch.sparse_csr`` tensor, or a ``scipy.sparse``
+  matrix (host);
+* a dense float64 ``torch.Tensor`` (GPU or host) or ``numpy.ndarray`` (host),
+  row-major.
+
+Host inputs are staged onto the GPU by the library inside the call; ``output="host"``
+returns numpy arrays copied back inside the call.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _capi as capi
+
+_handles: dict = {}
+
+
+def _dev_index(device=None) -> int:
+    if device is None:
+        return torch.cuda.current_device()
+    d = torch.device(device)
+    return d.index if d.index is not None else torch.cuda.current_device()
+
+
+def handle(device=None):
+    """Library handle of a CUDA device (created once per device)."""
+    lib = capi.load()
+    idx = _dev_index(device)
+    h = _handles.get(idx)
+    if h is None:
+        hp = C.c_void_p()
+        capi.check(lib.tsvd_create(C.byref(hp), idx), "tsvd_create")
+        h = hp
+        _handles[idx] = h
+    return h
+
+
+def _stream_ptr(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+@dataclasses.dataclass
+class CsrMatrix:
+    """CSR matrix with int32 indices and float64 values (GPU or host tensors)."""
+    row_ptr: torch.Tensor
+    col_idx: torch.Tensor
+    val: torch.Tensor
+    shape: tuple
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col_idx.numel())
+
+    @property
+    def device(self):
+        return self.val.device
+
+    @staticmethod
+    def from_scipy(A, device="cuda", pin_memory: bool = False) -> "CsrMatrix":
+        import scipy.sparse as sp
+        A = sp.csr_matrix(A)
+        rp = torch.from_numpy(np.ascontiguousarray(A.indptr, dtype=np.int32))
+        ci = torch.from_numpy(np.ascontiguousarray(A.indices, dtype=np.int32))
+        va = torch.from_numpy(np.ascontiguousarray(A.data, dtype=np.float64))
+        if str(device) == "cpu":
+            if pin_memory:
+                rp, ci, va = rp.pin_memory(), ci.pin_memory(), va.pin_memory()
+            return CsrMatrix(rp, ci, va, tuple(A.shape))
+        return CsrMatrix(rp.to(device), ci.to(device), va.to(device), tuple(A.shape))
+
+    def to_scipy(self):
+        import scipy.sparse as sp
+        return sp.csr_matrix((self.val.cpu().numpy(), self.col_idx.cpu().numpy(), self.row_ptr.cpu().numpy()),
+                             shape=self.shape)
+
+
+def _ptr(t) -> int:
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _desc(A):
+    """(TsvdMatrix, keep-alive list, torch.device or None for host)."""
+    import scipy.sparse as sp
+    d = capi.TsvdMatrix()
+    keep = []
+    if isinstance(A, torch.Tensor) and A.layout == torch.sparse_csr:
+        A = CsrMatrix(A.crow_indices().to(torch.int32), A.col_indices().to(torch.int32),
+                      A.values().to(torch.float64), tuple(A.shape))
+    if sp.issparse(A):
+        A = sp.csr_matrix(A)
+        rp = np.ascontiguousarray(A.indptr, dtype=np.int32)
+        ci = np.ascontiguousarray(A.indices, dtype=np.int32)
+        va = np.ascontiguousarray(A.data, dtype=np.float64)
+        keep += [rp, ci, va]
+        d.m, d.n = A.shape
+        d.format, d.location = capi.TSVD_CSR, capi.TSVD_HOST
+        d.val, d.row_ptr, d.col_idx, d.nnz = va.ctypes.data, rp.ctypes.data, ci.ctypes.data, ci.size
+        return d, keep, None
+    if isinstance(A, CsrMatrix):
+        for t, dt in ((A.row_ptr, torch.int32), (A.col_idx, torch.int32), (A.val, torch.float64)):
+            if t.dtype != dt or not t.is_contiguous():
+                raise TypeError("CsrMatrix needs contiguous int32 indices and float64 values")
+        keep += [A.row_ptr, A.col_idx, A.val]
+        d.m, d.n = A.shape
+        d.format = capi.TSVD_CSR
+        dev = A.val.device
+        d.location = capi.TSVD_DEVICE if dev.type == "cuda" else capi.TSVD_HOST
+        d.val, d.row_ptr, d.col_idx, d.nnz = A.val.data_ptr(), A.row_ptr.data_ptr(), A.col_idx.data_ptr(), A.nnz
+        return d, keep, (dev if dev.type == "cuda" else None)
+    if isinstance(A, np.ndarray):
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        keep.append(A)
+        d.m, d.n = A.shape
+        d.format, d.location = capi.TSVD_DENSE, capi.TSVD_HOST
+        d.val, d.ld = A.ctypes.data, A.shape[1]
+        return d, keep, None
+    if isinstance(A, torch.Tensor):
+        if A.dtype != torch.float64 or A.dim() != 2 or A.stride(1) != 1:
+            raise TypeError("dense A must be a 2-D float64 tensor with unit column stride")
+        keep.append(A)
+        d.m, d.n = A.shape
+        d.format = capi.TSVD_DENSE
+        d.location = capi.TSVD_DEVICE if A.is_cuda else capi.TSVD_HOST
+        d.val, d.ld = A.data_ptr(), A.stride(0)
+        return d, keep, (A.device if A.is_cuda else None)
+    raise TypeError(f"unsupported matrix type {type(A)!r}")
+
+
+def _ws(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+@dataclasses.dataclass
+class SvdResult:
+    sigma: object
+    U: object
+    V: object
+    info: dict
+    status: int
+
+
+def _run_driver(fn_name, method, A, k, a, c, seed, tol, max_restarts, qr_block, start_block, output, device,
+                profile=False):
+    lib = capi.load()
+    desc, keep, dev = _desc(A)
+    if dev is None:
+        dev = torch.device("cuda", _dev_index(device))
+    opts = capi.TsvdOpts()
+    lib.tsvd_default_opts(C.byref(opts))
+    opts.tol = float(tol)
+    opts.max_restarts = int(max_restarts)
+    opts.qr_block = int(qr_block)
+    opts.output_location = capi.TSVD_HOST if output == "host" else capi.TSVD_DEVICE
+    opts.flags = capi.TSVD_FLAG_PROFILE if profile else 0
+    if start_block is not None:
+        if not (isinstance(start_block, torch.Tensor) and start_block.is_cuda and start_block.dtype == torch.float64
+                and start_block.is_contiguous()):
+            raise TypeError("start_block must be a contiguous float64 CUDA tensor")
+        keep.append(start_block)
+        opts.start_block = start_block.data_ptr()
+    with torch.cuda.device(dev):
+        opts.stream = _stream_ptr(dev)
+        nbytes = C.c_size_t()
+        capi.check(lib.tsvd_workspace_size(C.byref(desc), method, k, a, c, C.byref(opts), C.byref(nbytes)),
+                   "tsvd_workspace_size")
+        ws = _ws(nbytes.value, dev)
+        m, n = int(desc.m), int(desc.n)
+        if output == "host":
+            sigma = np.empty(k)
+            U = np.empty((m, k))
+            V = np.empty((n, k))
+        else:
+            sigma = torch.empty(k, dtype=torch.float64, device=dev)
+            U = torch.empty((m, k), dtype=torch.float64, device=dev)
+            V = torch.empty((n, k), dtype=torch.float64, device=dev)
+        info = capi.TsvdInfo()
+        rc = getattr(lib, fn_name)(handle(dev), C.byref(desc), k, a, c, C.c_uint64(seed), C.byref(opts),
+                                   ws.data_ptr(), ws.numel(), _ptr(sigma), _ptr(U), _ptr(V), C.byref(info))
+        capi.check(rc, fn_name, allow_not_converged=True)
+    del keep
+    return SvdResult(sigma, U, V, info.as_dict(), rc)
+
+
+def blanczos(A, k: int, b: int, r: int, seed: int = 0, tol: float = 1e-6, max_restarts: int = 50,
+             start_block: Optional[torch.Tensor] = None, output: str = "device", device=None,
+             profile: bool = False) -> SvdResult:
+    """LancSVD (Alg. 2): k triplets with blocks of width b, r blocks per restart cycle.
+    ``profile`` times every kernel class with CUDA events (``info['prof_*']``)."""
+    return _run_driver("tsvd_blanczos", capi.TSVD_METHOD_BLANCZOS, A, k, b, r, seed, tol, max_restarts, 0,
+                       start_block, output, device, profile)
+
+
+def rsvd(A, k: int, p: int, q: int, seed: int = 0, qr_block: int = 0, start_block: Optional[torch.Tensor] = None,
+         output: str = "device", device=None, profile: bool = False) -> SvdResult:
+    """RandSVD (Alg. 1): k triplets, oversampling p, q power steps (q + 1 trips)."""
+    return _run_driver("tsvd_rsvd", capi.TSVD_METHOD_RSVD, A, k, p, q, seed, 0.0, 0, qr_block, start_block, output,
+                       device, profile)
+
+
+# ---------------------------------------------------------------------------
+# Building blocks (GPU tensors in, GPU tensors out).
+# ---------------------------------------------------------------------------
+def _cuda_f64(t: torch.Tensor, name: str):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.dim() == 2
+            and t.stride(1) == 1):
+        raise TypeError(f"{name} must be a 2-D float64 CUDA tensor with unit column stride")
+
+
+def gaussian_block(rows: int, cols: int, seed: int, stream_id: int, device=None) -> torch.Tensor:
+    """N(0,1) block from Philox4x32-10 + Box-Muller (the library's start blocks)."""
+    lib = capi.load()
+    dev = torch.device("cuda", _dev_index(device))
+    out = torch.empty((rows, cols), dtype=torch.float64, device=dev)
+    with torch.cuda.device(dev):
+        capi.check(lib.tsvd_gaussian_block(rows, cols, C.c_uint64(seed), C.c_uint32(stream_id), out.data_ptr(),
+                                           max(cols, 1), _stream_ptr(dev)), "tsvd_gaussian_block")
+    return out
+
+
+def csr_transpose(A: CsrMatrix) -> CsrMatrix:
+    """CSR of A^T (rows of A^T list original rows in increasing order)."""
+    lib = capi.load()
+    dev = A.val.device
+    m, n = A.shape
+    nnz = A.nnz
+    trp = torch.empty(n + 1, dtype=torch.int32, device=dev)
+    tci = torch.empty(max(nnz, 1), dtype=torch.int32, device=dev)
+    tva = torch.empty(max(nnz, 1), dtype=torch.float64, device=dev)
+    with torch.cuda.device(dev):
+        nb = C.c_size_t()
+        capi.check(lib.tsvd_csr_transpose_workspace(m, n, nnz, C.byref(nb)), "tsvd_csr_transpose_workspace")
+        ws = _ws(nb.value, dev)
+        capi.check(lib.tsvd_csr_transpose(handle(dev), m, n, nnz, A.row_ptr.data_ptr(), A.col_idx.data_ptr(),
+                                          A.val.data_ptr(), trp.data_ptr(), tci.data_ptr(), tva.data_ptr(),
+                                          ws.data_ptr(), ws.numel(), _stream_ptr(dev)), "tsvd_csr_transpose")
+    return CsrMatrix(trp, tci[:nnz], tva[:nnz], (n, m))
+
+
+def spmm(A: CsrMatrix, X: torch.Tensor) -> torch.Tensor:
+    """Y = A X for CSR A on the GPU."""
+    lib = capi.load()
+    _cuda_f64(X, "X")
+    dev = X.device
+    m, n = A.shape
+    w = X.shape[1]
+    Y = torch.empty((m, w), dtype=torch.float64, device=dev)
+    with torch.cuda.device(dev):
+        ws = _ws(capi.TSVD_SPMM_WORKSPACE, dev)
+        capi.check(lib.tsvd_spmm(handle(dev), m, n, A.nnz, A.row_ptr.data_ptr(), A.col_idx.data_ptr(),
+                                 A.val.data_ptr(), w, X.data_ptr(), X.stride(0), Y.data_ptr(), max(w, 1),
+                                 ws.data_ptr(), ws.numel(), _stream_ptr(dev)), "tsvd_spmm")
+    return Y
+
+
+def dense_mm(A: torch.Tensor, X: torch.Tensor, trans: bool = False) -> torch.Tensor:
+    """op(A) X for dense row-major A on the GPU."""
+    lib = capi.load()
+    _cuda_f64(A, "A")
+    _cuda_f64(X, "X")
+    dev = A.device
+    m, n = A.shape
+    w = X.shape[1]
+    Y = torch.empty(((n if trans else m), w), dtype=torch.float64, device=dev)
+    with torch.cuda.device(dev):
+        nb = C.c_size_t()
+        capi.check(lib.tsvd_dense_mm_workspace(int(trans), m, n, w, C.byref(nb)), "tsvd_dense_mm_workspace")
+        ws = _ws(nb.value, dev)
+        capi.check(lib.tsvd_dense_mm(handle(dev), int(trans), m, n, A.data_ptr(), A.stride(0), w, X.data_ptr(),
+                                     X.stride(0), Y.data_ptr(), max(w, 1), ws.data_ptr(), ws.numel(),
+                                     _stream_ptr(dev)), "tsvd_dense_mm")
+    return Y
+
+
+def _orth_ws(q, s, b, dev):
+    nb = C.c_size_t()
+    capi.check(capi.load().tsvd_orth_workspace(q, s, b, C.byref(nb)), "tsvd_orth_workspace")
+    return _ws(nb.value + 256 * 4 + 8 * (s + b) * b, dev)
+
+
+def cholqr2(Y: torch.Tensor, seed: int = 0):
+    """CholeskyQR2 (Alg. 4) of a copy of Y: returns (Q, R, breakdowns)."""
+    lib = capi.load()
+    _cuda_f64(Y, "Y")
+    dev = Y.device
+    Q = Y.clone()
+    q, b = Q.shape
+    R = torch.empty((b, b), dtype=torch.float64, device=dev)
+    rep, bd = C.c_int(0), C.c_int(0)
+    with torch.cuda.device(dev):
+        ws = _orth_ws(q, 0, b, dev)
+        capi.check(lib.tsvd_cholqr2(handle(dev), q, b, Q.data_ptr(), Q.stride(0), R.data_ptr(), C.c_uint64(seed),
+                                    C.byref(rep), C.byref(bd), ws.data_ptr(), ws.numel(), _stream_ptr(dev)),
+                   "tsvd_cholqr2")
+    return Q, R, bd.value
+
+
+def cgs_cqr2(Y: torch.Tensor, P: torch.Tensor, seed: int = 0):
+    """CGS-CQR2 (Alg. 5) of a copy of Y against P: returns (Q, H, R, breakdowns)."""
+    lib = capi.load()
+    _cuda_f64(Y, "Y")
+    _cuda_f64(P, "P")
+    dev = Y.device
+    Q = Y.clone()
+    q, b = Q.shape
+    s = P.shape[1]
+    R = torch.empty((b, b), dtype=torch.float64, device=dev)
+    H = torch.empty((max(s, 1), b), dtype=torch.float64, device=dev)
+    rep, bd = C.c_int(0), C.c_int(0)
+    with torch.cuda.device(dev):
+        ws = _orth_ws(q, s, b, dev)
+        capi.check(lib.tsvd_cgs_cqr2(handle(dev), q, s, b, P.data_ptr(), P.stride(0), Q.data_ptr(), Q.stride(0),
+                                     H.data_ptr(), R.data_ptr(), C.c_uint64(seed), C.byref(rep), C.byref(bd),
+                                     ws.data_ptr(), ws.numel(), _stream_ptr(dev)), "tsvd_cgs_cqr2")
+    return Q, H[:s], R, bd.value
+
+
+def cgs_qr(Y: torch.Tensor, b: int, seed: int = 0):
+    """CGS-QR (Alg. 3) of a copy of Y with column blocks of width b: returns (Q, R, breakdowns)."""
+    lib = capi.load()
+    _cuda_f64(Y, "Y")
+    dev = Y.device
+    Q = Y.clone()
+    q, r = Q.shape
+    R = torch.empty((r, r), dtype=torch.float64, device=dev)
+    rep, bd = C.c_int(0), C.c_int(0)
+    with torch.cuda.device(dev):
+        ws = _orth_ws(q, r, min(b, r), dev)
+        capi.check(lib.tsvd_cgs_qr(handle(dev), q, r, b, Q.data_ptr(), Q.stride(0), R.data_ptr(), C.c_uint64(seed),
+                                   C.byref(rep), C.byref(bd), ws.data_ptr(), ws.numel(), _stream_ptr(dev)),
+                   "tsvd_cgs_qr")
+    return Q, R, bd.value
+
+
+def small_svd(B: torch.Tensor):
+    """SVD of a small square matrix by the device Jacobi kernel: (Ubar, sigma, Vbar, sweeps)."""
+    lib = capi.load()
+    _cuda_f64(B, "B")
+    dev = B.device
+    n = B.shape[0]
+    if B.shape[1] != n:
+        raise ValueError("B must be square")
+    U = torch.empty((n, n), dtype=torch.float64, device=dev)
+    V = torch.empty((n, n), dtype=torch.float64, device=dev)
+    s = torch.empty(n, dtype=torch.float64, device=dev)
+    sweeps = C.c_int(0)
+    with torch.cuda.device(dev):
+        nb = C.c_size_t()
+        capi.check(lib.tsvd_small_svd_workspace(n, C.byref(nb)), "tsvd_small_svd_workspace")
+        ws = _ws(nb.value, dev)
+        capi.check(lib.tsvd_small_svd(handle(dev), n, B.data_ptr(), B.stride(0), U.data_ptr(), s.data_ptr(),
+                                      V.data_ptr(), C.byref(sweeps), ws.data_ptr(), ws.numel(), _stream_ptr(dev)),
+                   "tsvd_small_svd")
+    return U, s, V, sweeps.value

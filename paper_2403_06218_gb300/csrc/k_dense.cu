@@ -1,0 +1,577 @@
+// Dense FP64 kernels of the orthogonalisation building blocks (Table 1):
+//   gemm_tn   C = X^T Z        Gram W = Q^T Q (Alg. 4 S1/S4, Alg. 5 S3/S8),
+//                              projection H = P^T Q (Alg. 5 S1/S6), A^T X for dense A;
+//   gemm_nn   Y = b Y + a X M  update Q - P H (Alg. 5 S2/S7), TRSM applied as the
+//                              product with L^{-T} (Alg. 4 S3/S6, Alg. 5 S5/S10),
+//                              Ritz/restart products (Alg. 1 S6/S7, Alg. 2 S7-S9), A X;
+//   chol_inv  W = L L^T and L^{-T} of the b x b Gram matrix (POTRF of Table 1);
+//   trmm      R = Lbar^T L^T (Alg. 4 S7, Alg. 5 S11);
+// plus the Philox/Box-Muller start block, residual column norms, the Lanczos
+// residual estimate and the output sign convention.
+//
+// On GB300 the FP64 pipe issues 2 DFMA/clk/SM (about 1.2 TFLOP/s for the chip),
+// which puts every one of these products far above the FP64 ridge point: the
+// design goal is the minimum number of DFMAs spread over all SMs, not memory
+// traffic.  Symmetric Gram matrices compute only their upper half, triangular
+// factors skip their zero half at warp granularity, and split-K partial sums
+// are reduced in a fixed order so results are bitwise reproducible.
+#include "tsvd_internal.cuh"
+
+namespace tsvd {
+namespace {
+
+// ---------------------------------------------------------------------------
+// gemm_tn: CTA = 4 warps computes a 32 x 32 region of C over one row slab.
+// Warp (wr, wc) owns a 16 x 16 sub-tile; lane owns C[i][jg .. jg+7].
+// ---------------------------------------------------------------------------
+constexpr int kTnR = 32;
+constexpr int kTnKc = 32;
+
+__device__ inline void decode_upper(int lin, int nr, int& ri, int& rj) {
+    int r = 0;
+    while (lin >= nr - r) {
+        lin -= nr - r;
+        ++r;
+    }
+    ri = r;
+    rj = r + lin;
+}
+
+__global__ void __launch_bounds__(128) gemm_tn_kernel(int64_t q, int64_t s, int64_t b,
+                                                      const double* __restrict__ X, int64_t ldx,
+                                                      const double* __restrict__ Z, int64_t ldz,
+                                                      double* __restrict__ out, int64_t ldo,
+                                                      int64_t slab_stride, int64_t slab_rows, int symmetric,
+                                                      int nreg_s, int nreg_b) {
+    __shared__ double Xs[kTnKc][kTnR];
+    __shared__ double Zs[kTnKc][kTnR];
+    int ri, rj;
+    if (symmetric) {
+        decode_upper((int)blockIdx.x, nreg_s, ri, rj);
+    } else {
+        ri = (int)blockIdx.x / nreg_b;
+        rj = (int)blockIdx.x % nreg_b;
+    }
+    const int64_t r0 = (int64_t)blockIdx.y * slab_rows;
+    const int64_t r1 = min(q, r0 + slab_rows);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int wr = warp >> 1, wc = warp & 1;
+    const int i = lane >> 1, jg = (lane & 1) * 8;
+    const bool active = !(symmetric && ri == rj && wr > wc);
+    double acc[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) acc[t] = 0.0;
+    const int64_t xc0 = (int64_t)ri * kTnR, zc0 = (int64_t)rj * kTnR;
+    for (int64_t k0 = r0; k0 < r1; k0 += kTnKc) {
+        for (int idx = tid; idx < kTnKc * kTnR; idx += 128) {
+            const int rr = idx / kTnR, cc = idx % kTnR;
+            const int64_t row = k0 + rr;
+            const bool rin = row < r1;
+            Xs[rr][cc] = (rin && xc0 + cc < s) ? X[row * ldx + xc0 + cc] : 0.0;
+            Zs[rr][cc] = (rin && zc0 + cc < b) ? Z[row * ldz + zc0 + cc] : 0.0;
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll 4
+            for (int kk = 0; kk < kTnKc; ++kk) {
+                const double x = Xs[kk][wr * 16 + i];
+                const double* zr = &Zs[kk][wc * 16 + jg];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) acc[t] = fma(x, zr[t], acc[t]);
+            }
+        }
+        __syncthreads();
+    }
+    if (!active) return;
+    const int64_t orow = xc0 + wr * 16 + i;
+    if (orow >= s) return;
+    double* o = out + (int64_t)blockIdx.y * slab_stride + orow * ldo + zc0 + wc * 16 + jg;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        if (zc0 + wc * 16 + jg + t < b) o[t] = acc[t];
+    }
+}
+
+// C[i][j] = sum over slabs (fixed order) of partial[slab][i][j]; symmetric reads
+// the upper element for both halves.
+__global__ void gemm_tn_reduce_kernel(int64_t s, int64_t b, int slabs, const double* __restrict__ partial,
+                                      int64_t slab_stride, double* __restrict__ C, int64_t ldc, int symmetric) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= s * b) return;
+    int64_t i = idx / b, j = idx % b;
+    const int64_t ii = (symmetric && i > j) ? j : i;
+    const int64_t jj = (symmetric && i > j) ? i : j;
+    double acc = 0.0;
+    for (int sl = 0; sl < slabs; ++sl) acc += partial[(int64_t)sl * slab_stride + ii * b + jj];
+    C[i * ldc + j] = acc;
+}
+
+struct TnPlan {
+    int nreg_s, nreg_b, regions, slabs;
+    int64_t slab_rows;
+};
+
+TnPlan tn_plan(const tsvd_handle* h, int64_t q, int64_t s, int64_t b, bool symmetric) {
+    TnPlan p;
+    p.nreg_s = (int)((s + kTnR - 1) / kTnR);
+    p.nreg_b = (int)((b + kTnR - 1) / kTnR);
+    p.regions = symmetric ? p.nreg_s * (p.nreg_s + 1) / 2 : p.nreg_s * p.nreg_b;
+    const int64_t target = 8LL * (h ? h->sm_count : 152);
+    int64_t slabs = (target + p.regions - 1) / p.regions;
+    const int64_t max_slabs = (q + 255) / 256;
+    if (slabs > max_slabs) slabs = max_slabs;
+    if (slabs > 65535) slabs = 65535;
+    if (slabs < 1) slabs = 1;
+    int64_t rows = (q + slabs - 1) / slabs;
+    rows = (rows + kTnKc - 1) / kTnKc * kTnKc;
+    if (rows < kTnKc) rows = kTnKc;
+    p.slab_rows = rows;
+    p.slabs = (int)((q + rows - 1) / rows);
+    if (p.slabs < 1) p.slabs = 1;
+    return p;
+}
+
+// ---------------------------------------------------------------------------
+// gemm_nn: CTA = 4 warps, 32 rows; lane = row, warp w owns CW columns of the
+// current panel (4*CW columns).  X tile and M chunk staged in shared memory,
+// output staged for coalesced stores.
+// ---------------------------------------------------------------------------
+template <int CW>
+__global__ void __launch_bounds__(128) gemm_nn_kernel(int64_t q, int64_t s, int64_t b, double alpha,
+                                                      const double* __restrict__ X, int64_t ldx,
+                                                      const double* __restrict__ M, int64_t ldm, double beta,
+                                                      double* Y, int64_t ldy, int upper) {
+    constexpr int PW = 4 * CW;
+    __shared__ double Xs[32][33];
+    __shared__ double Ms[32][PW + 1];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    for (int64_t c0 = 0; c0 < b; c0 += PW) {
+        double acc[CW];
+#pragma unroll
+        for (int c = 0; c < CW; ++c) acc[c] = 0.0;
+        const int64_t jw_hi = c0 + (int64_t)(warp + 1) * CW - 1;  // last column of this warp
+        int64_t kmax = s;
+        if (upper) kmax = min(s, c0 + PW);
+        for (int64_t k0 = 0; k0 < kmax; k0 += 32) {
+            for (int idx = tid; idx < 32 * 32; idx += 128) {
+                const int rr = idx >> 5, kk = idx & 31;
+                const int64_t row = r0 + rr, k = k0 + kk;
+                Xs[rr][kk] = (row < q && k < s) ? X[row * ldx + k] : 0.0;
+            }
+            for (int idx = tid; idx < 32 * PW; idx += 128) {
+                const int kk = idx / PW, cc = idx % PW;
+                const int64_t k = k0 + kk, col = c0 + cc;
+                const bool in = k < s && col < b && !(upper && k > col);
+                Ms[kk][cc] = in ? M[k * ldm + col] : 0.0;
+            }
+            __syncthreads();
+            if (!(upper && k0 > jw_hi)) {
+#pragma unroll 4
+                for (int kk = 0; kk < 32; ++kk) {
+                    const double x = Xs[lane][kk];
+                    const double* mr = &Ms[kk][warp * CW];
+#pragma unroll
+                    for (int c = 0; c < CW; ++c) acc[c] = fma(x, mr[c], acc[c]);
+                }
+            }
+            __syncthreads();
+        }
+        // stage through shared memory (reusing Ms) for coalesced stores
+#pragma unroll
+        for (int c = 0; c < CW; ++c) Ms[lane][warp * CW + c] = acc[c];
+        __syncthreads();
+        for (int idx = tid; idx < 32 * PW; idx += 128) {
+            const int rr = idx / PW, cc = idx % PW;
+            const int64_t row = r0 + rr, col = c0 + cc;
+            if (row < q && col < b) {
+                double* y = Y + row * ldy + col;
+                const double v = alpha * Ms[rr][cc];
+                *y = (beta != 0.0) ? fma(beta, *y, v) : v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// chol_inv: one CTA.  Right-looking Cholesky in shared memory, breakdown test
+// d <= b*eps*max_i W_ii, then in-place inversion of L (column j from the last
+// to the first, using the already inverted trailing block).
+// ---------------------------------------------------------------------------
+__device__ inline void tri_decode(int idx, int& ii, int& kk) {
+    int r = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
+    while (r * (r + 1) / 2 > idx) --r;
+    while ((r + 1) * (r + 2) / 2 <= idx) ++r;
+    ii = r;
+    kk = idx - r * (r + 1) / 2;
+}
+
+__global__ void __launch_bounds__(256) chol_inv_kernel(int b, const double* __restrict__ W, double* __restrict__ Lt,
+                                                       double* __restrict__ Mt, int* status) {
+    extern __shared__ double sm[];
+    const int ld = b + 1;
+    double* A = sm;
+    double* tmp = sm + (size_t)b * ld;
+    __shared__ double s_thresh;
+    __shared__ int s_bad;
+    const int tid = threadIdx.x;
+    for (int idx = tid; idx < b * b; idx += blockDim.x) A[(idx / b) * ld + idx % b] = W[idx];
+    __syncthreads();
+    if (tid == 0) {
+        double wmax = 0.0;
+        int bad = 0;
+        for (int i = 0; i < b; ++i) {
+            const double d = A[i * ld + i];
+            if (!isfinite(d)) bad = 2;
+            if (d > wmax) wmax = d;
+        }
+        if (bad == 0 && !(wmax > 0.0)) bad = 1;
+        s_bad = bad;
+        s_thresh = (double)b * kEps * wmax;
+    }
+    __syncthreads();
+    for (int j = 0; j < b && s_bad == 0; ++j) {
+        const double d = A[j * ld + j];
+        if (!isfinite(d) || !(d > s_thresh)) {
+            __syncthreads();
+            if (tid == 0) s_bad = isfinite(d) ? 1 : 2;
+            __syncthreads();
+            break;
+        }
+        const double ljj = sqrt(d);
+        for (int i = j + 1 + tid; i < b; i += blockDim.x) A[i * ld + j] /= ljj;
+        __syncthreads();
+        if (tid == 0) A[j * ld + j] = ljj;
+        const int nn = b - j - 1;
+        const int cnt = nn * (nn + 1) / 2;
+        for (int idx = tid; idx < cnt; idx += blockDim.x) {
+            int ii, kk;
+            tri_decode(idx, ii, kk);
+            const int i = j + 1 + ii, k = j + 1 + kk;
+            A[i * ld + k] = fma(-A[i * ld + j], A[k * ld + j], A[i * ld + k]);
+        }
+        __syncthreads();
+    }
+    if (s_bad) {
+        if (tid == 0) atomicOr(&status[s_bad == 2 ? kStNonfinite : kStBreakdown], 1);
+        for (int idx = tid; idx < b * b; idx += blockDim.x) {
+            const double v = (idx / b == idx % b) ? 1.0 : 0.0;
+            Lt[idx] = v;
+            Mt[idx] = v;
+        }
+        return;
+    }
+    // Lt = L^T (upper)
+    for (int idx = tid; idx < b * b; idx += blockDim.x) {
+        const int i = idx / b, j = idx % b;
+        Lt[idx] = (j >= i) ? A[j * ld + i] : 0.0;
+    }
+    __syncthreads();
+    // in-place inverse of the lower triangle
+    for (int j = b - 1; j >= 0; --j) {
+        if (tid == 0) A[j * ld + j] = 1.0 / A[j * ld + j];
+        for (int i = j + 1 + tid; i < b; i += blockDim.x) tmp[i] = A[i * ld + j];
+        __syncthreads();
+        const double ajj = -A[j * ld + j];
+        for (int i = j + 1 + tid; i < b; i += blockDim.x) {
+            double acc = 0.0;
+            for (int k = j + 1; k <= i; ++k) acc = fma(A[i * ld + k], tmp[k], acc);
+            A[i * ld + j] = ajj * acc;
+        }
+        __syncthreads();
+    }
+    // Mt = L^{-T} (upper)
+    for (int idx = tid; idx < b * b; idx += blockDim.x) {
+        const int i = idx / b, j = idx % b;
+        Mt[idx] = (j >= i) ? A[j * ld + i] : 0.0;
+    }
+}
+
+// out = A U, A and U upper triangular b x b (ld b).  Block = one row i.
+__global__ void trmm_upper_kernel(int b, const double* __restrict__ A, const double* __restrict__ U,
+                                  double* __restrict__ out, int64_t ldo, int trans) {
+    const int i = blockIdx.x;
+    for (int j = threadIdx.x; j < b; j += blockDim.x) {
+        double acc = 0.0;
+        for (int k = i; k <= j; ++k) acc = fma(A[i * b + k], U[k * b + j], acc);
+        if (trans)
+            out[(int64_t)j * ldo + i] = acc;
+        else
+            out[(int64_t)i * ldo + j] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11) and Box-Muller.
+// ---------------------------------------------------------------------------
+__device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+    }
+}
+
+__global__ void gaussian_kernel(int64_t rows, int64_t cols, uint32_t k0, uint32_t k1, uint32_t sid,
+                                double* __restrict__ out, int64_t ld) {
+    const int64_t n_el = rows * cols;
+    const int64_t n_pairs = (n_el + 1) / 2;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_pairs;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c[4] = {(uint32_t)(t & 0xffffffffu), (uint32_t)((uint64_t)t >> 32), sid, 0u};
+        philox4x32_10(c, k0, k1);
+        const double two53 = 1.1102230246251565e-16;  // 2^-53
+        const double u1 = (double)(((uint64_t)(c[0] >> 5) << 26) + (c[1] >> 6) + 1) * two53;
+        const double u2 = (double)(((uint64_t)(c[2] >> 5) << 26) + (c[3] >> 6) + 1) * two53;
+        const double rad = sqrt(-2.0 * log(u1));
+        double sn, cs;
+        sincospi(2.0 * u2, &sn, &cs);
+        const int64_t e0 = 2 * t, e1 = 2 * t + 1;
+        out[(e0 / cols) * ld + (e0 % cols)] = rad * cs;
+        if (e1 < n_el) out[(e1 / cols) * ld + (e1 % cols)] = rad * sn;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Residual column sums of squares, Lanczos estimate, sign convention.
+// ---------------------------------------------------------------------------
+__global__ void colres_partial_kernel(int64_t q, int k, const double* __restrict__ Y, int64_t ldy,
+                                      const double* __restrict__ U, int64_t ldu, const double* __restrict__ sigma,
+                                      double* __restrict__ partial, int64_t rows_per) {
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per, r1 = min(q, r0 + rows_per);
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        const double sj = sigma[j];
+        double acc = 0.0;
+        for (int64_t i = r0; i < r1; ++i) {
+            const double d = fma(-U[i * ldu + j], sj, Y[i * ldy + j]);
+            acc = fma(d, d, acc);
+        }
+        partial[(int64_t)blockIdx.x * k + j] = acc;
+    }
+}
+
+__global__ void colres_reduce_kernel(int k, int g, const double* __restrict__ partial, double* __restrict__ out) {
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        double acc = 0.0;
+        for (int t = 0; t < g; ++t) acc += partial[(int64_t)t * k + j];
+        out[j] = acc;
+    }
+}
+
+__global__ void lanczos_rho_kernel(int b, int k, const double* __restrict__ Rr, const double* __restrict__ V,
+                                   int64_t ldv, double* __restrict__ rho) {
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        double acc = 0.0;
+        for (int i = 0; i < b; ++i) {
+            double yi = 0.0;
+            for (int l = i; l < b; ++l) yi = fma(Rr[i * b + l], V[(int64_t)l * ldv + j], yi);
+            acc = fma(yi, yi, acc);
+        }
+        rho[j] = sqrt(acc);
+    }
+}
+
+__global__ void argmax_partial_kernel(int64_t n, int k, const double* __restrict__ V, int64_t ldv,
+                                      int64_t rows_per, double* __restrict__ pv, int64_t* __restrict__ pi) {
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per, r1 = min(n, r0 + rows_per);
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        double best = -1.0;
+        int64_t bi = 0;
+        for (int64_t i = r0; i < r1; ++i) {
+            const double a = fabs(V[i * ldv + j]);
+            if (a > best) {
+                best = a;
+                bi = i;
+            }
+        }
+        pv[(int64_t)blockIdx.x * k + j] = best;
+        pi[(int64_t)blockIdx.x * k + j] = bi;
+    }
+}
+
+__global__ void argmax_sign_kernel(int k, int g, const double* __restrict__ pv, const int64_t* __restrict__ pi,
+                                   const double* __restrict__ V, int64_t ldv, double* __restrict__ sgn) {
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        double best = -1.0;
+        int64_t bi = 0;
+        for (int t = 0; t < g; ++t) {
+            const double a = pv[(int64_t)t * k + j];
+            if (a > best) {
+                best = a;
+                bi = pi[(int64_t)t * k + j];
+            }
+        }
+        sgn[j] = V[bi * ldv + j] < 0.0 ? -1.0 : 1.0;
+    }
+}
+
+__global__ void apply_sign_kernel(int64_t rows, int k, double* __restrict__ A, int64_t lda,
+                                  const double* __restrict__ sgn) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * k) return;
+    const int64_t i = idx / k;
+    const int j = (int)(idx % k);
+    if (sgn[j] < 0.0) A[i * lda + j] = -A[i * lda + j];
+}
+
+int colres_groups(int64_t q) {
+    int64_t g = (q + 255) / 256;
+    if (g > 512) g = 512;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+size_t gemm_tn_ws(tsvd_handle* h, int64_t q, int64_t s, int64_t b, bool symmetric) {
+    const TnPlan p = tn_plan(h, q, s, b, symmetric);
+    if (p.slabs == 1 && !symmetric) return 0;
+    return align256(sizeof(double) * (size_t)p.slabs * (size_t)s * (size_t)b);
+}
+
+cudaError_t gemm_tn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, const double* X, int64_t ldx,
+                    const double* Z, int64_t ldz, double* C, int64_t ldc, bool symmetric, double* partial,
+                    cudaStream_t st) {
+    if (s == 0 || b == 0) return cudaSuccess;
+    const TnPlan p = tn_plan(h, q, s, b, symmetric);
+    if (q == 0) {
+        for (int64_t i = 0; i < s; ++i) {
+            cudaError_t e = cudaMemsetAsync(C + i * ldc, 0, sizeof(double) * b, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    const dim3 grid((unsigned)p.regions, (unsigned)p.slabs);
+    // algorithmic work: 2qsb flops (the upper half, q b (b+1), for a Gram matrix);
+    // compulsory traffic: X and Z read once, C written once
+    ProfScope prof(h, TSVD_K_GEMM_TN, symmetric ? (double)q * b * (b + 1) : 2.0 * q * s * b,
+                   8.0 * ((double)q * (symmetric ? b : s + b) + (double)s * b), st);
+    if (p.slabs == 1 && !symmetric) {
+        h->launches++;
+        gemm_tn_kernel<<<grid, 128, 0, st>>>(q, s, b, X, ldx, Z, ldz, C, ldc, 0, p.slab_rows, 0, p.nreg_s,
+                                             p.nreg_b);
+        return cudaGetLastError();
+    }
+    const int64_t stride = s * b;
+    h->launches += 2;
+    gemm_tn_kernel<<<grid, 128, 0, st>>>(q, s, b, X, ldx, Z, ldz, partial, b, stride, p.slab_rows,
+                                         symmetric ? 1 : 0, p.nreg_s, p.nreg_b);
+    const int64_t tot = s * b;
+    gemm_tn_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(s, b, p.slabs, partial, stride, C, ldc,
+                                                                        symmetric ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t gemm_nn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, double alpha, const double* X, int64_t ldx,
+                    const double* M, int64_t ldm, double beta, double* Y, int64_t ldy, bool upper,
+                    cudaStream_t st) {
+    if (q == 0 || b == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((q + 31) / 32);
+    ProfScope prof(h, TSVD_K_GEMM_NN, upper ? (double)q * b * (b + 1) : 2.0 * q * s * b,
+                   8.0 * ((double)q * s + (double)s * b + (double)q * b * (beta != 0.0 ? 2 : 1)), st);
+    h->launches++;
+    if (b <= 32) {
+        gemm_nn_kernel<8><<<grid, 128, 0, st>>>(q, s, b, alpha, X, ldx, M, ldm, beta, Y, ldy, upper ? 1 : 0);
+    } else if (b <= 64) {
+        gemm_nn_kernel<16><<<grid, 128, 0, st>>>(q, s, b, alpha, X, ldx, M, ldm, beta, Y, ldy, upper ? 1 : 0);
+    } else {
+        gemm_nn_kernel<32><<<grid, 128, 0, st>>>(q, s, b, alpha, X, ldx, M, ldm, beta, Y, ldy, upper ? 1 : 0);
+    }
+    return cudaGetLastError();
+}
+
+static size_t chol_smem(int b) { return sizeof(double) * ((size_t)b * (b + 1) + b); }
+
+cudaError_t chol_inv(tsvd_handle* h, int b, const double* W, double* Lt, double* Mt, int* status,
+                     cudaStream_t st) {
+    const size_t smem = chol_smem(b);
+    static thread_local int configured_device = -1;
+    if (configured_device != h->device) {
+        cudaError_t e = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)chol_smem(TSVD_MAX_BLOCK));
+        if (e != cudaSuccess) return e;
+        configured_device = h->device;
+    }
+    ProfScope prof(h, TSVD_K_CHOL, 2.0 * b * b * (double)b / 3.0, 24.0 * b * b, st);
+    h->launches++;
+    chol_inv_kernel<<<1, 256, smem, st>>>(b, W, Lt, Mt, status);
+    return cudaGetLastError();
+}
+
+cudaError_t trmm_upper(tsvd_handle* h, int b, const double* A, const double* U, double* out, int64_t ldo,
+                       bool trans, cudaStream_t st) {
+    ProfScope prof(h, TSVD_K_OTHER, b * b * (double)b / 3.0, 24.0 * b * b, st);
+    h->launches++;
+    trmm_upper_kernel<<<b, 128, 0, st>>>(b, A, U, out, ldo, trans ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t gaussian(tsvd_handle* h, int64_t rows, int64_t cols, uint64_t seed, uint32_t stream_id, double* out,
+                     int64_t ld, cudaStream_t st) {
+    const int64_t n_pairs = (rows * cols + 1) / 2;
+    if (n_pairs == 0) return cudaSuccess;
+    int64_t blocks = (n_pairs + 255) / 256;
+    if (blocks > 8LL * h->sm_count * 8) blocks = 8LL * h->sm_count * 8;
+    ProfScope prof(h, TSVD_K_OTHER, 0.0, 8.0 * rows * cols, st);
+    h->launches++;
+    gaussian_kernel<<<(unsigned)blocks, 256, 0, st>>>(rows, cols, (uint32_t)(seed & 0xffffffffu),
+                                                      (uint32_t)(seed >> 32), stream_id, out, ld);
+    return cudaGetLastError();
+}
+
+size_t colres_ws(int64_t q, int k) { return align256(sizeof(double) * (size_t)colres_groups(q) * (size_t)k); }
+
+cudaError_t col_residual_sq(tsvd_handle* h, int64_t q, int k, const double* Y, int64_t ldy, const double* U,
+                            int64_t ldu, const double* sigma, double* out, double* partial, cudaStream_t st) {
+    const int g = colres_groups(q);
+    const int64_t rows_per = (q + g - 1) / g;
+    ProfScope prof(h, TSVD_K_OTHER, 0.0, 0.0, st);
+    h->launches += 2;
+    colres_partial_kernel<<<g, 128, 0, st>>>(q, k, Y, ldy, U, ldu, sigma, partial, rows_per);
+    colres_reduce_kernel<<<1, 128, 0, st>>>(k, g, partial, out);
+    return cudaGetLastError();
+}
+
+cudaError_t lanczos_rho(tsvd_handle* h, int b, int k, const double* Rr, const double* Vlast, int64_t ldv,
+                        double* rho, cudaStream_t st) {
+    ProfScope prof(h, TSVD_K_OTHER, 0.0, 0.0, st);
+    h->launches++;
+    lanczos_rho_kernel<<<1, 128, 0, st>>>(b, k, Rr, Vlast, ldv, rho);
+    return cudaGetLastError();
+}
+
+size_t sign_fix_ws(int64_t n, int k) {
+    const size_t g = (size_t)colres_groups(n);
+    return align256(sizeof(double) * g * k) + align256(sizeof(int64_t) * g * k) + align256(sizeof(double) * k);
+}
+
+cudaError_t sign_fix(tsvd_handle* h, int64_t n, int64_t m, int k, double* V, int64_t ldv, double* U, int64_t ldu,
+                     void* ws, cudaStream_t st) {
+    const int g = colres_groups(n);
+    char* p = static_cast<char*>(ws);
+    double* pv = reinterpret_cast<double*>(p);
+    p += align256(sizeof(double) * (size_t)g * k);
+    int64_t* pi = reinterpret_cast<int64_t*>(p);
+    p += align256(sizeof(int64_t) * (size_t)g * k);
+    double* sgn = reinterpret_cast<double*>(p);
+    const int64_t rows_per = (n + g - 1) / g;
+    ProfScope prof(h, TSVD_K_OTHER, 0.0, 0.0, st);
+    h->launches += 4;
+    argmax_partial_kernel<<<g, 128, 0, st>>>(n, k, V, ldv, rows_per, pv, pi);
+    argmax_sign_kernel<<<1, 128, 0, st>>>(k, g, pv, pi, V, ldv, sgn);
+    if (n * k > 0) apply_sign_kernel<<<(unsigned)((n * k + 255) / 256), 256, 0, st>>>(n, k, V, ldv, sgn);
+    if (m * k > 0) apply_sign_kernel<<<(unsigned)((m * k + 255) / 256), 256, 0, st>>>(m, k, U, ldu, sgn);
+    return cudaGetLastError();
+}
+
+}  // namespace tsvd

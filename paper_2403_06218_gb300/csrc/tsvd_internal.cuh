@@ -1,0 +1,205 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "tsvd.h"
+
+// CUDA-event timing per kernel class (TSVD_FLAG_PROFILE).
+struct tsvd_prof_rec {
+    int cls;
+    cudaEvent_t e0, e1;
+    double flops, bytes;
+};
+
+struct tsvd_handle {
+    int device;
+    int sm_count;
+    int jacobi_coop_blocks;  // co-resident CTAs of the cooperative Jacobi kernel
+    int64_t launches;        // kernels enqueued through this handle (running total)
+    bool profiling = false;
+    std::vector<tsvd_prof_rec> recs;
+    std::vector<cudaEvent_t> pool;
+};
+
+namespace tsvd {
+
+constexpr double kEps = 2.220446049250313e-16;  // 2^-52
+
+// Device status words live at the front of every workspace; kernels set them,
+// the host reads them back after a stream synchronisation.
+enum StatusWord : int {
+    kStBreakdown = 0,    // Cholesky pivot at/below the breakdown threshold
+    kStNonfinite = 1,    // NaN/Inf met
+    kStBadCsr = 2,       // CSR structure invalid
+    kStTimeout = 3,      // a bounded device-side wait gave up
+    kStSweeps = 4,       // Jacobi sweeps used
+    kStCount = 16
+};
+
+#define TSVD_TRY_CUDA(expr)                                   \
+    do {                                                      \
+        cudaError_t tsvd_e_ = (expr);                         \
+        if (tsvd_e_ != cudaSuccess) return TSVD_ERR_CUDA;     \
+    } while (0)
+
+#define TSVD_TRY(expr)                                        \
+    do {                                                      \
+        int tsvd_s_ = (expr);                                 \
+        if (tsvd_s_ < 0) return tsvd_s_;                      \
+    } while (0)
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Brackets the launches of one kernel class with events on the launching stream.
+class ProfScope {
+  public:
+    ProfScope(tsvd_handle* h, int cls, double flops, double bytes, cudaStream_t st)
+        : h_(h && h->profiling ? h : nullptr), st_(st) {
+        if (!h_) return;
+        rec_.cls = cls;
+        rec_.flops = flops;
+        rec_.bytes = bytes;
+        rec_.e0 = get();
+        rec_.e1 = get();
+        cudaEventRecord(rec_.e0, st_);
+    }
+    ~ProfScope() {
+        if (!h_) return;
+        cudaEventRecord(rec_.e1, st_);
+        h_->recs.push_back(rec_);
+    }
+
+  private:
+    cudaEvent_t get() {
+        if (!h_->pool.empty()) {
+            cudaEvent_t e = h_->pool.back();
+            h_->pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    tsvd_handle* h_;
+    cudaStream_t st_;
+    tsvd_prof_rec rec_{};
+};
+
+// Sums the recorded events into info->prof_* (the stream must be synchronised).
+void prof_collect(tsvd_handle* h, tsvd_info* info);
+
+// Bump allocator over caller-owned workspace.  With base == nullptr it only
+// measures (sizing pass); the same carving code runs for both passes.
+struct Arena {
+    char* base = nullptr;
+    size_t cap = 0;
+    size_t off = 0;
+    template <typename T>
+    T* take(size_t count) {
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += align256(count * sizeof(T));
+        return p;
+    }
+    bool fits() const { return base == nullptr || off <= cap; }
+};
+
+inline int check_ws(const void* ws, size_t have, size_t need) {
+    if (need == 0) return TSVD_OK;
+    if (ws == nullptr || have < need) return TSVD_ERR_WORKSPACE;
+    if ((reinterpret_cast<uintptr_t>(ws) & 255u) != 0) return TSVD_ERR_WORKSPACE;
+    return TSVD_OK;
+}
+
+// Reads the status words back (synchronises the stream) and maps them to a code.
+int read_status(cudaStream_t st, const int* d_status, int* h_status /* kStCount */);
+
+// ---- kernel launchers (return cudaError_t of the launch) -------------------
+// All matrices row-major with explicit leading dimensions.
+
+// y = A x, CSR A (m rows), x (w columns, ldx), y (ldy).  Entries whose column
+// is outside [0, n) are skipped and flag kStBadCsr.
+cudaError_t launch_spmm(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr,
+                        const int32_t* col_idx, const double* val, int w, const double* X,
+                        int64_t ldx, double* Y, int64_t ldy, int* status, cudaStream_t st);
+
+size_t csr_transpose_ws(int64_t m, int64_t n, int64_t nnz);
+int csr_transpose(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr,
+                  const int32_t* col_idx, const double* val, int32_t* t_row_ptr,
+                  int32_t* t_col_idx, double* t_val, Arena& ar, int* status, cudaStream_t st);
+
+// C (s x b, ldc) = X^T Z over q rows; X (q x s, ldx), Z (q x b, ldz).
+// symmetric: X == Z and s == b; only the upper half is computed and mirrored.
+size_t gemm_tn_ws(tsvd_handle* h, int64_t q, int64_t s, int64_t b, bool symmetric);
+cudaError_t gemm_tn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, const double* X, int64_t ldx,
+                    const double* Z, int64_t ldz, double* C, int64_t ldc, bool symmetric,
+                    double* partial_ws, cudaStream_t st);
+
+// Y (q x b, ldy) = beta Y + alpha X M; X (q x s, ldx), M (s x b, ldm).
+// upper: M is upper triangular (entries below the diagonal are not read).
+// Y may alias X (in place) when s == b and ldx == ldy.
+cudaError_t gemm_nn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, double alpha, const double* X,
+                    int64_t ldx, const double* M, int64_t ldm, double beta, double* Y, int64_t ldy,
+                    bool upper, cudaStream_t st);
+
+// Cholesky W = L L^T of a b x b SPD matrix (ld b) in one CTA; writes
+// Lt = L^T and Mt = L^{-T} (both upper, ld b).  Sets kStBreakdown on a pivot
+// <= b*eps*max_i W_ii, kStNonfinite on NaN/Inf.
+cudaError_t chol_inv(tsvd_handle* h, int b, const double* W, double* Lt, double* Mt, int* status,
+                     cudaStream_t st);
+
+// out = A U where A, U are b x b upper triangular (ld b); trans writes out^T.
+cudaError_t trmm_upper(tsvd_handle* h, int b, const double* A, const double* U, double* out,
+                       int64_t ldo, bool trans, cudaStream_t st);
+
+cudaError_t gaussian(tsvd_handle* h, int64_t rows, int64_t cols, uint64_t seed, uint32_t stream_id,
+                     double* out, int64_t ld, cudaStream_t st);
+
+// Small SVD by one-sided Jacobi.
+size_t small_svd_ws(int n);
+int small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* Ubar, double* sigma,
+              double* Vbar, Arena& ar, int* status, cudaStream_t st);
+
+// out[j] = sum_i (Y[i,j] - U[i,j] * sigma[j])^2 for j < k  (deterministic).
+size_t colres_ws(int64_t q, int k);
+cudaError_t col_residual_sq(tsvd_handle* h, int64_t q, int k, const double* Y, int64_t ldy,
+                            const double* U, int64_t ldu, const double* sigma, double* out,
+                            double* partial, cudaStream_t st);
+
+// rho[j] = || Rr * Vlast[:, j] ||_2, Rr b x b upper (ld b), Vlast b rows of Vbar (ld ldv), j < k.
+cudaError_t lanczos_rho(tsvd_handle* h, int b, int k, const double* Rr, const double* Vlast,
+                        int64_t ldv, double* rho, cudaStream_t st);
+
+// Flip (u_j, v_j) so that the largest-magnitude entry of v_j (first on ties) is positive.
+size_t sign_fix_ws(int64_t n, int k);
+cudaError_t sign_fix(tsvd_handle* h, int64_t n, int64_t m, int k, double* V, int64_t ldv,
+                     double* U, int64_t ldu, void* ws, cudaStream_t st);
+
+// Strided 2-D copy of a rows x cols block of doubles (device to device).
+inline cudaError_t copy_block(const double* src, int64_t lds, double* dst, int64_t ldd,
+                              int64_t rows, int64_t cols, cudaStream_t st) {
+    if (rows == 0 || cols == 0) return cudaSuccess;
+    return cudaMemcpy2DAsync(dst, ldd * sizeof(double), src, lds * sizeof(double),
+                             cols * sizeof(double), rows, cudaMemcpyDeviceToDevice, st);
+}
+
+// ---- orthogonalisation (orth.cu) -------------------------------------------
+struct OrthCtx {
+    uint64_t seed = 0;
+    int replacements = 0;  // Philox replacement columns drawn (stream 0x100 + t)
+    int fallbacks = 0;     // Cholesky breakdowns sent to the CGS2 fallback
+};
+
+size_t orth_ws(tsvd_handle* h, int64_t q, int64_t s, int b);
+// Y (q x b) <- Q; R (b x b, ld ldr, trans: write R^T); H (s x b, ld b) optional.
+int cgs_cqr2(tsvd_handle* h, int64_t q, int64_t s, int b, const double* P, int64_t ldp,
+             double* Y, int64_t ldy, double* H, double* R, int64_t ldr, bool r_trans,
+             OrthCtx& ctx, Arena ar, int* status, cudaStream_t st);
+int cgs_qr(tsvd_handle* h, int64_t q, int r, int b, double* Y, int64_t ldy, double* R,
+           OrthCtx& ctx, Arena ar, int* status, cudaStream_t st);
+
+}  // namespace tsvd

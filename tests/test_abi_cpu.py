@@ -1,0 +1,74 @@
+"""The C-ABI library builds, loads and exports every entry point include/tsvd.h
+declares; host-side argument validation works without a GPU.  No compute calls."""
+
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "tsvd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\s*\*)\s+(tsvd_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("tsvd_rsvd", "tsvd_blanczos", "tsvd_create", "tsvd_destroy", "tsvd_workspace_size",
+                 "tsvd_spmm", "tsvd_csr_transpose", "tsvd_cholqr2", "tsvd_cgs_cqr2", "tsvd_cgs_qr",
+                 "tsvd_small_svd", "tsvd_gaussian_block", "tsvd_dense_mm"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(tsvd):
+    lib = tsvd.load()
+    for name in _declared():
+        assert hasattr(lib, name), name
+    from paper_2403_06218_gb300 import _capi
+    bound = {n for n, _, _ in _capi.SIGNATURES}
+    assert bound == set(_declared())
+
+
+def test_host_side_validation_without_gpu(tsvd):
+    from paper_2403_06218_gb300 import _capi
+    lib = tsvd.load()
+    opts = _capi.TsvdOpts()
+    lib.tsvd_default_opts(C.byref(opts))
+    assert opts.tol == 1e-6 and opts.max_restarts == 50 and opts.qr_block == 0
+    assert lib.tsvd_status_string(_capi.TSVD_ERR_WORKSPACE).decode().startswith("workspace")
+    d = _capi.TsvdMatrix()
+    d.m, d.n, d.format, d.location, d.ld = 100, 50, _capi.TSVD_DENSE, _capi.TSVD_DEVICE, 50
+    d.val = 1  # never dereferenced by the sizing call
+    nb = C.c_size_t()
+    # k > min(m, n), l > n, b > TSVD_MAX_BLOCK, r*b > n are rejected before any device work
+    assert lib.tsvd_workspace_size(C.byref(d), 0, 60, 0, 1, None, C.byref(nb)) == _capi.TSVD_ERR_INVALID_ARG
+    assert lib.tsvd_workspace_size(C.byref(d), 0, 10, 41, 1, None, C.byref(nb)) == _capi.TSVD_ERR_INVALID_ARG
+    assert lib.tsvd_workspace_size(C.byref(d), 1, 10, 129, 1, None, C.byref(nb)) == _capi.TSVD_ERR_UNSUPPORTED
+    assert lib.tsvd_workspace_size(C.byref(d), 1, 10, 16, 4, None, C.byref(nb)) == _capi.TSVD_ERR_INVALID_ARG
+    assert lib.tsvd_workspace_size(C.byref(d), 1, 10, 8, 4, None, C.byref(nb)) == _capi.TSVD_OK
+    small = nb.value
+    d.m, d.n, d.ld = 1000, 500, 500
+    assert lib.tsvd_workspace_size(C.byref(d), 1, 10, 8, 4, None, C.byref(nb)) == _capi.TSVD_OK
+    assert nb.value > small
+    # bad dtype / format
+    d.dtype = 7
+    assert lib.tsvd_workspace_size(C.byref(d), 1, 10, 8, 4, None, C.byref(nb)) == _capi.TSVD_ERR_UNSUPPORTED
+    d.dtype, d.format = 0, 9
+    assert lib.tsvd_workspace_size(C.byref(d), 1, 10, 8, 4, None, C.byref(nb)) == _capi.TSVD_ERR_INVALID_ARG
+    # a call without a handle is rejected
+    assert lib.tsvd_blanczos(None, C.byref(d), 1, 1, 1, 0, None, None, 0, None, None, None, None) == \
+        _capi.TSVD_ERR_INVALID_ARG
+    assert lib.tsvd_small_svd_workspace(0, C.byref(nb)) == _capi.TSVD_ERR_INVALID_ARG
+    assert lib.tsvd_small_svd_workspace(4096, C.byref(nb)) == _capi.TSVD_ERR_UNSUPPORTED
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    from paper_2403_06218_gb300 import _capi
+    monkeypatch.setattr(_capi, "LIB_PATH", tmp_path / "libtsvd.so")
+    monkeypatch.setattr(_capi, "_lib", None)
+    with pytest.raises(ImportError):
+        _capi.load()

@@ -1,0 +1,341 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Sizes span several tiles and ragged tails; tolerances are stated per test and
+follow from the arithmetic (FP64 sums in a different order: a few ulps times
+the condition of the quantity compared).  All inputs are seeded; the start
+blocks are drawn by the library itself (Philox) and independently by the
+oracle, and compared first.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from helpers import subspace_sin
+from oracle import tsvd_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+EPS = np.finfo(np.float64).eps
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _t(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+# ------------------------------------------------------------------ start block
+@pytest.mark.parametrize("rows,cols,seed,stream", [(1, 1, 0, 1), (333, 17, 5, 2), (1000, 64, 2**40 + 3, 0x101)])
+def test_gaussian_block_matches_oracle(tsvd, torch_cuda, rows, cols, seed, stream):
+    g = _np(tsvd.gaussian_block(rows, cols, seed, stream))
+    o = O.gaussian_block(rows, cols, seed, stream)
+    # identical Philox words; log/sin/cos of two libraries differ by a few ulps
+    np.testing.assert_allclose(g, o, rtol=0, atol=1e-14 * np.maximum(1.0, np.abs(o)).max())
+
+
+# ------------------------------------------------------------------ SpMM and transpose
+@pytest.mark.parametrize("w", [1, 3, 20, 64, 100, 128, 200])
+def test_spmm_matches_oracle(tsvd, torch_cuda, w):
+    torch = torch_cuda
+    A = workloads.csr_uniform(1003, 517, 9, seed=w)
+    A = A.tolil()
+    A[5, :] = 0       # empty rows
+    A[1002, :] = 0
+    A = A.tocsr()
+    X = np.random.default_rng(w).standard_normal((517, w))
+    Ad = tsvd.CsrMatrix.from_scipy(A)
+    Y = _np(tsvd.spmm(Ad, _t(torch, X)))
+    ref = A @ X
+    bound = 2 * 10 * EPS * (abs(A) @ np.abs(X)) + 1e-300
+    assert np.all(np.abs(Y - ref) <= bound)
+    assert np.all(Y[5] == 0) and np.all(Y[1002] == 0)
+
+
+def test_spmm_strided_blocks(tsvd, torch_cuda):
+    torch = torch_cuda
+    A = workloads.csr_uniform(300, 200, 7, seed=3)
+    Xbig = np.random.default_rng(0).standard_normal((200, 40))
+    Xt = _t(torch, Xbig)[:, 5:29]          # ld 40, 24 columns, unaligned start
+    Y = _np(tsvd.spmm(tsvd.CsrMatrix.from_scipy(A), Xt))
+    np.testing.assert_allclose(Y, A @ Xbig[:, 5:29], rtol=1e-13, atol=1e-13)
+
+
+def test_csr_transpose_is_exact(tsvd, torch_cuda):
+    # column degrees span the warp (<=32), CTA (<=4096) and global-memory sort paths
+    rng = np.random.default_rng(7)
+    m, n = 9000, 300
+    rows, cols = [], []
+    for i in range(m):
+        c = rng.choice(n, size=3, replace=False)
+        rows += [i] * 3
+        cols += list(c)
+    rows += list(range(m))          # column 0 gets 9000 entries (global path)
+    cols += [0] * m
+    rows += list(range(0, m, 3))    # column 1 gets >= 3000 entries (CTA path)
+    cols += [1] * len(range(0, m, 3))
+    import scipy.sparse as sp
+    A = sp.coo_matrix((rng.standard_normal(len(rows)), (rows, cols)), shape=(m, n)).tocsr()
+    A.sum_duplicates()
+    T = tsvd.csr_transpose(tsvd.CsrMatrix.from_scipy(A))
+    ref = A.T.tocsr()
+    ref.sort_indices()
+    assert np.array_equal(_np(T.row_ptr), ref.indptr)
+    assert np.array_equal(_np(T.col_idx), ref.indices)
+    assert np.array_equal(_np(T.val), ref.data)
+
+
+def test_csr_invalid_column_is_rejected(tsvd, torch_cuda):
+    torch = torch_cuda
+    A = workloads.csr_uniform(50, 40, 4, seed=1)
+    Ad = tsvd.CsrMatrix.from_scipy(A)
+    Ad.col_idx[7] = 40               # out of range: skipped by the kernel and reported
+    with pytest.raises(tsvd.TsvdError):
+        tsvd.csr_transpose(Ad)
+    with pytest.raises(tsvd.TsvdError):
+        tsvd.spmm(Ad, torch.ones((40, 3), dtype=torch.float64, device="cuda"))
+
+
+# ------------------------------------------------------------------ dense products
+@pytest.mark.parametrize("m,n,w", [(512, 256, 20), (777, 333, 64), (100, 1000, 128), (64, 64, 1)])
+def test_dense_mm_matches_numpy(tsvd, torch_cuda, m, n, w):
+    torch = torch_cuda
+    rng = np.random.default_rng(m)
+    A = rng.standard_normal((m, n))
+    X1 = rng.standard_normal((n, w))
+    X2 = rng.standard_normal((m, w))
+    Y1 = _np(tsvd.dense_mm(_t(torch, A), _t(torch, X1), trans=False))
+    Y2 = _np(tsvd.dense_mm(_t(torch, A), _t(torch, X2), trans=True))
+    assert np.all(np.abs(Y1 - A @ X1) <= 2 * n * EPS * (np.abs(A) @ np.abs(X1)))
+    assert np.all(np.abs(Y2 - A.T @ X2) <= 2 * m * EPS * (np.abs(A.T) @ np.abs(X2)))
+
+
+# ------------------------------------------------------------------ orthogonalisation
+def _cond_block(rng, q, b, cond):
+    U, _ = np.linalg.qr(rng.standard_normal((q, b)))
+    V, _ = np.linalg.qr(rng.standard_normal((b, b)))
+    return (U * np.logspace(0, -np.log10(cond), b)) @ V.T
+
+
+@pytest.mark.parametrize("q,b,cond", [(100, 1, 1.0), (1000, 16, 1e3), (4099, 64, 1e6), (20000, 128, 10.0)])
+def test_cholqr2_matches_oracle(tsvd, torch_cuda, q, b, cond):
+    torch = torch_cuda
+    Y = _cond_block(np.random.default_rng(q), q, b, cond)
+    Q, R, bd = tsvd.cholqr2(_t(torch, Y))
+    Qo, Ro = oracle.cholqr2(Y)
+    assert bd == 0
+    Q, R = _np(Q), _np(R)
+    np.testing.assert_allclose(R, Ro, rtol=0, atol=1e-12 * cond * np.abs(Ro).max())
+    np.testing.assert_allclose(Q, Qo, rtol=0, atol=1e-12 * cond)
+    assert np.abs(Q.T @ Q - np.eye(b)).max() < 1e-13
+
+
+@pytest.mark.parametrize("q,s,b", [(1000, 16, 16), (5003, 320, 64), (3000, 7, 5)])
+def test_cgs_cqr2_matches_oracle(tsvd, torch_cuda, q, s, b):
+    torch = torch_cuda
+    rng = np.random.default_rng(s)
+    P, _ = np.linalg.qr(rng.standard_normal((q, s)))
+    Y = rng.standard_normal((q, b)) + P @ rng.standard_normal((s, b)) * 5
+    Q, H, R, bd = tsvd.cgs_cqr2(_t(torch, Y), _t(torch, P))
+    Qo, Ho, Ro = oracle.cgs_cqr2(Y, P)
+    assert bd == 0
+    np.testing.assert_allclose(_np(R), Ro, rtol=0, atol=1e-12 * np.abs(Ro).max())
+    np.testing.assert_allclose(_np(H), Ho, rtol=0, atol=1e-12 * np.abs(Ho).max())
+    np.testing.assert_allclose(_np(Q), Qo, rtol=0, atol=1e-12)
+    assert np.abs(P.T @ _np(Q)).max() < 1e-13
+
+
+@pytest.mark.parametrize("r,b", [(20, 20), (24, 5), (128, 128), (200, 64)])
+def test_cgs_qr_matches_oracle(tsvd, torch_cuda, r, b):
+    torch = torch_cuda
+    Y = _cond_block(np.random.default_rng(r), 3000, r, 1e4)
+    Q, R, bd = tsvd.cgs_qr(_t(torch, Y), b)
+    Qo, Ro = oracle.cgs_qr(Y, b)
+    np.testing.assert_allclose(_np(R), Ro, rtol=0, atol=1e-11 * np.abs(Ro).max())
+    np.testing.assert_allclose(_np(Q), Qo, rtol=0, atol=1e-9)
+
+
+def test_cholqr2_breakdown_fallback_matches_oracle(tsvd, torch_cuda):
+    torch = torch_cuda
+    rng = np.random.default_rng(2)
+    Y = rng.standard_normal((200, 6))
+    Y[:, 3] = Y[:, 0] + 2.0 * Y[:, 1]
+    Y[:, 5] = 0.0
+    Q, R, bd = tsvd.cholqr2(_t(torch, Y), seed=5)
+    ctx = O._Ctx(seed=5)
+    Qo, Ro = oracle.cholqr2(Y, ctx)
+    assert bd == 1 and ctx.fallbacks == 1
+    Q, R = _np(Q), _np(R)
+    assert np.abs(Q.T @ Q - np.eye(6)).max() < 1e-13
+    assert np.abs(Q @ R - Y).max() < 1e-12
+    # the dependent directions are the same Philox replacements on both sides
+    np.testing.assert_allclose(Q, Qo, atol=1e-10)
+    np.testing.assert_allclose(R, Ro, atol=1e-10)
+
+
+# ------------------------------------------------------------------ small SVD
+@pytest.mark.parametrize("n", [1, 2, 3, 20, 63, 64, 65, 200, 512])
+def test_small_svd_matches_oracle(tsvd, torch_cuda, n):
+    torch = torch_cuda
+    rng = np.random.default_rng(n)
+    B = rng.standard_normal((n, n))
+    if n >= 20:
+        B = np.tril(B)  # the projected matrices of both methods are triangular/banded
+    U, s, V, sweeps = tsvd.small_svd(_t(torch, B))
+    Uo, so, Vo = oracle.small_svd(B)
+    U, s, V = _np(U), _np(s), _np(V)
+    assert 1 <= sweeps < 40
+    np.testing.assert_allclose(s, so, rtol=1e-12, atol=1e-13 * so[0])
+    assert np.abs((U * s) @ V.T - B).max() < 1e-12 * so[0]
+    assert np.abs(V.T @ V - np.eye(n)).max() < 1e-12
+    # singular vectors of well separated values agree element by element (same sign convention)
+    gap = np.ones(n)
+    if n > 1:
+        d = np.abs(np.diff(so)) / so[0]
+        gap = np.minimum(np.r_[d, np.inf], np.r_[np.inf, d])
+    ok = gap > 1e-6
+    np.testing.assert_allclose(V[:, ok], Vo[:, ok], atol=1e-9)
+    ok &= so > 1e-8 * so[0]
+    np.testing.assert_allclose(U[:, ok], Uo[:, ok], atol=1e-9)
+
+
+# ------------------------------------------------------------------ drivers
+def _cfg1():
+    return workloads.dense_known_spectrum(512, 256, seed=0)
+
+
+def test_rsvd_cfg1_matches_oracle(tsvd, torch_cuda):
+    torch = torch_cuda
+    A, s_true, U0, V0 = _cfg1()
+    res = tsvd.rsvd(_t(torch, A), 10, 10, 2, seed=0)
+    so, Uo, Vo, info = oracle.rsvd(A, 10, 10, 2, seed=0)
+    s, U, V = _np(res.sigma), _np(res.U), _np(res.V)
+    np.testing.assert_allclose(s, so, rtol=1e-10)
+    assert subspace_sin(U, Uo) < 1e-8 and subspace_sin(V, Vo) < 1e-8
+    np.testing.assert_allclose(U, Uo, atol=1e-8)
+    np.testing.assert_allclose(V, Vo, atol=1e-8)
+    assert abs(res.info["resid_max"] - info.resid_max) < 1e-8 * info.resid_max
+
+
+def test_blanczos_cfg1_matches_oracle(tsvd, torch_cuda):
+    torch = torch_cuda
+    A, s_true, U0, V0 = _cfg1()
+    res = tsvd.blanczos(_t(torch, A), 10, 16, 4, seed=0, tol=1e-6, max_restarts=50)
+    so, Uo, Vo, info = oracle.blanczos(A, 10, 16, 4, seed=0, tol=1e-6, max_restarts=50)
+    assert res.status == 0 and res.info["converged"] == 1
+    assert res.info["restarts"] == info.restarts
+    s, U, V = _np(res.sigma), _np(res.U), _np(res.V)
+    np.testing.assert_allclose(s, so, rtol=1e-10)
+    assert subspace_sin(U, Uo) < 1e-8 and subspace_sin(V, Vo) < 1e-8
+    np.testing.assert_allclose(V, Vo, atol=1e-8)
+    assert res.info["resid_max"] <= 1e-6
+
+
+def test_blanczos_sparse_rectangular_and_transposed(tsvd, torch_cuda):
+    """Fixed cycle count: GPU and oracle follow the same trajectory (sigma 1e-10,
+    subspaces 1e-8).  Converged runs: basic restart amplifies rounding-level
+    differences by about 10x per cycle once the restart block's boundary gap
+    dominates (perturbing the oracle's own start block by 1e-15 moves its
+    converged subspace by ~1e-7 here), so there the subspaces are checked against
+    the dense SVD within tol / relative gap, and sigma against the oracle."""
+    for (m, n) in ((3001, 1200), (700, 2500)):
+        A = workloads.csr_uniform(m, n, 11, seed=m)
+        Ad = tsvd.CsrMatrix.from_scipy(A)
+        res = tsvd.blanczos(Ad, 8, 8, 5, seed=3, tol=0.0, max_restarts=2)
+        so, Uo, Vo, info = oracle.blanczos(A, 8, 8, 5, seed=3, tol=0.0, max_restarts=2)
+        assert res.info["transposed"] == int(m < n) == int(info.transposed)
+        assert res.info["iterations"] == 3 == info.iterations
+        s, U, V = _np(res.sigma), _np(res.U), _np(res.V)
+        assert U.shape == (m, 8) and V.shape == (n, 8)
+        np.testing.assert_allclose(s, so, rtol=1e-10)
+        assert subspace_sin(U, Uo) < 1e-8 and subspace_sin(V, Vo) < 1e-8
+        np.testing.assert_allclose(V, Vo, atol=1e-8)
+        # converged to 1e-8
+        tol = 1e-8
+        res = tsvd.blanczos(Ad, 8, 8, 5, seed=3, tol=tol, max_restarts=400)
+        so, Uo, Vo, info = oracle.blanczos(A, 8, 8, 5, seed=3, tol=tol, max_restarts=400)
+        assert res.status == 0 and info.converged
+        assert abs(res.info["restarts"] - info.restarts) <= 1
+        s, U, V = _np(res.sigma), _np(res.U), _np(res.V)
+        np.testing.assert_allclose(s, so, rtol=1e-10)
+        assert np.linalg.norm(A @ V - U * s, axis=0).max() <= tol * s[0] * 1.0001
+        Ut, st_, Vt = np.linalg.svd(A.toarray(), full_matrices=False)
+        relgap = (st_[7] - st_[8]) / st_[0]
+        np.testing.assert_allclose(s, st_[:8], rtol=10 * tol)
+        assert subspace_sin(V, Vt[:8].T) < 10 * tol / relgap
+        assert subspace_sin(U, Ut[:, :8]) < 10 * tol / relgap
+
+
+def test_rsvd_sparse_blocked_qr_matches_oracle(tsvd, torch_cuda):
+    A = workloads.csr_uniform(4000, 2500, 8, seed=5)
+    res = tsvd.rsvd(tsvd.CsrMatrix.from_scipy(A), 12, 28, 3, seed=9, qr_block=16)
+    so, Uo, Vo, info = oracle.rsvd(A, 12, 28, 3, seed=9, qr_block=16)
+    s, U, V = _np(res.sigma), _np(res.U), _np(res.V)
+    np.testing.assert_allclose(s, so, rtol=1e-10)
+    assert subspace_sin(U, Uo) < 1e-8 and subspace_sin(V, Vo) < 1e-8
+
+
+def test_host_buffers_and_determinism(tsvd, torch_cuda):
+    A = workloads.csr_uniform(2000, 1500, 9, seed=21)
+    dev = tsvd.blanczos(tsvd.CsrMatrix.from_scipy(A), 6, 6, 4, seed=1, tol=1e-7)
+    host = tsvd.blanczos(A, 6, 6, 4, seed=1, tol=1e-7, output="host")
+    again = tsvd.blanczos(tsvd.CsrMatrix.from_scipy(A), 6, 6, 4, seed=1, tol=1e-7)
+    assert isinstance(host.U, np.ndarray)
+    np.testing.assert_array_equal(_np(dev.sigma), host.sigma)
+    np.testing.assert_array_equal(_np(dev.U), host.U)
+    np.testing.assert_array_equal(_np(dev.V), _np(again.V))
+
+
+def test_rank_deficient_matches_oracle(tsvd, torch_cuda):
+    torch = torch_cuda
+    rng = np.random.default_rng(6)
+    A = rng.standard_normal((60, 3)) @ rng.standard_normal((3, 40))
+    res = tsvd.blanczos(_t(torch, A), 3, 2, 4, seed=2, tol=1e-10, max_restarts=5)
+    so, Uo, Vo, info = oracle.blanczos(A, 3, 2, 4, seed=2, tol=1e-10, max_restarts=5)
+    np.testing.assert_allclose(_np(res.sigma), so, rtol=1e-10)
+    assert res.info["breakdowns"] >= 1 and info.breakdowns >= 1
+
+
+def test_start_block_argument(tsvd, torch_cuda):
+    torch = torch_cuda
+    A, _, _, _ = _cfg1()
+    Om = np.random.default_rng(3).standard_normal((512, 16))
+    res = tsvd.blanczos(_t(torch, A), 10, 16, 4, tol=1e-8, start_block=_t(torch, Om))
+    so, Uo, Vo, info = oracle.blanczos(A, 10, 16, 4, tol=1e-8, start_block=Om)
+    np.testing.assert_allclose(_np(res.sigma), so, rtol=1e-10)
+    assert subspace_sin(_np(res.V), Vo) < 1e-8
+
+
+def test_invalid_arguments_raise(tsvd, torch_cuda):
+    torch = torch_cuda
+    A = torch.zeros((30, 20), dtype=torch.float64, device="cuda")
+    with pytest.raises(tsvd.TsvdError):
+        tsvd.blanczos(A, 5, 4, 6)        # r*b = 24 > min(m, n)
+    with pytest.raises(tsvd.TsvdError):
+        tsvd.rsvd(A, 15, 10, 1)          # k + p > n
+
+
+# ------------------------------------------------------------------ full-size bench configuration
+def test_blanczos_full_size_sparse_two_cycles(tsvd, torch_cuda):
+    """100,000 x 100,000 CSR, 10 nnz/row, k = b = 64, r = 8 (the benchmark's launch
+    configuration), two restart cycles on both sides from the same start block."""
+    A = workloads.csr_uniform(100_000, 100_000, 10, seed=1)
+    res = tsvd.blanczos(tsvd.CsrMatrix.from_scipy(A), 64, 64, 8, seed=1, tol=0.0, max_restarts=1)
+    so, Uo, Vo, info = oracle.blanczos(A, 64, 64, 8, seed=1, tol=0.0, max_restarts=1)
+    assert res.info["iterations"] == 2 == info.iterations
+    s, U, V = _np(res.sigma), _np(res.U), _np(res.V)
+    np.testing.assert_allclose(s, so, rtol=1e-10)
+    # individual Ritz vectors are not resolved after two cycles (gaps ~1e-4); compare the subspace
+    assert subspace_sin(V, Vo) < 1e-8 and subspace_sin(U, Uo) < 1e-8
+    assert abs(res.info["resid_max"] - info.resid_max) < 1e-6 * info.resid_max
