@@ -30,6 +30,10 @@ WORKLOADS = {
     # name: (matrix, method, params)
     "sparse100k-lanczos": dict(kind="csr", m=100_000, n=100_000, d=10, seed=1, method="blanczos",
                                k=64, b=64, r=16, tol=1e-6, max_restarts=50, oracle_cycles=9),
+    # the same solve in the mixed-precision form (FP32 products, FP64 small algebra and final step)
+    "sparse100k-lanczos-mixed": dict(kind="csr", m=100_000, n=100_000, d=10, seed=1, method="blanczos",
+                                     k=64, b=64, r=16, tol=1e-6, max_restarts=50, oracle_cycles=9,
+                                     precision="mixed"),
     "sparse100k-rsvd": dict(kind="csr", m=100_000, n=100_000, d=10, seed=1, method="rsvd",
                             k=64, p=64, q=3),
     "dense512-lanczos": dict(kind="dense", m=512, n=256, seed=0, method="blanczos",
@@ -59,10 +63,11 @@ def _make_matrix(cfg, rank):
 
 
 def _solve(tsvd, cfg, A, seed, profile=False, output="device"):
+    prec = cfg.get("precision", "fp64")
     if cfg["method"] == "blanczos":
         return tsvd.blanczos(A, cfg["k"], cfg["b"], cfg["r"], seed=seed, tol=cfg["tol"],
-                             max_restarts=cfg["max_restarts"], profile=profile, output=output)
-    return tsvd.rsvd(A, cfg["k"], cfg["p"], cfg["q"], seed=seed, profile=profile, output=output)
+                             max_restarts=cfg["max_restarts"], profile=profile, output=output, precision=prec)
+    return tsvd.rsvd(A, cfg["k"], cfg["p"], cfg["q"], seed=seed, profile=profile, output=output, precision=prec)
 
 
 def _oracle_solve(cfg, A, seed, cycles=None):
@@ -182,6 +187,28 @@ def run_reference(args, cfg):
     return 0
 
 
+def run_case(case):
+    """One building block at the largest shape of the benchmark solve (inputs > L2)."""
+    import torch
+    import paper_2403_06218_gb300 as tsvd
+    g = torch.Generator(device="cuda").manual_seed(0)
+    if case == "orth":
+        # n-side CGS-CQR2 of the last Lanczos step: q = 100,000, s = 15 * 64, b = 64
+        P = tsvd.cgs_qr(torch.randn(100_000, 960, dtype=torch.float64, device="cuda", generator=g), 128)[0]
+        Y = torch.randn(100_000, 64, dtype=torch.float64, device="cuda", generator=g)
+        for _ in range(2):
+            Q, H, R, bd = tsvd.cgs_cqr2(Y, P)
+    else:
+        # projected matrix of one restart cycle: 1024 x 1024 lower block bidiagonal
+        B = torch.tril(torch.randn(1024, 1024, dtype=torch.float64, device="cuda", generator=g))
+        B = B - torch.tril(B, -65)
+        for _ in range(2):
+            tsvd.small_svd(B)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": case, "ok": True}))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -190,8 +217,12 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--workload", default="sparse100k-lanczos", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default=None, choices=("orth", "svd"),
+                    help="run one building block at its benchmark shape (for profiler captures) and exit")
     args = ap.parse_args(argv)
     cfg = WORKLOADS[args.workload]
+    if args.case:
+        return run_case(args.case)
     if args.impl == "reference":
         return run_reference(args, cfg)
 
@@ -226,8 +257,8 @@ def main(argv=None):
     seed = cfg["seed"] + rank
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
-    for _ in range(args.warmup):
-        res = _solve(tsvd, cfg, A_dev, seed)
+    for _ in range(args.warmup):  # profiled too, so the timed steps reuse the library's pooled CUDA events
+        res = _solve(tsvd, cfg, A_dev, seed, profile=True)
     torch.cuda.synchronize()
 
     # ---- timed region: K solves, A resident in HBM ----
@@ -293,7 +324,7 @@ def main(argv=None):
     line = {
         "metric": METRIC, "value": ms_step / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32+f64" if cfg.get("precision") == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": args.workload, **{k: v for k, v in cfg.items() if k != "oracle_cycles"},
                    "parallelism": f"replicas{world}", "l2": "flushed before every step (256 MiB write)"},
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -51,12 +51,19 @@ extern "C" {
 /* ---- enumerations ------------------------------------------------------ */
 #define TSVD_DENSE   0   /* tsvd_matrix.format: row-major dense                    */
 #define TSVD_CSR     1   /* tsvd_matrix.format: compressed sparse row              */
-#define TSVD_F64     0   /* tsvd_matrix.dtype                                      */
+#define TSVD_F64     0   /* tsvd_matrix.dtype: FP64 values                         */
+#define TSVD_F32     1   /* tsvd_matrix.dtype: FP32 values (widened exactly where FP64 is needed) */
 #define TSVD_DEVICE  0   /* memory location of a buffer                            */
 #define TSVD_HOST    1
 
 #define TSVD_METHOD_RSVD      0
 #define TSVD_METHOD_BLANCZOS  1
+
+/* tsvd_opts.precision */
+#define TSVD_PREC_FP64   0   /* every step in FP64 (the paper's method)                      */
+#define TSVD_PREC_MIXED  1   /* FP32 A, blocks, bases and products; FP64 Gram reductions,
+                                Cholesky, R, B, small SVD, and a final FP64 Rayleigh-Ritz
+                                step on the Ritz vectors with the FP64 A (k <= TSVD_MAX_BLOCK) */
 
 /* Largest block width of one Cholesky factorisation (CholeskyQR2 / CGS-CQR2);
  * CGS-QR splits wider blocks (Alg. 3).  Largest small-SVD order. */
@@ -102,6 +109,8 @@ typedef struct tsvd_opts {
                                   RandSVD n' x (k+p), LancSVD m' x b, row-major, ld = cols,
                                   where m' >= n' are the dimensions after the m<n transpose */
     void* stream;            /* cudaStream_t */
+    int32_t precision;       /* TSVD_PREC_FP64 (default) or TSVD_PREC_MIXED */
+    int32_t reserved;
 } tsvd_opts;
 
 /* Per-call report.  Phase times are CUDA-event milliseconds on `stream`. */

@@ -25,7 +25,9 @@ point of use (labels G1..G23, listed with reasons in the design notes):
       every output right vector has its largest-magnitude entry positive.
 * G21 LancSVD convergence: rho_j = ||R_r vbar_j[last b rows]||_2 <= tol*sigma_1
       for all j < k, confirmed by the explicit residual.
-* G1  residual: ||A v_j - sigma_j u_j||_2 / sigma_1 (and / sigma_j).
+* G1  residual: max over j of the two one-sided residuals ||A v_j - sigma_j u_j||_2
+      and ||A^T u_j - sigma_j v_j||_2, divided by sigma_1 (the second is ~0 by
+      construction for both methods, so this equals the first in exact arithmetic).
 """
 
 from __future__ import annotations
@@ -326,6 +328,15 @@ class OracleInfo:
     transposed: bool = False
 
 
+def _resid_max(op, sigma, U, V):
+    """max_j of both one-sided residuals over sigma_1 (reading G1), in the m >= n orientation."""
+    if not sigma[0] > 0:
+        return float("nan")
+    av = np.linalg.norm(op.mul(V) - U * sigma, axis=0)
+    atu = np.linalg.norm(op.tmul(U) - V * sigma, axis=0)
+    return float(max(np.max(av), np.max(atu)) / sigma[0])
+
+
 def residuals(A, sigma, U, V):
     """Per-triplet residual norms for the metric of Sec. 4 (reading G1).
 
@@ -368,8 +379,7 @@ def rsvd(A, k: int, p: int, q: int, seed: int = 0, qr_block: int = 0,
     sigma = s[:k].copy()
     U, V = _output_signs(U, V)
     info.breakdowns = ctx.fallbacks
-    av = np.linalg.norm(op.mul(V) - U * sigma, axis=0)
-    info.resid_max = float(np.max(av) / sigma[0]) if sigma[0] > 0 else float("nan")
+    info.resid_max = _resid_max(op, sigma, U, V)
     if op.t:
         U, V = V, U
     return sigma, U, V, info
@@ -428,8 +438,7 @@ def blanczos(A, k: int, b: int, r: int, seed: int = 0, tol: float = 1e-6,
             U = Pbar @ Ub[:, :k]                                  # S9
             V = P @ Vb[:, :k]                                     # S8 (reading G2)
             sigma = s[:k].copy()
-            av = np.linalg.norm(op.mul(V) - U * sigma, axis=0)
-            info.resid_max = float(np.max(av) / sigma[0]) if sigma[0] > 0 else float("nan")
+            info.resid_max = _resid_max(op, sigma, U, V)
             if (done and info.resid_max <= tol) or info.restarts >= max_restarts:
                 info.converged = bool(info.resid_max <= tol)
                 break

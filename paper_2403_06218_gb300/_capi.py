@@ -20,6 +20,9 @@ TSVD_ERR_UNSUPPORTED = -6
 TSVD_DENSE = 0
 TSVD_CSR = 1
 TSVD_F64 = 0
+TSVD_F32 = 1
+TSVD_PREC_FP64 = 0
+TSVD_PREC_MIXED = 1
 TSVD_DEVICE = 0
 TSVD_HOST = 1
 TSVD_METHOD_RSVD = 0
@@ -45,6 +48,7 @@ class TsvdOpts(C.Structure):
         ("tol", C.c_double), ("max_restarts", C.c_int32), ("qr_block", C.c_int32),
         ("output_location", C.c_int32), ("flags", C.c_int32),
         ("start_block", C.c_void_p), ("stream", C.c_void_p),
+        ("precision", C.c_int32), ("reserved", C.c_int32),
     ]
 
 

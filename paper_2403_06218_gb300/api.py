@@ -71,11 +71,13 @@ class CsrMatrix:
 
     @staticmethod
     def from_scipy(A, device="cuda", pin_memory: bool = False) -> "CsrMatrix":
+        """Copies a scipy CSR matrix (float64 or float32 values are kept as they are)."""
         import scipy.sparse as sp
         A = sp.csr_matrix(A)
         rp = torch.from_numpy(np.ascontiguousarray(A.indptr, dtype=np.int32))
         ci = torch.from_numpy(np.ascontiguousarray(A.indices, dtype=np.int32))
-        va = torch.from_numpy(np.ascontiguousarray(A.data, dtype=np.float64))
+        vdt = np.float32 if A.data.dtype == np.float32 else np.float64
+        va = torch.from_numpy(np.ascontiguousarray(A.data, dtype=vdt))
         if str(device) == "cpu":
             if pin_memory:
                 rp, ci, va = rp.pin_memory(), ci.pin_memory(), va.pin_memory()
@@ -104,38 +106,45 @@ def _desc(A):
                       A.values().to(torch.float64), tuple(A.shape))
     if sp.issparse(A):
         A = sp.csr_matrix(A)
+        f32 = A.data.dtype == np.float32
         rp = np.ascontiguousarray(A.indptr, dtype=np.int32)
         ci = np.ascontiguousarray(A.indices, dtype=np.int32)
-        va = np.ascontiguousarray(A.data, dtype=np.float64)
+        va = np.ascontiguousarray(A.data, dtype=np.float32 if f32 else np.float64)
         keep += [rp, ci, va]
         d.m, d.n = A.shape
         d.format, d.location = capi.TSVD_CSR, capi.TSVD_HOST
+        d.dtype = capi.TSVD_F32 if f32 else capi.TSVD_F64
         d.val, d.row_ptr, d.col_idx, d.nnz = va.ctypes.data, rp.ctypes.data, ci.ctypes.data, ci.size
         return d, keep, None
     if isinstance(A, CsrMatrix):
-        for t, dt in ((A.row_ptr, torch.int32), (A.col_idx, torch.int32), (A.val, torch.float64)):
+        for t, dt in ((A.row_ptr, torch.int32), (A.col_idx, torch.int32)):
             if t.dtype != dt or not t.is_contiguous():
-                raise TypeError("CsrMatrix needs contiguous int32 indices and float64 values")
+                raise TypeError("CsrMatrix needs contiguous int32 indices")
+        if A.val.dtype not in (torch.float64, torch.float32) or not A.val.is_contiguous():
+            raise TypeError("CsrMatrix needs contiguous float64 or float32 values")
         keep += [A.row_ptr, A.col_idx, A.val]
         d.m, d.n = A.shape
         d.format = capi.TSVD_CSR
+        d.dtype = capi.TSVD_F32 if A.val.dtype == torch.float32 else capi.TSVD_F64
         dev = A.val.device
         d.location = capi.TSVD_DEVICE if dev.type == "cuda" else capi.TSVD_HOST
         d.val, d.row_ptr, d.col_idx, d.nnz = A.val.data_ptr(), A.row_ptr.data_ptr(), A.col_idx.data_ptr(), A.nnz
         return d, keep, (dev if dev.type == "cuda" else None)
     if isinstance(A, np.ndarray):
-        A = np.ascontiguousarray(A, dtype=np.float64)
+        A = np.ascontiguousarray(A, dtype=np.float32 if A.dtype == np.float32 else np.float64)
         keep.append(A)
         d.m, d.n = A.shape
         d.format, d.location = capi.TSVD_DENSE, capi.TSVD_HOST
+        d.dtype = capi.TSVD_F32 if A.dtype == np.float32 else capi.TSVD_F64
         d.val, d.ld = A.ctypes.data, A.shape[1]
         return d, keep, None
     if isinstance(A, torch.Tensor):
-        if A.dtype != torch.float64 or A.dim() != 2 or A.stride(1) != 1:
-            raise TypeError("dense A must be a 2-D float64 tensor with unit column stride")
+        if A.dtype not in (torch.float64, torch.float32) or A.dim() != 2 or A.stride(1) != 1:
+            raise TypeError("dense A must be a 2-D float64/float32 tensor with unit column stride")
         keep.append(A)
         d.m, d.n = A.shape
         d.format = capi.TSVD_DENSE
+        d.dtype = capi.TSVD_F32 if A.dtype == torch.float32 else capi.TSVD_F64
         d.location = capi.TSVD_DEVICE if A.is_cuda else capi.TSVD_HOST
         d.val, d.ld = A.data_ptr(), A.stride(0)
         return d, keep, (A.device if A.is_cuda else None)
@@ -155,8 +164,11 @@ class SvdResult:
     status: int
 
 
+_PRECISIONS = {"fp64": capi.TSVD_PREC_FP64, "mixed": capi.TSVD_PREC_MIXED}
+
+
 def _run_driver(fn_name, method, A, k, a, c, seed, tol, max_restarts, qr_block, start_block, output, device,
-                profile=False):
+                profile=False, precision="fp64"):
     lib = capi.load()
     desc, keep, dev = _desc(A)
     if dev is None:
@@ -168,6 +180,9 @@ def _run_driver(fn_name, method, A, k, a, c, seed, tol, max_restarts, qr_block, 
     opts.qr_block = int(qr_block)
     opts.output_location = capi.TSVD_HOST if output == "host" else capi.TSVD_DEVICE
     opts.flags = capi.TSVD_FLAG_PROFILE if profile else 0
+    if precision not in _PRECISIONS:
+        raise ValueError(f"precision must be one of {sorted(_PRECISIONS)}")
+    opts.precision = _PRECISIONS[precision]
     if start_block is not None:
         if not (isinstance(start_block, torch.Tensor) and start_block.is_cuda and start_block.dtype == torch.float64
                 and start_block.is_contiguous()):
@@ -199,18 +214,20 @@ def _run_driver(fn_name, method, A, k, a, c, seed, tol, max_restarts, qr_block, 
 
 def blanczos(A, k: int, b: int, r: int, seed: int = 0, tol: float = 1e-6, max_restarts: int = 50,
              start_block: Optional[torch.Tensor] = None, output: str = "device", device=None,
-             profile: bool = False) -> SvdResult:
+             profile: bool = False, precision: str = "fp64") -> SvdResult:
     """LancSVD (Alg. 2): k triplets with blocks of width b, r blocks per restart cycle.
-    ``profile`` times every kernel class with CUDA events (``info['prof_*']``)."""
+    ``profile`` times every kernel class with CUDA events (``info['prof_*']``);
+    ``precision="mixed"`` selects the FP32-product form with FP64 small algebra
+    and a final FP64 Rayleigh-Ritz step."""
     return _run_driver("tsvd_blanczos", capi.TSVD_METHOD_BLANCZOS, A, k, b, r, seed, tol, max_restarts, 0,
-                       start_block, output, device, profile)
+                       start_block, output, device, profile, precision)
 
 
 def rsvd(A, k: int, p: int, q: int, seed: int = 0, qr_block: int = 0, start_block: Optional[torch.Tensor] = None,
-         output: str = "device", device=None, profile: bool = False) -> SvdResult:
+         output: str = "device", device=None, profile: bool = False, precision: str = "fp64") -> SvdResult:
     """RandSVD (Alg. 1): k triplets, oversampling p, q power steps (q + 1 trips)."""
     return _run_driver("tsvd_rsvd", capi.TSVD_METHOD_RSVD, A, k, p, q, seed, 0.0, 0, qr_block, start_block, output,
-                       device, profile)
+                       device, profile, precision)
 
 
 # ---------------------------------------------------------------------------

@@ -1,0 +1,648 @@
+// RandSVD (Alg. 1) and LancSVD (Alg. 2) on the device, for both precisions:
+//   T = double: the FP64 method of the paper;
+//   T = float : the mixed-precision form.  A and every tall block (Q, Qbar, the
+//               Lanczos bases) are FP32 and the products accumulate in FP32,
+//               while every Gram matrix, Cholesky factor, R, B and the small SVD
+//               stay FP64.  The returned triplets come from an FP64 Rayleigh-Ritz
+//               step: the Ritz vectors are re-orthonormalised in FP64, the k x k
+//               projection U^T A V is formed with the FP64 A and its SVD rotates
+//               them; the residual test uses the FP64 A.
+//
+// The host only sequences kernels and reads back a few status words (Cholesky
+// breakdown flags after each orthogonalisation, the Lanczos estimate once per
+// cycle, the explicit residual).  When m < n both methods run on A^T and swap U
+// and V on return (Sec. 2).
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "tsvd_internal.cuh"
+
+namespace tsvd {
+namespace {
+
+template <typename TI, typename TO>
+__global__ void convert2d_kernel(int64_t rows, int64_t cols, const TI* __restrict__ x, int64_t ldx,
+                                 TO* __restrict__ y, int64_t ldy) {
+    const int64_t tot = rows * cols;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / cols, c = i % cols;
+        y[r * ldy + c] = (TO)x[r * ldx + c];
+    }
+}
+
+template <typename TI, typename TO>
+cudaError_t convert2d(tsvd_handle* h, int64_t rows, int64_t cols, const TI* x, int64_t ldx, TO* y, int64_t ldy,
+                      cudaStream_t st) {
+    const int64_t tot = rows * cols;
+    if (tot == 0) return cudaSuccess;
+    int64_t blocks = (tot + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    ProfScope prof(h, TSVD_K_OTHER, 0.0, (double)(sizeof(TI) + sizeof(TO)) * tot, st);
+    h->launches++;
+    convert2d_kernel<TI, TO><<<(unsigned)blocks, 256, 0, st>>>(rows, cols, x, ldx, y, ldy);
+    return cudaGetLastError();
+}
+
+// op(A) as the methods see it (m >= n after the optional transpose), with the
+// values in the working precision T and in FP64 (the same arrays when T = double).
+template <typename T>
+struct Op {
+    bool sparse = false, transposed = false;
+    int64_t m = 0, n = 0;  // op(A)
+    int64_t M = 0, N = 0;  // A
+    int64_t nnz = 0;
+    const int32_t *rp = nullptr, *ci = nullptr;  // CSR(A)
+    int32_t *trp = nullptr, *tci = nullptr;      // CSR(A^T)
+    const T* va = nullptr;
+    const T* tva = nullptr;
+    const double* va64 = nullptr;
+    const double* tva64 = nullptr;
+    const T* dA = nullptr;  // dense A (row-major)
+    int64_t lda = 0;
+    const double* dA64 = nullptr;
+    int64_t lda64 = 0;
+    double* partial = nullptr;  // split-K scratch of dense A^T X
+};
+
+// Y (op.m x w) = op(A) X ; in precision TV with values V (sparse) or D (dense).
+template <typename TV>
+int apply(tsvd_handle* h, bool sparse, bool trans_of_A, int64_t M, int64_t N, int64_t nnz, const int32_t* rp,
+          const int32_t* ci, const TV* va, const int32_t* trp, const int32_t* tci, const TV* tva, const TV* dA,
+          int64_t lda, double* partial, int w, const TV* X, int64_t ldx, TV* Y, int64_t ldy, int* status,
+          cudaStream_t st) {
+    if (sparse) {
+        if (!trans_of_A)
+            TSVD_TRY_CUDA(launch_spmm<TV>(h, M, N, nnz, rp, ci, va, w, X, ldx, Y, ldy, status, st));
+        else
+            TSVD_TRY_CUDA(launch_spmm<TV>(h, N, M, nnz, trp, tci, tva, w, X, ldx, Y, ldy, status, st));
+    } else {
+        if (!trans_of_A)
+            TSVD_TRY_CUDA((gemm_nn<TV, TV, TV>(h, M, N, w, 1.0, dA, lda, X, ldx, 0.0, Y, ldy, false, st)));
+        else
+            TSVD_TRY_CUDA((gemm_tn<TV, TV>(h, M, N, w, dA, lda, X, ldx, Y, ldy, false, partial, st)));
+    }
+    return TSVD_OK;
+}
+
+// op(A) X and op(A)^T X in the working precision.
+template <typename T>
+int op_mul(tsvd_handle* h, Op<T>& op, int w, const T* X, int64_t ldx, T* Y, int64_t ldy, int* status,
+           cudaStream_t st) {
+    return apply<T>(h, op.sparse, op.transposed, op.M, op.N, op.nnz, op.rp, op.ci, op.va, op.trp, op.tci, op.tva,
+                    op.dA, op.lda, op.partial, w, X, ldx, Y, ldy, status, st);
+}
+template <typename T>
+int op_tmul(tsvd_handle* h, Op<T>& op, int w, const T* X, int64_t ldx, T* Y, int64_t ldy, int* status,
+            cudaStream_t st) {
+    return apply<T>(h, op.sparse, !op.transposed, op.M, op.N, op.nnz, op.rp, op.ci, op.va, op.trp, op.tci, op.tva,
+                    op.dA, op.lda, op.partial, w, X, ldx, Y, ldy, status, st);
+}
+// op(A) X and op(A)^T X with the FP64 values (final Rayleigh-Ritz step and residuals).
+template <typename T>
+int op_mul64(tsvd_handle* h, Op<T>& op, int w, const double* X, int64_t ldx, double* Y, int64_t ldy, int* status,
+             cudaStream_t st) {
+    return apply<double>(h, op.sparse, op.transposed, op.M, op.N, op.nnz, op.rp, op.ci, op.va64, op.trp, op.tci,
+                         op.tva64, op.dA64, op.lda64, op.partial, w, X, ldx, Y, ldy, status, st);
+}
+template <typename T>
+int op_tmul64(tsvd_handle* h, Op<T>& op, int w, const double* X, int64_t ldx, double* Y, int64_t ldy, int* status,
+              cudaStream_t st) {
+    return apply<double>(h, op.sparse, !op.transposed, op.M, op.N, op.nnz, op.rp, op.ci, op.va64, op.trp, op.tci,
+                         op.tva64, op.dA64, op.lda64, op.partial, w, X, ldx, Y, ldy, status, st);
+}
+
+size_t tn_partial_max(tsvd_handle* h, int64_t q, int64_t s, int wmax) {
+    size_t pb = 0;
+    for (int w = 1; w <= wmax; ++w) {
+        const size_t v = gemm_tn_ws(h, q, s, w, false);
+        if (v > pb) pb = v;
+    }
+    return pb;
+}
+
+// Carves and (when run) fills the operator: staged host input, CSR(A^T),
+// value conversions between FP64 and FP32, dense split-K scratch.
+template <typename T>
+int setup_op(tsvd_handle* h, const tsvd_matrix* A, int wmax, Arena& ar, Op<T>& op, int* status, cudaStream_t st,
+             bool run, float* ms_transpose) {
+    constexpr bool kF64 = sizeof(T) == sizeof(double);
+    const bool in64 = A->dtype == TSVD_F64;
+    const bool host = A->location == TSVD_HOST;
+    op.M = A->m;
+    op.N = A->n;
+    op.transposed = A->m < A->n;
+    op.m = op.transposed ? A->n : A->m;
+    op.n = op.transposed ? A->m : A->n;
+    op.sparse = A->format == TSVD_CSR;
+    const int64_t M = A->m, N = A->n;
+    if (op.sparse) {
+        const int64_t nnz = A->nnz;
+        op.nnz = nnz;
+        const int32_t* rp = A->row_ptr;
+        const int32_t* ci = A->col_idx;
+        const void* va = A->val;
+        if (host) {
+            int32_t* drp = ar.take<int32_t>(M + 1);
+            int32_t* dci = ar.take<int32_t>(nnz);
+            void* dva = in64 ? (void*)ar.take<double>(nnz) : (void*)ar.take<float>(nnz);
+            if (run) {
+                if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+                TSVD_TRY_CUDA(cudaMemcpyAsync(drp, rp, sizeof(int32_t) * (M + 1), cudaMemcpyHostToDevice, st));
+                TSVD_TRY_CUDA(cudaMemcpyAsync(dci, ci, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
+                TSVD_TRY_CUDA(cudaMemcpyAsync(dva, va, (in64 ? 8 : 4) * nnz, cudaMemcpyHostToDevice, st));
+            }
+            rp = drp;
+            ci = dci;
+            va = dva;
+        }
+        op.rp = rp;
+        op.ci = ci;
+        op.trp = ar.take<int32_t>(N + 1);
+        op.tci = ar.take<int32_t>(nnz);
+        void* tva_in = in64 ? (void*)ar.take<double>(nnz) : (void*)ar.take<float>(nnz);
+        if (run) {
+            if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+            Arena tmp = ar;  // transpose scratch, dead after the build
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (ms_transpose) {
+                cudaEventCreate(&e0);
+                cudaEventCreate(&e1);
+                cudaEventRecord(e0, st);
+            }
+            const int rc = in64 ? csr_transpose<double>(h, M, N, nnz, rp, ci, (const double*)va, op.trp, op.tci,
+                                                        (double*)tva_in, tmp, status, st)
+                                : csr_transpose<float>(h, M, N, nnz, rp, ci, (const float*)va, op.trp, op.tci,
+                                                       (float*)tva_in, tmp, status, st);
+            if (ms_transpose) {
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(ms_transpose, e0, e1);
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+            }
+            if (rc < 0) return rc;
+        } else {
+            Arena tmp = ar;
+            tmp.take<char>(csr_transpose_ws(M, N, nnz));
+            ar.off = tmp.off;  // size the scratch (the run reuses it later)
+        }
+        // values in both precisions
+        if (in64) {
+            op.va64 = (const double*)va;
+            op.tva64 = (const double*)tva_in;
+        } else {
+            double* v64 = ar.take<double>(nnz);
+            double* tv64 = ar.take<double>(nnz);
+            if (run) {
+                if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+                TSVD_TRY_CUDA((convert2d<float, double>(h, 1, nnz, (const float*)va, nnz, v64, nnz, st)));
+                TSVD_TRY_CUDA((convert2d<float, double>(h, 1, nnz, (const float*)tva_in, nnz, tv64, nnz, st)));
+            }
+            op.va64 = v64;
+            op.tva64 = tv64;
+        }
+        if (kF64) {
+            op.va = (const T*)op.va64;
+            op.tva = (const T*)op.tva64;
+        } else if (!in64) {
+            op.va = (const T*)va;
+            op.tva = (const T*)tva_in;
+        } else {
+            T* v = ar.take<T>(nnz);
+            T* tv = ar.take<T>(nnz);
+            if (run) {
+                if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+                TSVD_TRY_CUDA((convert2d<double, T>(h, 1, nnz, op.va64, nnz, v, nnz, st)));
+                TSVD_TRY_CUDA((convert2d<double, T>(h, 1, nnz, op.tva64, nnz, tv, nnz, st)));
+            }
+            op.va = v;
+            op.tva = tv;
+        }
+    } else {
+        const void* a = A->val;
+        int64_t lda = A->ld;
+        if (host) {
+            void* d = in64 ? (void*)ar.take<double>((size_t)M * N) : (void*)ar.take<float>((size_t)M * N);
+            if (run) {
+                if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+                const size_t es = in64 ? 8 : 4;
+                TSVD_TRY_CUDA(cudaMemcpy2DAsync(d, es * N, a, es * lda, es * N, M, cudaMemcpyHostToDevice, st));
+            }
+            a = d;
+            lda = N;
+        }
+        if (in64) {
+            op.dA64 = (const double*)a;
+            op.lda64 = lda;
+        } else {
+            double* d64 = ar.take<double>((size_t)M * N);
+            if (run) {
+                if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+                TSVD_TRY_CUDA((convert2d<float, double>(h, M, N, (const float*)a, lda, d64, N, st)));
+            }
+            op.dA64 = d64;
+            op.lda64 = N;
+        }
+        if (kF64) {
+            op.dA = (const T*)op.dA64;
+            op.lda = op.lda64;
+        } else if (!in64) {
+            op.dA = (const T*)a;
+            op.lda = lda;
+        } else {
+            T* d = ar.take<T>((size_t)M * N);
+            if (run) {
+                if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+                TSVD_TRY_CUDA((convert2d<double, T>(h, M, N, op.dA64, op.lda64, d, N, st)));
+            }
+            op.dA = d;
+            op.lda = N;
+        }
+        op.partial = ar.take<double>(tn_partial_max(h, M, N, wmax) / sizeof(double) + 1);
+    }
+    return TSVD_OK;
+}
+
+struct Timer {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStream_t st;
+    explicit Timer(cudaStream_t s) : st(s) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, st);
+    }
+    double stop() {
+        float ms = 0.f;
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    }
+    ~Timer() {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+};
+
+// Buffers of the final step and the outputs (FP64), shared by both methods.
+struct Final {
+    double *U64, *V64, *AV, *Mkk, *Uk, *Vk, *sk, *res, *cpart;
+    double *oU, *oV, *osig;  // device outputs when the caller wants host outputs
+    void* signws;
+};
+
+void carve_final(Arena& ar, const tsvd_opts* o, int64_t m, int64_t n, int k, bool mixed, Final& f) {
+    f = Final{};
+    if (mixed) {
+        f.U64 = ar.take<double>((size_t)m * k);
+        f.V64 = ar.take<double>((size_t)n * k);
+        f.Mkk = ar.take<double>((size_t)k * k);
+        f.Uk = ar.take<double>((size_t)k * k);
+        f.Vk = ar.take<double>((size_t)k * k);
+        f.sk = ar.take<double>(k);
+    }
+    f.AV = ar.take<double>((size_t)(m > n ? m : n) * k);
+    f.res = ar.take<double>(2 * (size_t)k);
+    f.cpart = ar.take<double>(colres_ws(m > n ? m : n, k) / sizeof(double) + 1);
+    f.signws = ar.take<char>(sign_fix_ws(m > n ? m : n, k));
+    if (o->output_location == TSVD_HOST) {
+        f.oU = ar.take<double>((size_t)m * k);
+        f.oV = ar.take<double>((size_t)n * k);
+        f.osig = ar.take<double>(k);
+    }
+}
+
+size_t final_tail_ws(tsvd_handle* h, int64_t m, int64_t n, int k, bool mixed) {
+    if (!mixed) return 0;
+    size_t a = orth_ws(h, m, 0, k), b = orth_ws(h, n, 0, k), c = small_svd_ws(k);
+    size_t p = tn_partial_max(h, m, k, k);
+    size_t r = a > b ? a : b;
+    if (c > r) r = c;
+    return r + p + 256;
+}
+
+// The returned triplets from the last small SVD: sigma, U = Bm Wm[:, :k],
+// V = Bn Wn[:, :k] (FP64 path), or the same followed by the FP64 Rayleigh-Ritz
+// step (mixed path).  Writes dev.{U,V,sigma} in op orientation.
+template <typename T>
+int final_triplets(tsvd_handle* h, Op<T>& op, int k, const T* Bm, int64_t ldbm, const double* Wm, int64_t ldwm,
+                   const T* Bn, int64_t ldbn, const double* Wn, int64_t ldwn, int wdim, const double* sig,
+                   Final& f, double* dU, double* dV, double* dsig, OrthCtx& ctx, Arena tail, int* status,
+                   cudaStream_t st, int* sweeps) {
+    constexpr bool kF64 = sizeof(T) == sizeof(double);
+    const int64_t m = op.m, n = op.n;
+    if (kF64) {
+        TSVD_TRY_CUDA((gemm_nn<T, double, double>(h, m, wdim, k, 1.0, Bm, ldbm, Wm, ldwm, 0.0, dU, k, false, st)));
+        TSVD_TRY_CUDA((gemm_nn<T, double, double>(h, n, wdim, k, 1.0, Bn, ldbn, Wn, ldwn, 0.0, dV, k, false, st)));
+        TSVD_TRY_CUDA(cudaMemcpyAsync(dsig, sig, sizeof(double) * k, cudaMemcpyDeviceToDevice, st));
+        return TSVD_OK;
+    }
+    // FP64 Rayleigh-Ritz on span(U), span(V)
+    TSVD_TRY_CUDA((gemm_nn<T, double, double>(h, m, wdim, k, 1.0, Bm, ldbm, Wm, ldwm, 0.0, f.U64, k, false, st)));
+    TSVD_TRY_CUDA((gemm_nn<T, double, double>(h, n, wdim, k, 1.0, Bn, ldbn, Wn, ldwn, 0.0, f.V64, k, false, st)));
+    TSVD_TRY(cgs_cqr2<double>(h, m, 0, k, nullptr, 0, f.U64, k, nullptr, f.Mkk, k, false, ctx, tail, status, st));
+    TSVD_TRY(cgs_cqr2<double>(h, n, 0, k, nullptr, 0, f.V64, k, nullptr, f.Mkk, k, false, ctx, tail, status, st));
+    TSVD_TRY(op_mul64(h, op, k, f.V64, k, f.AV, k, status, st));
+    Arena t2 = tail;
+    double* part = t2.take<double>(tn_partial_max(h, m, k, k) / sizeof(double) + 1);
+    if (!t2.fits()) return TSVD_ERR_WORKSPACE;
+    TSVD_TRY_CUDA((gemm_tn<double, double>(h, m, k, k, f.U64, k, f.AV, k, f.Mkk, k, false, part, st)));
+    TSVD_TRY(small_svd(h, k, f.Mkk, k, f.Uk, f.sk, f.Vk, k, t2, status, st));
+    TSVD_TRY_CUDA((gemm_nn<double, double, double>(h, m, k, k, 1.0, f.U64, k, f.Uk, k, 0.0, dU, k, false, st)));
+    TSVD_TRY_CUDA((gemm_nn<double, double, double>(h, n, k, k, 1.0, f.V64, k, f.Vk, k, 0.0, dV, k, false, st)));
+    TSVD_TRY_CUDA(cudaMemcpyAsync(dsig, f.sk, sizeof(double) * k, cudaMemcpyDeviceToDevice, st));
+    (void)sweeps;
+    return TSVD_OK;
+}
+
+// max_j max(||op(A) v_j - s_j u_j||, ||op(A)^T u_j - s_j v_j||) / s_1 with the FP64 A
+// (both one-sided residuals: the second vanishes by construction in the FP64
+// method, not after the mixed form's two-sided Rayleigh-Ritz step).
+template <typename T>
+int explicit_residual(tsvd_handle* h, Op<T>& op, int k, const double* U, const double* V, const double* sigma,
+                      Final& f, int* status, cudaStream_t st, double* out) {
+    TSVD_TRY(op_mul64(h, op, k, V, k, f.AV, k, status, st));
+    TSVD_TRY_CUDA(col_residual_sq(h, op.m, k, f.AV, k, U, k, sigma, f.res, f.cpart, st));
+    TSVD_TRY(op_tmul64(h, op, k, U, k, f.AV, k, status, st));
+    TSVD_TRY_CUDA(col_residual_sq(h, op.n, k, f.AV, k, V, k, sigma, f.res + k, f.cpart, st));
+    std::vector<double> hres(2 * k), hs(1);
+    TSVD_TRY_CUDA(cudaMemcpyAsync(hres.data(), f.res, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, st));
+    TSVD_TRY_CUDA(cudaMemcpyAsync(hs.data(), sigma, sizeof(double), cudaMemcpyDeviceToHost, st));
+    TSVD_TRY_CUDA(cudaStreamSynchronize(st));
+    double mx = 0.0;
+    for (int j = 0; j < 2 * k; ++j) mx = std::fmax(mx, std::sqrt(hres[j]));
+    *out = hs[0] > 0.0 ? mx / hs[0] : NAN;
+    return TSVD_OK;
+}
+
+// Sign convention, copies to the caller (host or device), U/V swap when transposed.
+template <typename T>
+int finish_outputs(tsvd_handle* h, const tsvd_opts* o, Op<T>& op, int k, double* dU, double* dV, double* dsig,
+                   Final& f, double* sigma, double* U, double* V, cudaStream_t st) {
+    TSVD_TRY_CUDA(sign_fix(h, op.n, op.m, k, dV, k, dU, k, f.signws, st));
+    if (o->output_location == TSVD_HOST) {
+        double* userU = op.transposed ? V : U;
+        double* userV = op.transposed ? U : V;
+        TSVD_TRY_CUDA(cudaMemcpyAsync(sigma, dsig, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        TSVD_TRY_CUDA(cudaMemcpyAsync(userU, dU, sizeof(double) * op.m * k, cudaMemcpyDeviceToHost, st));
+        TSVD_TRY_CUDA(cudaMemcpyAsync(userV, dV, sizeof(double) * op.n * k, cudaMemcpyDeviceToHost, st));
+    }
+    TSVD_TRY_CUDA(cudaStreamSynchronize(st));
+    return TSVD_OK;
+}
+
+int status_code(const int* hs) {
+    if (hs[kStTimeout]) return TSVD_ERR_TIMEOUT;
+    if (hs[kStNonfinite]) return TSVD_ERR_NONFINITE;
+    if (hs[kStBadCsr]) return TSVD_ERR_INVALID_ARG;
+    return TSVD_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// RandSVD
+// ---------------------------------------------------------------------------
+template <typename T>
+int rsvd_run(tsvd_handle* h, const tsvd_matrix* A, int k, int p, int q, int bq, uint64_t seed, const tsvd_opts* o,
+             char* ws, size_t ws_bytes, size_t* sizing, double* sigma, double* U, double* V, tsvd_info* info) {
+    constexpr bool kMixed = sizeof(T) != sizeof(double);
+    const bool run = sizing == nullptr;
+    cudaStream_t st = static_cast<cudaStream_t>(o->stream);
+    Arena ar{run ? ws : nullptr, ws_bytes, 0};
+    int* status = ar.take<int>(kStCount);
+    if (run) {
+        if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+        TSVD_TRY_CUDA(cudaMemsetAsync(status, 0, sizeof(int) * kStCount, st));
+    }
+    const int ell = k + p;
+    const int64_t l0 = h->launches;
+    Timer* total = run ? new Timer(st) : nullptr;
+    struct Del {
+        Timer* t;
+        ~Del() { delete t; }
+    } del{total};
+    Op<T> op;
+    float ms_t = 0.f;
+    TSVD_TRY(setup_op<T>(h, A, ell > k ? ell : k, ar, op, status, st, run, A->format == TSVD_CSR ? &ms_t : nullptr));
+    const int64_t m = op.m, n = op.n;
+    T* Qn = ar.take<T>((size_t)n * ell);
+    T* Qm = ar.take<T>((size_t)m * ell);
+    double* R = ar.take<double>((size_t)ell * ell);
+    double* Ub = ar.take<double>((size_t)ell * ell);
+    double* Vb = ar.take<double>((size_t)ell * ell);
+    double* sig = ar.take<double>(ell);
+    double* g64 = kMixed ? ar.take<double>((size_t)n * ell) : nullptr;
+    Final f;
+    carve_final(ar, o, m, n, k, kMixed, f);
+    if (!run) {
+        const int64_t qmax = m > n ? m : n;
+        size_t t1 = orth_ws(h, qmax, ell > bq ? ell - bq : 0, bq) + align256(sizeof(double) * (size_t)ell * bq);
+        const size_t t2 = small_svd_ws(ell), t3 = final_tail_ws(h, m, n, k, kMixed);
+        if (t2 > t1) t1 = t2;
+        if (t3 > t1) t1 = t3;
+        *sizing = ar.off + t1 + 256;
+        return TSVD_OK;
+    }
+    if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+    OrthCtx ctx;
+    ctx.seed = seed;
+    // Q_0 (n x l): raw Gaussian block (Alg. 1)
+    if (o->start_block) {
+        TSVD_TRY_CUDA((convert2d<double, T>(h, n, ell, o->start_block, ell, Qn, ell, st)));
+    } else if (kMixed) {
+        TSVD_TRY_CUDA(gaussian(h, n, ell, seed, 1u, g64, ell, st));
+        TSVD_TRY_CUDA((convert2d<double, T>(h, n, ell, g64, ell, Qn, ell, st)));
+    } else {
+        TSVD_TRY_CUDA(gaussian(h, n, ell, seed, 1u, reinterpret_cast<double*>(Qn), ell, st));
+    }
+    int iters = 0;
+    for (int it = 0; it <= q; ++it) {
+        TSVD_TRY(op_mul<T>(h, op, ell, Qn, ell, Qm, ell, status, st));                   // S1
+        TSVD_TRY(cgs_qr<T>(h, m, ell, bq, Qm, ell, R, ctx, ar, status, st));            // S2
+        TSVD_TRY(op_tmul<T>(h, op, ell, Qm, ell, Qn, ell, status, st));                  // S3
+        TSVD_TRY(cgs_qr<T>(h, n, ell, bq, Qn, ell, R, ctx, ar, status, st));            // S4
+        ++iters;
+    }
+    int hs[kStCount];
+    {
+        Arena sv = ar;
+        TSVD_TRY(small_svd(h, ell, R, ell, Ub, sig, Vb, k, sv, status, st));           // S5
+    }
+    double* dU = f.oU ? f.oU : (op.transposed ? V : U);
+    double* dV = f.oV ? f.oV : (op.transposed ? U : V);
+    double* dsig = f.osig ? f.osig : sigma;
+    // S6 U = Qbar Vbar, S7 V = Q Ubar (then the FP64 Rayleigh-Ritz step in the mixed form)
+    TSVD_TRY(final_triplets<T>(h, op, k, Qm, ell, Vb, ell, Qn, ell, Ub, ell, ell, sig, f, dU, dV, dsig, ctx, ar,
+                               status, st, nullptr));
+    TSVD_TRY(read_status(st, status, hs));
+    TSVD_TRY(status_code(hs));
+    const int sweeps = hs[kStSweeps];
+    TSVD_TRY(finish_outputs<T>(h, o, op, k, dU, dV, dsig, f, sigma, U, V, st));
+    const double ms_total = total->stop();
+    double resid = NAN;
+    TSVD_TRY(explicit_residual<T>(h, op, k, dU, dV, dsig, f, status, st, &resid));
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->iterations = iters;
+        info->breakdowns = ctx.fallbacks;
+        info->converged = 1;
+        info->transposed = op.transposed ? 1 : 0;
+        info->svd_sweeps = sweeps;
+        info->resid_max = resid;
+        info->rho_last = NAN;
+        info->ms_total = ms_total;
+        info->ms_transpose = ms_t;
+        info->kernel_launches = h->launches - l0;
+        prof_collect(h, info);
+    }
+    return TSVD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// LancSVD
+// ---------------------------------------------------------------------------
+template <typename T>
+int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint64_t seed, const tsvd_opts* o,
+                 char* ws, size_t ws_bytes, size_t* sizing, double* sigma, double* U, double* V, tsvd_info* info) {
+    constexpr bool kMixed = sizeof(T) != sizeof(double);
+    const bool run = sizing == nullptr;
+    cudaStream_t st = static_cast<cudaStream_t>(o->stream);
+    Arena ar{run ? ws : nullptr, ws_bytes, 0};
+    int* status = ar.take<int>(kStCount);
+    if (run) {
+        if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+        TSVD_TRY_CUDA(cudaMemsetAsync(status, 0, sizeof(int) * kStCount, st));
+    }
+    const int rb = r * b;
+    const int64_t l0 = h->launches;
+    Timer* total = run ? new Timer(st) : nullptr;
+    struct Del {
+        Timer* t;
+        ~Del() { delete t; }
+    } del{total};
+    Op<T> op;
+    float ms_t = 0.f;
+    TSVD_TRY(setup_op<T>(h, A, b > k ? b : k, ar, op, status, st, run, A->format == TSVD_CSR ? &ms_t : nullptr));
+    const int64_t m = op.m, n = op.n;
+    T* P = ar.take<T>((size_t)n * rb);
+    T* Pbar = ar.take<T>((size_t)m * rb);
+    T* Qnext = ar.take<T>((size_t)m * b);
+    double* B = ar.take<double>((size_t)rb * rb);
+    double* Ub = ar.take<double>((size_t)rb * rb);
+    double* Vb = ar.take<double>((size_t)rb * rb);
+    double* sig = ar.take<double>(rb);
+    double* Rr = ar.take<double>((size_t)b * b);
+    double* rho = ar.take<double>(k);
+    double* g64 = kMixed ? ar.take<double>((size_t)m * b) : nullptr;
+    Final f;
+    carve_final(ar, o, m, n, k, kMixed, f);
+    if (!run) {
+        size_t t1 = orth_ws(h, m, rb, b);
+        const size_t t2 = orth_ws(h, n, rb, b), t3 = small_svd_ws(rb), t4 = final_tail_ws(h, m, n, k, kMixed);
+        if (t2 > t1) t1 = t2;
+        if (t3 > t1) t1 = t3;
+        if (t4 > t1) t1 = t4;
+        *sizing = ar.off + t1 + 256;
+        return TSVD_OK;
+    }
+    if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+    OrthCtx ctx;
+    ctx.seed = seed;
+    double* dU = f.oU ? f.oU : (op.transposed ? V : U);
+    double* dV = f.oV ? f.oV : (op.transposed ? U : V);
+    double* dsig = f.osig ? f.osig : sigma;
+    // S1: random orthonormal Qbar_1 (m x b) in the first block column of Pbar
+    if (o->start_block) {
+        TSVD_TRY_CUDA((convert2d<double, T>(h, m, b, o->start_block, b, Pbar, rb, st)));
+    } else if (kMixed) {
+        TSVD_TRY_CUDA(gaussian(h, m, b, seed, 2u, g64, b, st));
+        TSVD_TRY_CUDA((convert2d<double, T>(h, m, b, g64, b, Pbar, rb, st)));
+    } else {
+        TSVD_TRY_CUDA(gaussian(h, m, b, seed, 2u, reinterpret_cast<double*>(Pbar), rb, st));
+    }
+    TSVD_TRY(cgs_cqr2<T>(h, m, 0, b, nullptr, 0, Pbar, rb, nullptr, Rr, b, false, ctx, ar, status, st));
+    int cycles = 0, restarts = 0, sweeps = 0, converged = 0;
+    double rho_last = NAN, resid = NAN;
+    std::vector<double> hrho(k), hsig(1);
+    int hs[kStCount];
+    for (;;) {
+        TSVD_TRY_CUDA(cudaMemsetAsync(B, 0, sizeof(double) * (size_t)rb * rb, st));
+        for (int i = 0; i < r; ++i) {
+            const int c0 = i * b;
+            T* Qi = P + c0;
+            TSVD_TRY(op_tmul<T>(h, op, b, Pbar + c0, rb, Qi, rb, status, st));                    // S2
+            double* Lii = B + (int64_t)c0 * rb + c0;
+            TSVD_TRY(cgs_cqr2<T>(h, n, c0, b, P, rb, Qi, rb, nullptr, Lii, rb, true, ctx, ar, status, st));  // S3
+            const bool last = (i + 1 == r);
+            T* dst = last ? Qnext : Pbar + c0 + b;
+            const int64_t ldd = last ? b : rb;
+            TSVD_TRY(op_mul<T>(h, op, b, Qi, rb, dst, ldd, status, st));                             // S4
+            double* Ri = last ? Rr : B + (int64_t)(c0 + b) * rb + c0;
+            TSVD_TRY(cgs_cqr2<T>(h, m, c0 + b, b, Pbar, rb, dst, ldd, nullptr, Ri, last ? b : rb, false, ctx, ar,
+                                 status, st));                                                       // S5
+        }
+        ++cycles;
+        {
+            Arena sv = ar;
+            TSVD_TRY(small_svd(h, rb, B, rb, Ub, sig, Vb, k > b ? k : b, sv, status, st));          // S6
+        }
+        TSVD_TRY_CUDA(lanczos_rho(h, b, k, Rr, Vb + (int64_t)(rb - b) * rb, rb, rho, st));
+        TSVD_TRY_CUDA(cudaMemcpyAsync(hrho.data(), rho, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        TSVD_TRY_CUDA(cudaMemcpyAsync(hsig.data(), sig, sizeof(double), cudaMemcpyDeviceToHost, st));
+        TSVD_TRY(read_status(st, status, hs));
+        TSVD_TRY(status_code(hs));
+        sweeps = hs[kStSweeps];
+        double rmax = 0.0;
+        for (int j = 0; j < k; ++j) rmax = std::fmax(rmax, hrho[j]);
+        rho_last = hsig[0] > 0.0 ? rmax / hsig[0] : NAN;
+        const bool done = rho_last <= o->tol;
+        if (done || restarts >= o->max_restarts) {
+            // S8/S9 (and the FP64 Rayleigh-Ritz step in the mixed form)
+            TSVD_TRY(final_triplets<T>(h, op, k, Pbar, rb, Ub, rb, P, rb, Vb, rb, rb, sig, f, dU, dV, dsig, ctx, ar,
+                                       status, st, nullptr));
+            TSVD_TRY(explicit_residual<T>(h, op, k, dU, dV, dsig, f, status, st, &resid));
+            if ((done && resid <= o->tol) || restarts >= o->max_restarts) {
+                converged = resid <= o->tol ? 1 : 0;
+                break;
+            }
+        }
+        ++restarts;
+        // S7: Qbar_1 = Pbar Ubar_1, re-orthonormalised by CholeskyQR2
+        TSVD_TRY_CUDA((gemm_nn<T, double, T>(h, m, rb, b, 1.0, Pbar, rb, Ub, rb, 0.0, Qnext, b, false, st)));
+        TSVD_TRY_CUDA(copy_block<T>(Qnext, b, Pbar, rb, m, b, st));
+        TSVD_TRY(cgs_cqr2<T>(h, m, 0, b, nullptr, 0, Pbar, rb, nullptr, Rr, b, false, ctx, ar, status, st));
+    }
+    TSVD_TRY(read_status(st, status, hs));
+    TSVD_TRY(status_code(hs));
+    TSVD_TRY(finish_outputs<T>(h, o, op, k, dU, dV, dsig, f, sigma, U, V, st));
+    const double ms_total = total->stop();
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->iterations = cycles;
+        info->restarts = restarts;
+        info->breakdowns = ctx.fallbacks;
+        info->converged = converged;
+        info->transposed = op.transposed ? 1 : 0;
+        info->svd_sweeps = sweeps;
+        info->resid_max = resid;
+        info->rho_last = rho_last;
+        info->ms_total = ms_total;
+        info->ms_transpose = ms_t;
+        info->kernel_launches = h->launches - l0;
+        prof_collect(h, info);
+    }
+    return converged ? TSVD_OK : TSVD_NOT_CONVERGED;
+}
+
+template int rsvd_run<double>(tsvd_handle*, const tsvd_matrix*, int, int, int, int, uint64_t, const tsvd_opts*,
+                              char*, size_t, size_t*, double*, double*, double*, tsvd_info*);
+template int rsvd_run<float>(tsvd_handle*, const tsvd_matrix*, int, int, int, int, uint64_t, const tsvd_opts*,
+                             char*, size_t, size_t*, double*, double*, double*, tsvd_info*);
+template int blanczos_run<double>(tsvd_handle*, const tsvd_matrix*, int, int, int, uint64_t, const tsvd_opts*,
+                                  char*, size_t, size_t*, double*, double*, double*, tsvd_info*);
+template int blanczos_run<float>(tsvd_handle*, const tsvd_matrix*, int, int, int, uint64_t, const tsvd_opts*,
+                                 char*, size_t, size_t*, double*, double*, double*, tsvd_info*);
+
+}  // namespace tsvd

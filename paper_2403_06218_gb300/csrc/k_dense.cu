@@ -37,14 +37,16 @@ __device__ inline void decode_upper(int lin, int nr, int& ri, int& rj) {
     rj = r + lin;
 }
 
+// TI: input element type (also the accumulation type within a slab); TW: type written.
+template <typename TI, typename TW>
 __global__ void __launch_bounds__(128) gemm_tn_kernel(int64_t q, int64_t s, int64_t b,
-                                                      const double* __restrict__ X, int64_t ldx,
-                                                      const double* __restrict__ Z, int64_t ldz,
-                                                      double* __restrict__ out, int64_t ldo,
+                                                      const TI* __restrict__ X, int64_t ldx,
+                                                      const TI* __restrict__ Z, int64_t ldz,
+                                                      TW* __restrict__ out, int64_t ldo,
                                                       int64_t slab_stride, int64_t slab_rows, int symmetric,
                                                       int nreg_s, int nreg_b) {
-    __shared__ double Xs[kTnKc][kTnR];
-    __shared__ double Zs[kTnKc][kTnR];
+    __shared__ TI Xs[kTnKc][kTnR];
+    __shared__ TI Zs[kTnKc][kTnR];
     int ri, rj;
     if (symmetric) {
         decode_upper((int)blockIdx.x, nreg_s, ri, rj);
@@ -58,24 +60,24 @@ __global__ void __launch_bounds__(128) gemm_tn_kernel(int64_t q, int64_t s, int6
     const int wr = warp >> 1, wc = warp & 1;
     const int i = lane >> 1, jg = (lane & 1) * 8;
     const bool active = !(symmetric && ri == rj && wr > wc);
-    double acc[8];
+    TI acc[8];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) acc[t] = 0.0;
+    for (int t = 0; t < 8; ++t) acc[t] = TI(0);
     const int64_t xc0 = (int64_t)ri * kTnR, zc0 = (int64_t)rj * kTnR;
     for (int64_t k0 = r0; k0 < r1; k0 += kTnKc) {
         for (int idx = tid; idx < kTnKc * kTnR; idx += 128) {
             const int rr = idx / kTnR, cc = idx % kTnR;
             const int64_t row = k0 + rr;
             const bool rin = row < r1;
-            Xs[rr][cc] = (rin && xc0 + cc < s) ? X[row * ldx + xc0 + cc] : 0.0;
-            Zs[rr][cc] = (rin && zc0 + cc < b) ? Z[row * ldz + zc0 + cc] : 0.0;
+            Xs[rr][cc] = (rin && xc0 + cc < s) ? X[row * ldx + xc0 + cc] : TI(0);
+            Zs[rr][cc] = (rin && zc0 + cc < b) ? Z[row * ldz + zc0 + cc] : TI(0);
         }
         __syncthreads();
         if (active) {
 #pragma unroll 4
             for (int kk = 0; kk < kTnKc; ++kk) {
-                const double x = Xs[kk][wr * 16 + i];
-                const double* zr = &Zs[kk][wc * 16 + jg];
+                const TI x = Xs[kk][wr * 16 + i];
+                const TI* zr = &Zs[kk][wc * 16 + jg];
 #pragma unroll
                 for (int t = 0; t < 8; ++t) acc[t] = fma(x, zr[t], acc[t]);
             }
@@ -85,17 +87,18 @@ __global__ void __launch_bounds__(128) gemm_tn_kernel(int64_t q, int64_t s, int6
     if (!active) return;
     const int64_t orow = xc0 + wr * 16 + i;
     if (orow >= s) return;
-    double* o = out + (int64_t)blockIdx.y * slab_stride + orow * ldo + zc0 + wc * 16 + jg;
+    TW* o = out + (int64_t)blockIdx.y * slab_stride + orow * ldo + zc0 + wc * 16 + jg;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
-        if (zc0 + wc * 16 + jg + t < b) o[t] = acc[t];
+        if (zc0 + wc * 16 + jg + t < b) o[t] = (TW)acc[t];
     }
 }
 
 // C[i][j] = sum over slabs (fixed order) of partial[slab][i][j]; symmetric reads
 // the upper element for both halves.
+template <typename TC>
 __global__ void gemm_tn_reduce_kernel(int64_t s, int64_t b, int slabs, const double* __restrict__ partial,
-                                      int64_t slab_stride, double* __restrict__ C, int64_t ldc, int symmetric) {
+                                      int64_t slab_stride, TC* __restrict__ C, int64_t ldc, int symmetric) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= s * b) return;
     int64_t i = idx / b, j = idx % b;
@@ -103,7 +106,7 @@ __global__ void gemm_tn_reduce_kernel(int64_t s, int64_t b, int slabs, const dou
     const int64_t jj = (symmetric && i > j) ? i : j;
     double acc = 0.0;
     for (int sl = 0; sl < slabs; ++sl) acc += partial[(int64_t)sl * slab_stride + ii * b + jj];
-    C[i * ldc + j] = acc;
+    C[i * ldc + j] = (TC)acc;
 }
 
 struct TnPlan {
@@ -116,7 +119,10 @@ TnPlan tn_plan(const tsvd_handle* h, int64_t q, int64_t s, int64_t b, bool symme
     p.nreg_s = (int)((s + kTnR - 1) / kTnR);
     p.nreg_b = (int)((b + kTnR - 1) / kTnR);
     p.regions = symmetric ? p.nreg_s * (p.nreg_s + 1) / 2 : p.nreg_s * p.nreg_b;
-    const int64_t target = 8LL * (h ? h->sm_count : 152);
+    // a fixed CTA target (8 per SM of a 152-SM GB300) keeps the split, the
+    // workspace size and the summation order independent of the device
+    (void)h;
+    const int64_t target = 8LL * 152;
     int64_t slabs = (target + p.regions - 1) / p.regions;
     const int64_t max_slabs = (q + 255) / 256;
     if (slabs > max_slabs) slabs = max_slabs;
@@ -136,20 +142,21 @@ TnPlan tn_plan(const tsvd_handle* h, int64_t q, int64_t s, int64_t b, bool symme
 // current panel (4*CW columns).  X tile and M chunk staged in shared memory,
 // output staged for coalesced stores.
 // ---------------------------------------------------------------------------
-template <int CW>
+// Accumulation in TX (the precision of the tall operand); M is converted to TX on load.
+template <int CW, typename TX, typename TM, typename TY>
 __global__ void __launch_bounds__(128) gemm_nn_kernel(int64_t q, int64_t s, int64_t b, double alpha,
-                                                      const double* __restrict__ X, int64_t ldx,
-                                                      const double* __restrict__ M, int64_t ldm, double beta,
-                                                      double* Y, int64_t ldy, int upper) {
+                                                      const TX* __restrict__ X, int64_t ldx,
+                                                      const TM* __restrict__ M, int64_t ldm, double beta,
+                                                      TY* Y, int64_t ldy, int upper) {
     constexpr int PW = 4 * CW;
-    __shared__ double Xs[32][33];
-    __shared__ double Ms[32][PW + 1];
+    __shared__ TX Xs[32][33];
+    __shared__ TX Ms[32][PW + 1];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t r0 = (int64_t)blockIdx.x * 32;
     for (int64_t c0 = 0; c0 < b; c0 += PW) {
-        double acc[CW];
+        TX acc[CW];
 #pragma unroll
-        for (int c = 0; c < CW; ++c) acc[c] = 0.0;
+        for (int c = 0; c < CW; ++c) acc[c] = TX(0);
         const int64_t jw_hi = c0 + (int64_t)(warp + 1) * CW - 1;  // last column of this warp
         int64_t kmax = s;
         if (upper) kmax = min(s, c0 + PW);
@@ -157,20 +164,20 @@ __global__ void __launch_bounds__(128) gemm_nn_kernel(int64_t q, int64_t s, int6
             for (int idx = tid; idx < 32 * 32; idx += 128) {
                 const int rr = idx >> 5, kk = idx & 31;
                 const int64_t row = r0 + rr, k = k0 + kk;
-                Xs[rr][kk] = (row < q && k < s) ? X[row * ldx + k] : 0.0;
+                Xs[rr][kk] = (row < q && k < s) ? X[row * ldx + k] : TX(0);
             }
             for (int idx = tid; idx < 32 * PW; idx += 128) {
                 const int kk = idx / PW, cc = idx % PW;
                 const int64_t k = k0 + kk, col = c0 + cc;
                 const bool in = k < s && col < b && !(upper && k > col);
-                Ms[kk][cc] = in ? M[k * ldm + col] : 0.0;
+                Ms[kk][cc] = in ? (TX)M[k * ldm + col] : TX(0);
             }
             __syncthreads();
             if (!(upper && k0 > jw_hi)) {
 #pragma unroll 4
                 for (int kk = 0; kk < 32; ++kk) {
-                    const double x = Xs[lane][kk];
-                    const double* mr = &Ms[kk][warp * CW];
+                    const TX x = Xs[lane][kk];
+                    const TX* mr = &Ms[kk][warp * CW];
 #pragma unroll
                     for (int c = 0; c < CW; ++c) acc[c] = fma(x, mr[c], acc[c]);
                 }
@@ -185,9 +192,9 @@ __global__ void __launch_bounds__(128) gemm_nn_kernel(int64_t q, int64_t s, int6
             const int rr = idx / PW, cc = idx % PW;
             const int64_t row = r0 + rr, col = c0 + cc;
             if (row < q && col < b) {
-                double* y = Y + row * ldy + col;
-                const double v = alpha * Ms[rr][cc];
-                *y = (beta != 0.0) ? fma(beta, *y, v) : v;
+                TY* y = Y + row * ldy + col;
+                const TX v = (TX)alpha * Ms[rr][cc];
+                *y = (beta != 0.0) ? (TY)fma((TX)beta, (TX)*y, v) : (TY)v;
             }
         }
         __syncthreads();
@@ -231,6 +238,7 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(int b, const double* __re
         s_thresh = (double)b * kEps * wmax;
     }
     __syncthreads();
+    __shared__ double s_inv;
     for (int j = 0; j < b && s_bad == 0; ++j) {
         const double d = A[j * ld + j];
         if (!isfinite(d) || !(d > s_thresh)) {
@@ -239,10 +247,17 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(int b, const double* __re
             __syncthreads();
             break;
         }
-        const double ljj = sqrt(d);
-        for (int i = j + 1 + tid; i < b; i += blockDim.x) A[i * ld + j] /= ljj;
+        // one thread does the scalar FP64 work (a warp-wide sqrt/divide costs the
+        // 2-lane FP64 pipe as much as 32 of them)
+        if (tid == 0) {
+            const double ljj = sqrt(d);
+            A[j * ld + j] = ljj;
+            s_inv = 1.0 / ljj;
+        }
         __syncthreads();
-        if (tid == 0) A[j * ld + j] = ljj;
+        const double inv = s_inv;
+        for (int i = j + 1 + tid; i < b; i += blockDim.x) A[i * ld + j] *= inv;
+        __syncthreads();
         const int nn = b - j - 1;
         const int cnt = nn * (nn + 1) / 2;
         for (int idx = tid; idx < cnt; idx += blockDim.x) {
@@ -439,14 +454,14 @@ size_t gemm_tn_ws(tsvd_handle* h, int64_t q, int64_t s, int64_t b, bool symmetri
     return align256(sizeof(double) * (size_t)p.slabs * (size_t)s * (size_t)b);
 }
 
-cudaError_t gemm_tn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, const double* X, int64_t ldx,
-                    const double* Z, int64_t ldz, double* C, int64_t ldc, bool symmetric, double* partial,
-                    cudaStream_t st) {
+template <typename TI, typename TC>
+cudaError_t gemm_tn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, const TI* X, int64_t ldx, const TI* Z,
+                    int64_t ldz, TC* C, int64_t ldc, bool symmetric, double* partial, cudaStream_t st) {
     if (s == 0 || b == 0) return cudaSuccess;
     const TnPlan p = tn_plan(h, q, s, b, symmetric);
     if (q == 0) {
         for (int64_t i = 0; i < s; ++i) {
-            cudaError_t e = cudaMemsetAsync(C + i * ldc, 0, sizeof(double) * b, st);
+            cudaError_t e = cudaMemsetAsync(C + i * ldc, 0, sizeof(TC) * b, st);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -455,40 +470,59 @@ cudaError_t gemm_tn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, const doubl
     // algorithmic work: 2qsb flops (the upper half, q b (b+1), for a Gram matrix);
     // compulsory traffic: X and Z read once, C written once
     ProfScope prof(h, TSVD_K_GEMM_TN, symmetric ? (double)q * b * (b + 1) : 2.0 * q * s * b,
-                   8.0 * ((double)q * (symmetric ? b : s + b) + (double)s * b), st);
+                   (double)sizeof(TI) * (double)q * (symmetric ? b : s + b) + (double)sizeof(TC) * s * b, st);
     if (p.slabs == 1 && !symmetric) {
         h->launches++;
-        gemm_tn_kernel<<<grid, 128, 0, st>>>(q, s, b, X, ldx, Z, ldz, C, ldc, 0, p.slab_rows, 0, p.nreg_s,
-                                             p.nreg_b);
+        gemm_tn_kernel<TI, TC><<<grid, 128, 0, st>>>(q, s, b, X, ldx, Z, ldz, C, ldc, 0, p.slab_rows, 0, p.nreg_s,
+                                                     p.nreg_b);
         return cudaGetLastError();
     }
     const int64_t stride = s * b;
     h->launches += 2;
-    gemm_tn_kernel<<<grid, 128, 0, st>>>(q, s, b, X, ldx, Z, ldz, partial, b, stride, p.slab_rows,
-                                         symmetric ? 1 : 0, p.nreg_s, p.nreg_b);
+    gemm_tn_kernel<TI, double><<<grid, 128, 0, st>>>(q, s, b, X, ldx, Z, ldz, partial, b, stride, p.slab_rows,
+                                                     symmetric ? 1 : 0, p.nreg_s, p.nreg_b);
     const int64_t tot = s * b;
-    gemm_tn_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(s, b, p.slabs, partial, stride, C, ldc,
-                                                                        symmetric ? 1 : 0);
+    gemm_tn_reduce_kernel<TC><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(s, b, p.slabs, partial, stride, C, ldc,
+                                                                            symmetric ? 1 : 0);
     return cudaGetLastError();
 }
 
-cudaError_t gemm_nn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, double alpha, const double* X, int64_t ldx,
-                    const double* M, int64_t ldm, double beta, double* Y, int64_t ldy, bool upper,
-                    cudaStream_t st) {
+template cudaError_t gemm_tn<double, double>(tsvd_handle*, int64_t, int64_t, int64_t, const double*, int64_t,
+                                             const double*, int64_t, double*, int64_t, bool, double*, cudaStream_t);
+template cudaError_t gemm_tn<float, double>(tsvd_handle*, int64_t, int64_t, int64_t, const float*, int64_t,
+                                            const float*, int64_t, double*, int64_t, bool, double*, cudaStream_t);
+template cudaError_t gemm_tn<float, float>(tsvd_handle*, int64_t, int64_t, int64_t, const float*, int64_t,
+                                           const float*, int64_t, float*, int64_t, bool, double*, cudaStream_t);
+
+template <typename TX, typename TM, typename TY>
+cudaError_t gemm_nn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, double alpha, const TX* X, int64_t ldx,
+                    const TM* M, int64_t ldm, double beta, TY* Y, int64_t ldy, bool upper, cudaStream_t st) {
     if (q == 0 || b == 0) return cudaSuccess;
     const unsigned grid = (unsigned)((q + 31) / 32);
     ProfScope prof(h, TSVD_K_GEMM_NN, upper ? (double)q * b * (b + 1) : 2.0 * q * s * b,
-                   8.0 * ((double)q * s + (double)s * b + (double)q * b * (beta != 0.0 ? 2 : 1)), st);
+                   (double)sizeof(TX) * q * s + (double)sizeof(TM) * s * b +
+                       (double)sizeof(TY) * q * b * (beta != 0.0 ? 2 : 1), st);
     h->launches++;
     if (b <= 32) {
-        gemm_nn_kernel<8><<<grid, 128, 0, st>>>(q, s, b, alpha, X, ldx, M, ldm, beta, Y, ldy, upper ? 1 : 0);
+        gemm_nn_kernel<8, TX, TM, TY><<<grid, 128, 0, st>>>(q, s, b, alpha, X, ldx, M, ldm, beta, Y, ldy, upper ? 1 : 0);
     } else if (b <= 64) {
-        gemm_nn_kernel<16><<<grid, 128, 0, st>>>(q, s, b, alpha, X, ldx, M, ldm, beta, Y, ldy, upper ? 1 : 0);
+        gemm_nn_kernel<16, TX, TM, TY><<<grid, 128, 0, st>>>(q, s, b, alpha, X, ldx, M, ldm, beta, Y, ldy,
+                                                             upper ? 1 : 0);
     } else {
-        gemm_nn_kernel<32><<<grid, 128, 0, st>>>(q, s, b, alpha, X, ldx, M, ldm, beta, Y, ldy, upper ? 1 : 0);
+        gemm_nn_kernel<32, TX, TM, TY><<<grid, 128, 0, st>>>(q, s, b, alpha, X, ldx, M, ldm, beta, Y, ldy,
+                                                             upper ? 1 : 0);
     }
     return cudaGetLastError();
 }
+
+#define TSVD_INST_NN(TX, TM, TY)                                                                                  \
+    template cudaError_t gemm_nn<TX, TM, TY>(tsvd_handle*, int64_t, int64_t, int64_t, double, const TX*, int64_t, \
+                                             const TM*, int64_t, double, TY*, int64_t, bool, cudaStream_t);
+TSVD_INST_NN(double, double, double)
+TSVD_INST_NN(float, double, float)
+TSVD_INST_NN(float, float, float)
+TSVD_INST_NN(float, double, double)
+#undef TSVD_INST_NN
 
 static size_t chol_smem(int b) { return sizeof(double) * ((size_t)b * (b + 1) + b); }
 

@@ -84,54 +84,97 @@ __global__ void jacobi_init_kernel(int n, int npad, const double* __restrict__ B
     }
 }
 
+constexpr int kJWarps = 4;     // warps per CTA when several CTAs share the sweep
+constexpr int kMaxSlots = 64;  // column pairs one CTA owns per round
+
+// One-sided Jacobi sweeps.  CTA b owns the round's pairs [b*ppb, (b+1)*ppb).
+// Per round: (A) each warp forms gamma = g_p.g_q for its pairs; (B) one lane per
+// pair turns (alpha, beta, gamma) into the rotation (c, s) and updates the squared
+// column norms alpha - t*gamma, beta + t*gamma (exact consequences of the rotation;
+// recomputed exactly at every sweep start); (C) the warps apply the rotations to
+// G (and to V when it is accumulated).  Scalar FP64 work (sqrt, division) is thus
+// done once per pair instead of once per lane.
 __global__ void jacobi_sweep_kernel(int n, int npad, double* __restrict__ G, double* __restrict__ V,
-                                    unsigned* ctl, double tol) {
-    const int lane = threadIdx.x & 31;
+                                    double* __restrict__ nrm, unsigned* ctl, double tol, int ppb) {
+    __shared__ double s_gam[kMaxSlots], s_c[kMaxSlots], s_s[kMaxSlots];
+    __shared__ int s_rot[kMaxSlots];
+    __shared__ int s_any;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    const int gw = blockIdx.x * wpb + (threadIdx.x >> 5);
-    const int total_w = gridDim.x * wpb;
     const int npairs = npad / 2;
+    const int base = blockIdx.x * ppb;
+    const int cnt = max(0, min(ppb, npairs - base));
     for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
-        bool rotated = false;
+        // exact squared column norms at the start of the sweep
+        for (int c = blockIdx.x * wpb + warp; c < npad; c += gridDim.x * wpb) {
+            const double* g = G + (int64_t)c * n;
+            double acc = 0.0;
+            for (int r = lane; r < n; r += 32) acc = fma(g[r], g[r], acc);
+            acc = warp_sum(acc);
+            if (lane == 0) nrm[c] = acc;
+        }
+        if (threadIdx.x == 0) s_any = 0;
+        if (!grid_sync(ctl)) return;
         for (int rnd = 0; rnd < npad - 1; ++rnd) {
-            for (int pi = gw; pi < npairs; pi += total_w) {
+            for (int slot = warp; slot < cnt; slot += wpb) {                     // (A)
+                const int pi = base + slot;
+                const int a = rr_player(pi, rnd, npad), bq = rr_player(npad - 1 - pi, rnd, npad);
+                const double* gp = G + (int64_t)min(a, bq) * n;
+                const double* gq = G + (int64_t)max(a, bq) * n;
+                double ga = 0.0;
+                for (int r = lane; r < n; r += 32) ga = fma(gp[r], gq[r], ga);
+                ga = warp_sum(ga);
+                if (lane == 0) s_gam[slot] = ga;
+            }
+            __syncthreads();
+            if (warp == 0) {                                                      // (B)
+                for (int slot = lane; slot < cnt; slot += 32) {
+                    const int pi = base + slot;
+                    const int a = rr_player(pi, rnd, npad), bq = rr_player(npad - 1 - pi, rnd, npad);
+                    const int p = min(a, bq), q = max(a, bq);
+                    const double al = nrm[p], be = nrm[q], ga = s_gam[slot];
+                    int rot = 0;
+                    if (ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+                        const double zeta = (be - al) / (2.0 * ga);
+                        const double t = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
+                        const double c = 1.0 / sqrt(fma(t, t, 1.0));
+                        s_c[slot] = c;
+                        s_s[slot] = c * t;
+                        nrm[p] = fma(-t, ga, al);
+                        nrm[q] = fma(t, ga, be);
+                        rot = 1;
+                        s_any = 1;
+                    }
+                    s_rot[slot] = rot;
+                }
+            }
+            __syncthreads();
+            for (int slot = warp; slot < cnt; slot += wpb) {                     // (C)
+                if (!s_rot[slot]) continue;
+                const int pi = base + slot;
                 const int a = rr_player(pi, rnd, npad), bq = rr_player(npad - 1 - pi, rnd, npad);
                 const int p = min(a, bq), q = max(a, bq);
+                const double c = s_c[slot], sn = s_s[slot];
                 double* gp = G + (int64_t)p * n;
                 double* gq = G + (int64_t)q * n;
-                double al = 0.0, be = 0.0, ga = 0.0;
                 for (int r = lane; r < n; r += 32) {
                     const double x = gp[r], y = gq[r];
-                    al = fma(x, x, al);
-                    be = fma(y, y, be);
-                    ga = fma(x, y, ga);
+                    gp[r] = fma(c, x, -sn * y);
+                    gq[r] = fma(sn, x, c * y);
                 }
-                al = warp_sum(al);
-                be = warp_sum(be);
-                ga = warp_sum(ga);
-                if (ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-                    const double zeta = (be - al) / (2.0 * ga);
-                    const double t = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
-                    const double c = 1.0 / sqrt(fma(t, t, 1.0));
-                    const double s = c * t;
-                    for (int r = lane; r < n; r += 32) {
-                        const double x = gp[r], y = gq[r];
-                        gp[r] = fma(c, x, -s * y);
-                        gq[r] = fma(s, x, c * y);
-                    }
+                if (V != nullptr) {
                     double* vp = V + (int64_t)p * npad;
                     double* vq = V + (int64_t)q * npad;
                     for (int r = lane; r < npad; r += 32) {
                         const double x = vp[r], y = vq[r];
-                        vp[r] = fma(c, x, -s * y);
-                        vq[r] = fma(s, x, c * y);
+                        vp[r] = fma(c, x, -sn * y);
+                        vq[r] = fma(sn, x, c * y);
                     }
-                    rotated = true;
                 }
             }
             if (!grid_sync(ctl)) return;
         }
-        if (rotated && lane == 0) atomicAdd(&ctl[kCtlRot + sweep], 1u);
+        if (threadIdx.x == 0 && s_any) atomicAdd(&ctl[kCtlRot + sweep], 1u);
         if (!grid_sync(ctl)) return;
         if (vload(&ctl[kCtlRot + sweep]) == 0u) {
             if (blockIdx.x == 0 && threadIdx.x == 0) ctl[kCtlSweeps] = (unsigned)(sweep + 1);
@@ -197,7 +240,9 @@ __global__ void __launch_bounds__(1024) jacobi_sort_kernel(int n, int npad, cons
     }
 }
 
-// CTA per output column j < n: sign convention and the row-major outputs.
+// CTA per output column j < n.  With V accumulated: the sign convention and the
+// row-major Ubar, Vbar.  Without V: Ubar = G / sigma only (the sign is fixed
+// later, together with the Vbar columns recovered from B^T Ubar).
 __global__ void __launch_bounds__(128) jacobi_out_kernel(int n, int npad, const double* __restrict__ G,
                                                          const double* __restrict__ V,
                                                          const double* __restrict__ sig, const int* __restrict__ perm,
@@ -207,11 +252,57 @@ __global__ void __launch_bounds__(128) jacobi_out_kernel(int n, int npad, const 
     __shared__ int bi[128];
     const int j = blockIdx.x;
     const int src = perm[j];
-    const double* v = V + (int64_t)src * npad;
+    double sgn = 1.0;
+    const double* v = V ? V + (int64_t)src * npad : nullptr;
+    if (v) {
+        double best = -1.0;
+        int besti = 0;
+        for (int r = threadIdx.x; r < n; r += blockDim.x) {
+            const double a = fabs(v[r]);
+            if (a > best) {
+                best = a;
+                besti = r;
+            }
+        }
+        bv[threadIdx.x] = best;
+        bi[threadIdx.x] = besti;
+        __syncthreads();
+        for (int d = 64; d > 0; d >>= 1) {
+            if (threadIdx.x < d) {
+                const double ob = bv[threadIdx.x + d];
+                const int oi = bi[threadIdx.x + d];
+                if (ob > bv[threadIdx.x] || (ob == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
+                    bv[threadIdx.x] = ob;
+                    bi[threadIdx.x] = oi;
+                }
+            }
+            __syncthreads();
+        }
+        sgn = v[bi[0]] < 0.0 ? -1.0 : 1.0;
+    }
+    const double sj = sig[j];
+    const double inv = sj > 0.0 ? 1.0 / sj : 0.0;
+    const double* g = G + (int64_t)src * n;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        Ubar[(int64_t)r * n + j] = sgn * (g[r] * inv);
+        if (v) Vbar[(int64_t)r * n + j] = sgn * v[r];
+    }
+    if (threadIdx.x == 0) sigma[j] = sj;
+}
+
+// Vbar[:, j] (held unscaled as B^T ubar_j) /= sigma_j, then the pair (ubar_j, vbar_j)
+// is flipped so the largest-magnitude entry of vbar_j (first on ties) is positive.
+__global__ void __launch_bounds__(128) jacobi_vfix_kernel(int n, const double* __restrict__ sigma,
+                                                          double* __restrict__ Ubar, double* __restrict__ Vbar) {
+    __shared__ double bv[128];
+    __shared__ int bi[128];
+    const int j = blockIdx.x;
+    const double sj = sigma[j];
+    const double inv = sj > 0.0 ? 1.0 / sj : 0.0;
     double best = -1.0;
     int besti = 0;
     for (int r = threadIdx.x; r < n; r += blockDim.x) {
-        const double a = fabs(v[r]);
+        const double a = fabs(Vbar[(int64_t)r * n + j] * inv);
         if (a > best) {
             best = a;
             besti = r;
@@ -231,15 +322,12 @@ __global__ void __launch_bounds__(128) jacobi_out_kernel(int n, int npad, const 
         }
         __syncthreads();
     }
-    const double sgn = v[bi[0]] < 0.0 ? -1.0 : 1.0;
-    const double sj = sig[j];
-    const double inv = sj > 0.0 ? 1.0 / sj : 0.0;
-    const double* g = G + (int64_t)src * n;
+    const double sgn = (Vbar[(int64_t)bi[0] * n + j] * inv) < 0.0 ? -1.0 : 1.0;
+    __syncthreads();
     for (int r = threadIdx.x; r < n; r += blockDim.x) {
-        Ubar[(int64_t)r * n + j] = sgn * (g[r] * inv);
-        Vbar[(int64_t)r * n + j] = sgn * v[r];
+        Vbar[(int64_t)r * n + j] = sgn * (Vbar[(int64_t)r * n + j] * inv);
+        Ubar[(int64_t)r * n + j] = sgn * Ubar[(int64_t)r * n + j];
     }
-    if (threadIdx.x == 0) sigma[j] = sj;
 }
 
 }  // namespace
@@ -250,21 +338,51 @@ size_t small_svd_ws(int n) {
     ar.take<double>((size_t)n * npad);
     ar.take<double>((size_t)npad * npad);
     ar.take<double>(npad);
+    ar.take<double>(npad);
     ar.take<int>(npad);
     ar.take<unsigned>(kCtlWords);
+    size_t part = 0;
+    for (int nv = 1; nv <= n; ++nv) {
+        const size_t v = gemm_tn_ws(nullptr, n, n, nv, false);
+        if (v > part) part = v;
+    }
+    ar.take<char>(part + sizeof(double));
     return ar.off;
 }
 
-int small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* Ubar, double* sigma, double* Vbar,
+static int jacobi_grid(const tsvd_handle* h, int npairs, int& block) {
+    if (npairs <= 32) {  // one CTA, one warp per pair, __syncthreads between rounds
+        block = 32 * npairs;
+        return 1;
+    }
+    block = 32 * kJWarps;
+    int nb = (npairs + kJWarps - 1) / kJWarps;
+    if (nb > h->sm_count) nb = h->sm_count;
+    const int min_nb = (npairs + kMaxSlots - 1) / kMaxSlots;
+    if (nb < min_nb) nb = min_nb;
+    if (nb > h->jacobi_coop_blocks) return 0;
+    return nb;
+}
+
+int small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* Ubar, double* sigma, double* Vbar, int nv,
               Arena& ar, int* status, cudaStream_t st) {
     if (n < 1 || n > TSVD_MAX_SMALL_SVD) return TSVD_ERR_UNSUPPORTED;
+    if (nv < 0 || nv > n) return TSVD_ERR_INVALID_ARG;
     const int npad = n + (n & 1);
+    const bool accumulate = (nv == n);
     double* G = ar.take<double>((size_t)n * npad);
     double* V = ar.take<double>((size_t)npad * npad);
+    double* nrm = ar.take<double>(npad);
     double* sig = ar.take<double>(npad);
     int* perm = ar.take<int>(npad);
     unsigned* ctl = ar.take<unsigned>(kCtlWords);
+    double* part = ar.take<double>(gemm_tn_ws(h, n, n, nv > 0 ? nv : 1, false) / sizeof(double) + 1);
     if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+    const int npairs = npad / 2;
+    int block = 0;
+    const int nblocks = jacobi_grid(h, npairs, block);
+    if (nblocks < 1) return TSVD_ERR_UNSUPPORTED;
+    const int ppb = (npairs + nblocks - 1) / nblocks;
     ProfScope prof(h, TSVD_K_SVD, 0.0, 0.0, st);
     TSVD_TRY_CUDA(cudaMemsetAsync(ctl, 0, sizeof(unsigned) * kCtlWords, st));
     const int64_t tot = (int64_t)npad * npad;
@@ -272,28 +390,37 @@ int small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* Ubar,
     jacobi_init_kernel<<<(unsigned)((tot + 255) / 256 < 4096 ? (tot + 255) / 256 : 4096), 256, 0, st>>>(
         n, npad, B, ldb, G, V);
     TSVD_TRY_CUDA(cudaGetLastError());
-    const int npairs = npad / 2;
     const double tol = (double)(n > 16 ? n : 16) * kEps;
-    if (npad <= 64) {
-        jacobi_sweep_kernel<<<1, 32 * npairs, 0, st>>>(n, npad, G, V, ctl, tol);
+    double* Vacc = accumulate ? V : nullptr;
+    if (nblocks == 1) {
+        jacobi_sweep_kernel<<<1, block, 0, st>>>(n, npad, G, Vacc, nrm, ctl, tol, ppb);
         TSVD_TRY_CUDA(cudaGetLastError());
     } else {
-        int nblocks = npairs < h->jacobi_coop_blocks ? npairs : h->jacobi_coop_blocks;
-        if (nblocks < 1) return TSVD_ERR_UNSUPPORTED;
-        void* args[] = {(void*)&n, (void*)&npad, (void*)&G, (void*)&V, (void*)&ctl, (void*)&tol};
-        TSVD_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_sweep_kernel, dim3(nblocks), dim3(32), args,
+        int nn = n, np = npad, pp = ppb;
+        double t = tol;
+        void* args[] = {(void*)&nn, (void*)&np, (void*)&G, (void*)&Vacc, (void*)&nrm, (void*)&ctl, (void*)&t,
+                        (void*)&pp};
+        TSVD_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_sweep_kernel, dim3(nblocks), dim3(block), args,
                                                   0, st));
     }
     jacobi_sort_kernel<<<1, 1024, 0, st>>>(n, npad, G, sig, perm, ctl, status);
-    jacobi_out_kernel<<<n, 128, 0, st>>>(n, npad, G, V, sig, perm, Ubar, sigma, Vbar);
+    jacobi_out_kernel<<<n, 128, 0, st>>>(n, npad, G, Vacc, sig, perm, Ubar, sigma, Vbar);
     TSVD_TRY_CUDA(cudaGetLastError());
+    if (!accumulate && nv > 0) {
+        // right vectors of the leading nv triplets: vbar_j = B^T ubar_j / sigma_j
+        TSVD_TRY_CUDA(gemm_tn(h, n, n, nv, B, ldb, Ubar, n, Vbar, n, false, part, st));
+        h->launches++;
+        jacobi_vfix_kernel<<<nv, 128, 0, st>>>(n, sigma, Ubar, Vbar);
+        TSVD_TRY_CUDA(cudaGetLastError());
+    }
     return TSVD_OK;
 }
 
-// Occupancy of the cooperative sweep kernel (called once per handle).
+// Co-resident CTAs of the cooperative sweep kernel at its multi-CTA block size.
 int jacobi_coop_capacity(int device, int sm_count) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_sweep_kernel, 32, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_sweep_kernel, 32 * kJWarps, 0) != cudaSuccess)
+        return 0;
     (void)device;
     return per_sm * sm_count;
 }

@@ -16,25 +16,37 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-// NV = number of double2 per lane per column panel (panel width 64*NV).
-template <int NV>
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<double> {
+    using type = double2;
+};
+template <>
+struct Vec2<float> {
+    using type = float2;
+};
+
+// NV = number of 2-element vectors per lane per column panel (panel width 64*NV).
+template <typename T, int NV>
 __global__ void __launch_bounds__(256) spmm_v2_kernel(int64_t m, int64_t n, const int32_t* __restrict__ rp,
                                                       const int32_t* __restrict__ ci,
-                                                      const double* __restrict__ va, int w,
-                                                      const double* __restrict__ X, int64_t ldx,
-                                                      double* __restrict__ Y, int64_t ldy, int* status) {
+                                                      const T* __restrict__ va, int w,
+                                                      const T* __restrict__ X, int64_t ldx,
+                                                      T* __restrict__ Y, int64_t ldy, int* status) {
+    using V2 = typename Vec2<T>::type;
     const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= m) return;
     const int beg = rp[row], end = rp[row + 1];
     for (int c0 = 0; c0 < w; c0 += 64 * NV) {
-        double2 acc[NV];
+        T ax[NV], ay[NV];
 #pragma unroll
-        for (int t = 0; t < NV; ++t) acc[t] = make_double2(0.0, 0.0);
+        for (int t = 0; t < NV; ++t) ax[t] = ay[t] = T(0);
         for (int e0 = beg; e0 < end; e0 += 32) {
             const int e = e0 + lane;
             int myc = 0;
-            double mya = 0.0;
+            T mya = T(0);
             if (e < end) {
                 myc = ci[e];
                 mya = va[e];
@@ -42,54 +54,58 @@ __global__ void __launch_bounds__(256) spmm_v2_kernel(int64_t m, int64_t n, cons
             const int cnt = min(32, end - e0);
             for (int j = 0; j < cnt; ++j) {
                 const int c = __shfl_sync(kFull, myc, j);
-                const double a = __shfl_sync(kFull, mya, j);
+                const T a = __shfl_sync(kFull, mya, j);
                 if ((uint64_t)(int64_t)c >= (uint64_t)n) {
                     if (lane == 0) atomicOr(&status[kStBadCsr], 1);
                     continue;
                 }
-                const double* xr = X + (int64_t)c * ldx + c0;
+                const T* xr = X + (int64_t)c * ldx + c0;
 #pragma unroll
                 for (int t = 0; t < NV; ++t) {
                     const int col = 2 * lane + 64 * t;
                     if (c0 + col + 1 < w) {
-                        const double2 x = *reinterpret_cast<const double2*>(xr + col);
-                        acc[t].x = fma(a, x.x, acc[t].x);
-                        acc[t].y = fma(a, x.y, acc[t].y);
+                        const V2 x = *reinterpret_cast<const V2*>(xr + col);
+                        ax[t] = fma(a, x.x, ax[t]);
+                        ay[t] = fma(a, x.y, ay[t]);
                     } else if (c0 + col < w) {
-                        acc[t].x = fma(a, xr[col], acc[t].x);
+                        ax[t] = fma(a, xr[col], ax[t]);
                     }
                 }
             }
         }
-        double* yr = Y + row * ldy + c0;
+        T* yr = Y + row * ldy + c0;
 #pragma unroll
         for (int t = 0; t < NV; ++t) {
             const int col = 2 * lane + 64 * t;
             if (c0 + col + 1 < w) {
-                *reinterpret_cast<double2*>(yr + col) = acc[t];
+                V2 v;
+                v.x = ax[t];
+                v.y = ay[t];
+                *reinterpret_cast<V2*>(yr + col) = v;
             } else if (c0 + col < w) {
-                yr[col] = acc[t].x;
+                yr[col] = ax[t];
             }
         }
     }
 }
 
 // Scalar variant for unaligned blocks: lane owns columns lane + 32 t.
+template <typename T>
 __global__ void __launch_bounds__(256) spmm_scalar_kernel(int64_t m, int64_t n, const int32_t* __restrict__ rp,
                                                           const int32_t* __restrict__ ci,
-                                                          const double* __restrict__ va, int w,
-                                                          const double* __restrict__ X, int64_t ldx,
-                                                          double* __restrict__ Y, int64_t ldy, int* status) {
+                                                          const T* __restrict__ va, int w,
+                                                          const T* __restrict__ X, int64_t ldx,
+                                                          T* __restrict__ Y, int64_t ldy, int* status) {
     const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= m) return;
     const int beg = rp[row], end = rp[row + 1];
     for (int c0 = 0; c0 < w; c0 += 128) {
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        T acc[4] = {T(0), T(0), T(0), T(0)};
         for (int e0 = beg; e0 < end; e0 += 32) {
             const int e = e0 + lane;
             int myc = 0;
-            double mya = 0.0;
+            T mya = T(0);
             if (e < end) {
                 myc = ci[e];
                 mya = va[e];
@@ -97,12 +113,12 @@ __global__ void __launch_bounds__(256) spmm_scalar_kernel(int64_t m, int64_t n, 
             const int cnt = min(32, end - e0);
             for (int j = 0; j < cnt; ++j) {
                 const int c = __shfl_sync(kFull, myc, j);
-                const double a = __shfl_sync(kFull, mya, j);
+                const T a = __shfl_sync(kFull, mya, j);
                 if ((uint64_t)(int64_t)c >= (uint64_t)n) {
                     if (lane == 0) atomicOr(&status[kStBadCsr], 1);
                     continue;
                 }
-                const double* xr = X + (int64_t)c * ldx + c0;
+                const T* xr = X + (int64_t)c * ldx + c0;
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
                     const int col = lane + 32 * t;
@@ -110,7 +126,7 @@ __global__ void __launch_bounds__(256) spmm_scalar_kernel(int64_t m, int64_t n, 
                 }
             }
         }
-        double* yr = Y + row * ldy + c0;
+        T* yr = Y + row * ldy + c0;
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             const int col = lane + 32 * t;
@@ -223,10 +239,11 @@ __global__ void scan_add_kernel(int64_t n, int32_t* __restrict__ out, const int3
 }
 
 // Warp per row: scatter (row, val) into the transposed arrays.
+template <typename T>
 __global__ void csr_scatter_kernel(int64_t m, int64_t n, int64_t nnz, const int32_t* __restrict__ rp,
-                                   const int32_t* __restrict__ ci, const double* __restrict__ va,
+                                   const int32_t* __restrict__ ci, const T* __restrict__ va,
                                    int32_t* __restrict__ cursor, int32_t* __restrict__ tci,
-                                   double* __restrict__ tva) {
+                                   T* __restrict__ tva) {
     const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= m) return;
@@ -242,19 +259,20 @@ __global__ void csr_scatter_kernel(int64_t m, int64_t n, int64_t nnz, const int3
 }
 
 // Segments of at most 32 entries: warp bitonic sort of (row, val) by row.
+template <typename T>
 __global__ void seg_sort_warp_kernel(int64_t n, const int32_t* __restrict__ trp, int32_t* __restrict__ tci,
-                                     double* __restrict__ tva) {
+                                     T* __restrict__ tva) {
     const int64_t seg = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (seg >= n) return;
     const int beg = trp[seg], len = trp[seg + 1] - beg;
     if (len <= 1 || len > 32) return;
     int key = lane < len ? tci[beg + lane] : INT_MAX;
-    double val = lane < len ? tva[beg + lane] : 0.0;
+    T val = lane < len ? tva[beg + lane] : T(0);
     for (int k = 2; k <= 32; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
             const int okey = __shfl_xor_sync(kFull, key, j);
-            const double oval = __shfl_xor_sync(kFull, val, j);
+            const T oval = __shfl_xor_sync(kFull, val, j);
             const bool up = (lane & k) == 0 || k == 32;
             const bool lower = (lane & j) == 0;
             const bool take_other = (lower == up) ? (okey < key) : (okey > key);
@@ -274,11 +292,12 @@ constexpr int kSegSmem = 4096;
 
 // Segments of 33..4096 entries: one CTA, bitonic sort (all blocks ascending,
 // first step of each merge compares i with i ^ (k-1)) in shared memory.
+template <typename T>
 __global__ void __launch_bounds__(256) seg_sort_cta_kernel(int64_t n, const int32_t* __restrict__ trp,
                                                            int32_t* __restrict__ tci,
-                                                           double* __restrict__ tva) {
+                                                           T* __restrict__ tva) {
     __shared__ int32_t sk[kSegSmem];
-    __shared__ double sv[kSegSmem];
+    __shared__ T sv[kSegSmem];
     for (int64_t seg = blockIdx.x; seg < n; seg += gridDim.x) {
         const int beg = trp[seg], len = trp[seg + 1] - beg;
         if (len <= 32 || len > kSegSmem) continue;
@@ -286,7 +305,7 @@ __global__ void __launch_bounds__(256) seg_sort_cta_kernel(int64_t n, const int3
         while (P < len) P <<= 1;
         for (int i = threadIdx.x; i < P; i += blockDim.x) {
             sk[i] = i < len ? tci[beg + i] : INT_MAX;
-            sv[i] = i < len ? tva[beg + i] : 0.0;
+            sv[i] = i < len ? tva[beg + i] : T(0);
         }
         __syncthreads();
         for (int k = 2; k <= P; k <<= 1) {
@@ -297,7 +316,7 @@ __global__ void __launch_bounds__(256) seg_sort_cta_kernel(int64_t n, const int3
                         const int tk = sk[i];
                         sk[i] = sk[p];
                         sk[p] = tk;
-                        const double tv = sv[i];
+                        const T tv = sv[i];
                         sv[i] = sv[p];
                         sv[p] = tv;
                     }
@@ -329,8 +348,9 @@ __global__ void seg_heavy_kernel(int64_t n, const int32_t* __restrict__ trp, int
 // One comparator stage of the same bitonic network in global memory, for the
 // long segments; comparators whose partner lies past the segment end are skipped
 // (those slots act as +infinity and never move below the end).
+template <typename T>
 __global__ void seg_sort_global_stage(const int32_t* __restrict__ trp, const int32_t* __restrict__ list,
-                                      int32_t* __restrict__ tci, double* __restrict__ tva, int k, int j,
+                                      int32_t* __restrict__ tci, T* __restrict__ tva, int k, int j,
                                       int64_t half_p) {
     const int seg = list[blockIdx.y];
     const int beg = trp[seg], len = trp[seg + 1] - beg;
@@ -345,37 +365,60 @@ __global__ void seg_sort_global_stage(const int32_t* __restrict__ trp, const int
         if (b < a) {
             tci[beg + lo] = b;
             tci[beg + hi] = a;
-            const double tv = tva[beg + lo];
+            const T tv = tva[beg + lo];
             tva[beg + lo] = tva[beg + hi];
             tva[beg + hi] = tv;
         }
     }
 }
 
+__global__ void to_float_kernel(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
+}
+
 }  // namespace
 
+cudaError_t convert_to_float(tsvd_handle* h, int64_t n, const double* x, float* y, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    h->launches++;
+    to_float_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, x, y);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_spmm(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr,
-                        const int32_t* col_idx, const double* val, int w, const double* X,
-                        int64_t ldx, double* Y, int64_t ldy, int* status, cudaStream_t st) {
+                        const int32_t* col_idx, const T* val, int w, const T* X, int64_t ldx, T* Y,
+                        int64_t ldy, int* status, cudaStream_t st) {
     if (m == 0 || w == 0) return cudaSuccess;
     // compulsory traffic: the CSR arrays, X and Y once each
+    const double es = (double)sizeof(T);
     ProfScope prof(h, TSVD_K_SPMM, 2.0 * nnz * w,
-                   12.0 * nnz + 4.0 * (m + 1) + 8.0 * (double)n * w + 8.0 * (double)m * w, st);
+                   (4.0 + es) * nnz + 4.0 * (m + 1) + es * (double)n * w + es * (double)m * w, st);
     const unsigned blocks = (unsigned)((m + 7) / 8);
-    const bool v2 = (ldx % 2 == 0) && (ldy % 2 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0) &&
-                    ((reinterpret_cast<uintptr_t>(Y) & 15) == 0);
+    const bool v2 = (ldx % 2 == 0) && (ldy % 2 == 0) && ((reinterpret_cast<uintptr_t>(X) & (2 * sizeof(T) - 1)) == 0) &&
+                    ((reinterpret_cast<uintptr_t>(Y) & (2 * sizeof(T) - 1)) == 0);
     h->launches++;
     if (v2 && w <= 64) {
-        spmm_v2_kernel<1><<<blocks, 256, 0, st>>>(m, n, row_ptr, col_idx, val, w, X, ldx, Y, ldy, status);
+        spmm_v2_kernel<T, 1><<<blocks, 256, 0, st>>>(m, n, row_ptr, col_idx, val, w, X, ldx, Y, ldy, status);
     } else if (v2 && w <= 128) {
-        spmm_v2_kernel<2><<<blocks, 256, 0, st>>>(m, n, row_ptr, col_idx, val, w, X, ldx, Y, ldy, status);
+        spmm_v2_kernel<T, 2><<<blocks, 256, 0, st>>>(m, n, row_ptr, col_idx, val, w, X, ldx, Y, ldy, status);
     } else if (v2) {
-        spmm_v2_kernel<4><<<blocks, 256, 0, st>>>(m, n, row_ptr, col_idx, val, w, X, ldx, Y, ldy, status);
+        spmm_v2_kernel<T, 4><<<blocks, 256, 0, st>>>(m, n, row_ptr, col_idx, val, w, X, ldx, Y, ldy, status);
     } else {
-        spmm_scalar_kernel<<<blocks, 256, 0, st>>>(m, n, row_ptr, col_idx, val, w, X, ldx, Y, ldy, status);
+        spmm_scalar_kernel<T><<<blocks, 256, 0, st>>>(m, n, row_ptr, col_idx, val, w, X, ldx, Y, ldy, status);
     }
     return cudaGetLastError();
 }
+
+template cudaError_t launch_spmm<double>(tsvd_handle*, int64_t, int64_t, int64_t, const int32_t*, const int32_t*,
+                                         const double*, int, const double*, int64_t, double*, int64_t, int*,
+                                         cudaStream_t);
+template cudaError_t launch_spmm<float>(tsvd_handle*, int64_t, int64_t, int64_t, const int32_t*, const int32_t*,
+                                        const float*, int, const float*, int64_t, float*, int64_t, int*,
+                                        cudaStream_t);
 
 size_t csr_transpose_ws(int64_t m, int64_t n, int64_t nnz) {
     (void)m;
@@ -390,9 +433,10 @@ size_t csr_transpose_ws(int64_t m, int64_t n, int64_t nnz) {
     return ar.off;
 }
 
+template <typename T>
 int csr_transpose(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr,
-                  const int32_t* col_idx, const double* val, int32_t* t_row_ptr, int32_t* t_col_idx,
-                  double* t_val, Arena& ar, int* status, cudaStream_t st) {
+                  const int32_t* col_idx, const T* val, int32_t* t_row_ptr, int32_t* t_col_idx,
+                  T* t_val, Arena& ar, int* status, cudaStream_t st) {
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
     int32_t* cnt = ar.take<int32_t>(n + 1);
     int32_t* cursor = ar.take<int32_t>(n + 1);
@@ -423,15 +467,15 @@ int csr_transpose(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz, const int32
     if (hs[kStBadCsr]) return TSVD_ERR_INVALID_ARG;
     if (m > 0) {
         h->launches++;
-        csr_scatter_kernel<<<(unsigned)((m + 7) / 8), 256, 0, st>>>(m, n, nnz, row_ptr, col_idx, val, cursor,
+        csr_scatter_kernel<T><<<(unsigned)((m + 7) / 8), 256, 0, st>>>(m, n, nnz, row_ptr, col_idx, val, cursor,
                                                                    t_col_idx, t_val);
         TSVD_TRY_CUDA(cudaGetLastError());
     }
     if (n > 0) {
         h->launches += 3;
-        seg_sort_warp_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(n, t_row_ptr, t_col_idx, t_val);
+        seg_sort_warp_kernel<T><<<(unsigned)((n + 7) / 8), 256, 0, st>>>(n, t_row_ptr, t_col_idx, t_val);
         const unsigned cta_grid = (unsigned)(n < 4 * (int64_t)h->sm_count ? n : 4 * (int64_t)h->sm_count);
-        seg_sort_cta_kernel<<<cta_grid, 256, 0, st>>>(n, t_row_ptr, t_col_idx, t_val);
+        seg_sort_cta_kernel<T><<<cta_grid, 256, 0, st>>>(n, t_row_ptr, t_col_idx, t_val);
         seg_heavy_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, t_row_ptr, heavy, hinfo);
         TSVD_TRY_CUDA(cudaGetLastError());
         int32_t hh[2];
@@ -445,7 +489,7 @@ int csr_transpose(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz, const int32
             for (int64_t k = 2; k <= P; k <<= 1) {
                 for (int64_t j = k >> 1; j > 0; j >>= 1) {
                     h->launches++;
-                    seg_sort_global_stage<<<dim3(gx, (unsigned)hh[0]), 256, 0, st>>>(
+                    seg_sort_global_stage<T><<<dim3(gx, (unsigned)hh[0]), 256, 0, st>>>(
                         t_row_ptr, heavy, t_col_idx, t_val, (int)k, (int)j, half_p);
                 }
             }
@@ -454,5 +498,10 @@ int csr_transpose(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz, const int32
     }
     return TSVD_OK;
 }
+
+template int csr_transpose<double>(tsvd_handle*, int64_t, int64_t, int64_t, const int32_t*, const int32_t*,
+                                   const double*, int32_t*, int32_t*, double*, Arena&, int*, cudaStream_t);
+template int csr_transpose<float>(tsvd_handle*, int64_t, int64_t, int64_t, const int32_t*, const int32_t*,
+                                  const float*, int32_t*, int32_t*, float*, Arena&, int*, cudaStream_t);
 
 }  // namespace tsvd

@@ -8,6 +8,11 @@
 // triangular solve Q L^{-T} is applied as a product with the explicitly inverted
 // factor (same DFMA count, a product kernel instead of a solve).  The outputs
 // follow the exact algebra: R = Lbar^T L^T and H = H + Hbar L^T.
+//
+// The routines are templated on the storage type T of the tall blocks: double for
+// the FP64 method, float for the mixed-precision form, where the products read
+// FP32 blocks but every Gram matrix, projection coefficient, Cholesky factor and R
+// stays FP64 (split-K partial sums are reduced in FP64).
 #include <cmath>
 #include <vector>
 
@@ -22,9 +27,16 @@ __global__ void axpy_kernel(int64_t n, const double* __restrict__ x, double* __r
 }
 
 // v[i*ld] = v[i*ld] / d[0]
-__global__ void scale_col_kernel(int64_t q, double* __restrict__ v, int64_t ld, const double* __restrict__ d) {
+template <typename T>
+__global__ void scale_col_kernel(int64_t q, T* __restrict__ v, int64_t ld, const double* __restrict__ d) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < q) v[i * ld] = v[i * ld] / d[0];
+    if (i < q) v[i * ld] = (T)((double)v[i * ld] / d[0]);
+}
+
+template <typename T>
+__global__ void d2t_kernel(int64_t n, const double* __restrict__ x, T* __restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (T)x[i];
 }
 
 __global__ void sqrt_kernel(double* __restrict__ x) { x[0] = sqrt(x[0]); }
@@ -48,13 +60,16 @@ __global__ void put_hcol_kernel(int64_t s, int j, const double* __restrict__ hco
         H[i * ldh + j] = hcol[i];
 }
 
+template <typename T>
 struct OrthWs {
-    double *W, *Lt1, *Mt1, *Lt2, *Mt2, *H1, *H2, *partial, *save;
-    double *fcol, *fh, *fhacc, *fc, *fcacc, *fnrm;
+    double *W, *Lt1, *Mt1, *Lt2, *Mt2, *H1, *H2, *partial;
+    T *save, *fcol;
+    double *fcol64, *fh, *fhacc, *fc, *fcacc, *fnrm;
 };
 
-OrthWs carve(tsvd_handle* h, Arena& ar, int64_t q, int64_t s, int b) {
-    OrthWs w{};
+template <typename T>
+OrthWs<T> carve(tsvd_handle* h, Arena& ar, int64_t q, int64_t s, int b) {
+    OrthWs<T> w{};
     const size_t bb = (size_t)b * b;
     w.W = ar.take<double>(bb);
     w.Lt1 = ar.take<double>(bb);
@@ -74,8 +89,9 @@ OrthWs carve(tsvd_handle* h, Arena& ar, int64_t q, int64_t s, int b) {
     for (int j = 1; j <= b; ++j) upd(gemm_tn_ws(h, q, j, 1, false));
     upd(gemm_tn_ws(h, q, 1, 1, true));
     w.partial = ar.take<double>(pbytes / sizeof(double) + 1);
-    w.save = ar.take<double>((size_t)q * b);
-    w.fcol = ar.take<double>((size_t)q);
+    w.save = ar.take<T>((size_t)q * b);
+    w.fcol = ar.take<T>((size_t)q);
+    w.fcol64 = ar.take<double>((size_t)q);
     w.fh = ar.take<double>((size_t)(s > 0 ? s : 1));
     w.fhacc = ar.take<double>((size_t)(s > 0 ? s : 1));
     w.fc = ar.take<double>((size_t)b);
@@ -85,7 +101,8 @@ OrthWs carve(tsvd_handle* h, Arena& ar, int64_t q, int64_t s, int b) {
 }
 
 // One CholeskyQR step (Alg. 4 S1-S3): W = Y^T Y, W = L L^T, Y <- Y L^{-T}.
-cudaError_t cholqr_step(tsvd_handle* h, int64_t q, int b, double* Y, int64_t ldy, double* W, double* Lt, double* Mt,
+template <typename T>
+cudaError_t cholqr_step(tsvd_handle* h, int64_t q, int b, T* Y, int64_t ldy, double* W, double* Lt, double* Mt,
                         double* partial, int* status, cudaStream_t st) {
     cudaError_t e = gemm_tn(h, q, b, b, Y, ldy, Y, ldy, W, b, true, partial, st);
     if (e != cudaSuccess) return e;
@@ -95,8 +112,9 @@ cudaError_t cholqr_step(tsvd_handle* h, int64_t q, int b, double* Y, int64_t ldy
 }
 
 // v -= [P, Yprev] ([P, Yprev]^T v), twice; accumulating coefficients when asked.
-int project_twice(tsvd_handle* h, int64_t q, int64_t s, const double* P, int64_t ldp, int j, const double* Yprev,
-                  int64_t ldy, double* v, int64_t ldv, OrthWs& w, bool accumulate, cudaStream_t st) {
+template <typename T>
+int project_twice(tsvd_handle* h, int64_t q, int64_t s, const T* P, int64_t ldp, int j, const T* Yprev,
+                  int64_t ldy, T* v, int64_t ldv, OrthWs<T>& w, bool accumulate, cudaStream_t st) {
     for (int pass = 0; pass < 2; ++pass) {
         if (s > 0) {
             TSVD_TRY_CUDA(gemm_tn(h, q, s, 1, P, ldp, v, ldv, w.fh, 1, false, w.partial, st));
@@ -119,7 +137,8 @@ int project_twice(tsvd_handle* h, int64_t q, int64_t s, const double* P, int64_t
     return TSVD_OK;
 }
 
-int read_norm(tsvd_handle* h, int64_t q, const double* v, int64_t ldv, OrthWs& w, double* out, cudaStream_t st) {
+template <typename T>
+int read_norm(tsvd_handle* h, int64_t q, const T* v, int64_t ldv, OrthWs<T>& w, double* out, cudaStream_t st) {
     TSVD_TRY_CUDA(gemm_tn(h, q, 1, 1, v, ldv, v, ldv, w.fnrm, 1, true, w.partial, st));
     h->launches++;
     sqrt_kernel<<<1, 1, 0, st>>>(w.fnrm);
@@ -131,11 +150,12 @@ int read_norm(tsvd_handle* h, int64_t q, const double* v, int64_t ldv, OrthWs& w
 
 // Column-wise CGS with re-orthogonalisation (fallback of Sec. 3.2):
 // Y_in = P H + Q R, P^T Q = 0, Q^T Q = I; numerically dependent columns get Philox replacements.
-int cgs2_columns(tsvd_handle* h, int64_t q, int64_t s, int b, const double* P, int64_t ldp, double* Y, int64_t ldy,
-                 double* H, int64_t ldh, double* R, int64_t ldr, bool r_trans, OrthCtx& ctx, OrthWs& w,
+template <typename T>
+int cgs2_columns(tsvd_handle* h, int64_t q, int64_t s, int b, const T* P, int64_t ldp, T* Y, int64_t ldy,
+                 double* H, int64_t ldh, double* R, int64_t ldr, bool r_trans, OrthCtx& ctx, OrthWs<T>& w,
                  cudaStream_t st) {
     for (int j = 0; j < b; ++j) {
-        double* v = Y + j;
+        T* v = Y + j;
         double nrm0 = 0.0, nrm = 0.0;
         TSVD_TRY(read_norm(h, q, v, ldy, w, &nrm0, st));
         if (s > 0) TSVD_TRY_CUDA(cudaMemsetAsync(w.fhacc, 0, sizeof(double) * s, st));
@@ -153,8 +173,10 @@ int cgs2_columns(tsvd_handle* h, int64_t q, int64_t s, int b, const double* P, i
         TSVD_TRY_CUDA(cudaGetLastError());
         if (!(nrm > 1e-10 * nrm0) || nrm0 == 0.0) {
             // dependent column: replace its direction by a Philox N(0,1) column
-            TSVD_TRY_CUDA(gaussian(h, q, 1, ctx.seed, 0x100u + (uint32_t)ctx.replacements, w.fcol, 1, st));
+            TSVD_TRY_CUDA(gaussian(h, q, 1, ctx.seed, 0x100u + (uint32_t)ctx.replacements, w.fcol64, 1, st));
             ctx.replacements++;
+            h->launches++;
+            d2t_kernel<T><<<(unsigned)((q + 255) / 256), 256, 0, st>>>(q, w.fcol64, w.fcol);
             TSVD_TRY(project_twice(h, q, s, P, ldp, j, Y, ldy, w.fcol, 1, w, false, st));
             double zn = 0.0;
             TSVD_TRY(read_norm(h, q, w.fcol, 1, w, &zn, st));
@@ -162,7 +184,7 @@ int cgs2_columns(tsvd_handle* h, int64_t q, int64_t s, int b, const double* P, i
             TSVD_TRY_CUDA(copy_block(w.fcol, 1, v, ldy, q, 1, st));
         }
         h->launches++;
-        scale_col_kernel<<<(unsigned)((q + 255) / 256), 256, 0, st>>>(q, v, ldy, w.fnrm);
+        scale_col_kernel<T><<<(unsigned)((q + 255) / 256), 256, 0, st>>>(q, v, ldy, w.fnrm);
         TSVD_TRY_CUDA(cudaGetLastError());
     }
     return TSVD_OK;
@@ -178,15 +200,16 @@ int read_status(cudaStream_t st, const int* d_status, int* h_status) {
 
 size_t orth_ws(tsvd_handle* h, int64_t q, int64_t s, int b) {
     Arena ar;
-    carve(h, ar, q, s, b);
+    carve<double>(h, ar, q, s, b);
     return ar.off;
 }
 
-int cgs_cqr2(tsvd_handle* h, int64_t q, int64_t s, int b, const double* P, int64_t ldp, double* Y, int64_t ldy,
+template <typename T>
+int cgs_cqr2(tsvd_handle* h, int64_t q, int64_t s, int b, const T* P, int64_t ldp, T* Y, int64_t ldy,
              double* H, double* R, int64_t ldr, bool r_trans, OrthCtx& ctx, Arena ar, int* status,
              cudaStream_t st) {
     if (b < 1 || b > TSVD_MAX_BLOCK || q < b) return TSVD_ERR_INVALID_ARG;
-    OrthWs w = carve(h, ar, q, s, b);
+    OrthWs<T> w = carve<T>(h, ar, q, s, b);
     if (!ar.fits()) return TSVD_ERR_WORKSPACE;
     TSVD_TRY_CUDA(copy_block(Y, ldy, w.save, b, q, b, st));
     if (s > 0) {
@@ -217,13 +240,14 @@ int cgs_cqr2(tsvd_handle* h, int64_t q, int64_t s, int b, const double* P, int64
     return TSVD_OK;
 }
 
-int cgs_qr(tsvd_handle* h, int64_t q, int r, int b, double* Y, int64_t ldy, double* R, OrthCtx& ctx, Arena ar,
+template <typename T>
+int cgs_qr(tsvd_handle* h, int64_t q, int r, int b, T* Y, int64_t ldy, double* R, OrthCtx& ctx, Arena ar,
            int* status, cudaStream_t st) {
     if (b < 1) return TSVD_ERR_INVALID_ARG;
     if (b > r) b = r;
     TSVD_TRY_CUDA(cudaMemsetAsync(R, 0, sizeof(double) * (size_t)r * r, st));
     // S1: first block by CholeskyQR2; its R goes to R[0:b, 0:b]
-    TSVD_TRY(cgs_cqr2(h, q, 0, b, nullptr, 0, Y, ldy, nullptr, R, r, false, ctx, ar, status, st));
+    TSVD_TRY(cgs_cqr2<T>(h, q, 0, b, nullptr, 0, Y, ldy, nullptr, R, r, false, ctx, ar, status, st));
     for (int c0 = b; c0 < r; c0 += b) {  // S2: later blocks against the earlier ones
         const int c1 = c0 + b < r ? c0 + b : r;
         const int bw = c1 - c0;
@@ -231,11 +255,20 @@ int cgs_qr(tsvd_handle* h, int64_t q, int r, int b, double* Y, int64_t ldy, doub
         Arena sub = ar;
         double* Hp = sub.take<double>((size_t)c0 * bw);
         if (!sub.fits()) return TSVD_ERR_WORKSPACE;
-        TSVD_TRY(cgs_cqr2(h, q, c0, bw, Y, ldy, Y + c0, ldy, Hp, R + (int64_t)c0 * r + c0, r, false, ctx, sub,
-                          status, st));
+        TSVD_TRY(cgs_cqr2<T>(h, q, c0, bw, Y, ldy, Y + c0, ldy, Hp, R + (int64_t)c0 * r + c0, r, false, ctx, sub,
+                             status, st));
         TSVD_TRY_CUDA(copy_block(Hp, bw, R + c0, r, c0, bw, st));
     }
     return TSVD_OK;
 }
+
+template int cgs_cqr2<double>(tsvd_handle*, int64_t, int64_t, int, const double*, int64_t, double*, int64_t,
+                              double*, double*, int64_t, bool, OrthCtx&, Arena, int*, cudaStream_t);
+template int cgs_cqr2<float>(tsvd_handle*, int64_t, int64_t, int, const float*, int64_t, float*, int64_t, double*,
+                             double*, int64_t, bool, OrthCtx&, Arena, int*, cudaStream_t);
+template int cgs_qr<double>(tsvd_handle*, int64_t, int, int, double*, int64_t, double*, OrthCtx&, Arena, int*,
+                            cudaStream_t);
+template int cgs_qr<float>(tsvd_handle*, int64_t, int, int, float*, int64_t, double*, OrthCtx&, Arena, int*,
+                           cudaStream_t);
 
 }  // namespace tsvd

@@ -123,27 +123,38 @@ int read_status(cudaStream_t st, const int* d_status, int* h_status /* kStCount 
 
 // y = A x, CSR A (m rows), x (w columns, ldx), y (ldy).  Entries whose column
 // is outside [0, n) are skipped and flag kStBadCsr.
+// T = double (FP64 path) or float (mixed path: FP32 values and blocks).
+template <typename T>
 cudaError_t launch_spmm(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr,
-                        const int32_t* col_idx, const double* val, int w, const double* X,
-                        int64_t ldx, double* Y, int64_t ldy, int* status, cudaStream_t st);
+                        const int32_t* col_idx, const T* val, int w, const T* X,
+                        int64_t ldx, T* Y, int64_t ldy, int* status, cudaStream_t st);
 
 size_t csr_transpose_ws(int64_t m, int64_t n, int64_t nnz);
+template <typename T>
 int csr_transpose(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr,
-                  const int32_t* col_idx, const double* val, int32_t* t_row_ptr,
-                  int32_t* t_col_idx, double* t_val, Arena& ar, int* status, cudaStream_t st);
+                  const int32_t* col_idx, const T* val, int32_t* t_row_ptr,
+                  int32_t* t_col_idx, T* t_val, Arena& ar, int* status, cudaStream_t st);
+
+// y[i] = (float)x[i]
+cudaError_t convert_to_float(tsvd_handle* h, int64_t n, const double* x, float* y, cudaStream_t st);
 
 // C (s x b, ldc) = X^T Z over q rows; X (q x s, ldx), Z (q x b, ldz).
 // symmetric: X == Z and s == b; only the upper half is computed and mirrored.
+// TI in {double, float} is the input and in-slab accumulation type; split-K
+// partial sums are FP64; TC is the output type.
 size_t gemm_tn_ws(tsvd_handle* h, int64_t q, int64_t s, int64_t b, bool symmetric);
-cudaError_t gemm_tn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, const double* X, int64_t ldx,
-                    const double* Z, int64_t ldz, double* C, int64_t ldc, bool symmetric,
+template <typename TI, typename TC>
+cudaError_t gemm_tn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, const TI* X, int64_t ldx,
+                    const TI* Z, int64_t ldz, TC* C, int64_t ldc, bool symmetric,
                     double* partial_ws, cudaStream_t st);
 
 // Y (q x b, ldy) = beta Y + alpha X M; X (q x s, ldx), M (s x b, ldm).
 // upper: M is upper triangular (entries below the diagonal are not read).
 // Y may alias X (in place) when s == b and ldx == ldy.
-cudaError_t gemm_nn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, double alpha, const double* X,
-                    int64_t ldx, const double* M, int64_t ldm, double beta, double* Y, int64_t ldy,
+// Accumulates in TX; M is converted to TX.
+template <typename TX, typename TM, typename TY>
+cudaError_t gemm_nn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, double alpha, const TX* X,
+                    int64_t ldx, const TM* M, int64_t ldm, double beta, TY* Y, int64_t ldy,
                     bool upper, cudaStream_t st);
 
 // Cholesky W = L L^T of a b x b SPD matrix (ld b) in one CTA; writes
@@ -159,10 +170,12 @@ cudaError_t trmm_upper(tsvd_handle* h, int b, const double* A, const double* U, 
 cudaError_t gaussian(tsvd_handle* h, int64_t rows, int64_t cols, uint64_t seed, uint32_t stream_id,
                      double* out, int64_t ld, cudaStream_t st);
 
-// Small SVD by one-sided Jacobi.
+// Small SVD by one-sided Jacobi.  nv == n accumulates every right vector; nv < n
+// recovers only the leading nv right vectors as B^T ubar_j / sigma_j (columns
+// j >= nv of Vbar are left undefined and those of Ubar carry no sign convention).
 size_t small_svd_ws(int n);
 int small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* Ubar, double* sigma,
-              double* Vbar, Arena& ar, int* status, cudaStream_t st);
+              double* Vbar, int nv, Arena& ar, int* status, cudaStream_t st);
 
 // out[j] = sum_i (Y[i,j] - U[i,j] * sigma[j])^2 for j < k  (deterministic).
 size_t colres_ws(int64_t q, int k);
@@ -179,12 +192,13 @@ size_t sign_fix_ws(int64_t n, int k);
 cudaError_t sign_fix(tsvd_handle* h, int64_t n, int64_t m, int k, double* V, int64_t ldv,
                      double* U, int64_t ldu, void* ws, cudaStream_t st);
 
-// Strided 2-D copy of a rows x cols block of doubles (device to device).
-inline cudaError_t copy_block(const double* src, int64_t lds, double* dst, int64_t ldd,
-                              int64_t rows, int64_t cols, cudaStream_t st) {
+// Strided 2-D copy of a rows x cols block (device to device).
+template <typename T>
+inline cudaError_t copy_block(const T* src, int64_t lds, T* dst, int64_t ldd, int64_t rows, int64_t cols,
+                              cudaStream_t st) {
     if (rows == 0 || cols == 0) return cudaSuccess;
-    return cudaMemcpy2DAsync(dst, ldd * sizeof(double), src, lds * sizeof(double),
-                             cols * sizeof(double), rows, cudaMemcpyDeviceToDevice, st);
+    return cudaMemcpy2DAsync(dst, ldd * sizeof(T), src, lds * sizeof(T), cols * sizeof(T), rows,
+                             cudaMemcpyDeviceToDevice, st);
 }
 
 // ---- orthogonalisation (orth.cu) -------------------------------------------
@@ -194,12 +208,16 @@ struct OrthCtx {
     int fallbacks = 0;     // Cholesky breakdowns sent to the CGS2 fallback
 };
 
+// Workspace of one orthogonalisation (sized for double blocks, which covers float).
 size_t orth_ws(tsvd_handle* h, int64_t q, int64_t s, int b);
 // Y (q x b) <- Q; R (b x b, ld ldr, trans: write R^T); H (s x b, ld b) optional.
-int cgs_cqr2(tsvd_handle* h, int64_t q, int64_t s, int b, const double* P, int64_t ldp,
-             double* Y, int64_t ldy, double* H, double* R, int64_t ldr, bool r_trans,
+// T = double or float (storage of P and Y); H and R are FP64.
+template <typename T>
+int cgs_cqr2(tsvd_handle* h, int64_t q, int64_t s, int b, const T* P, int64_t ldp,
+             T* Y, int64_t ldy, double* H, double* R, int64_t ldr, bool r_trans,
              OrthCtx& ctx, Arena ar, int* status, cudaStream_t st);
-int cgs_qr(tsvd_handle* h, int64_t q, int r, int b, double* Y, int64_t ldy, double* R,
+template <typename T>
+int cgs_qr(tsvd_handle* h, int64_t q, int r, int b, T* Y, int64_t ldy, double* R,
            OrthCtx& ctx, Arena ar, int* status, cudaStream_t st);
 
 }  // namespace tsvd

