@@ -268,6 +268,32 @@ int tsvd_small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb,
                    double* Ubar, double* sigma, double* Vbar, int* sweeps,
                    void* ws, size_t ws_bytes, void* stream);
 
+/* ---- allocation-free variant ------------------------------------------- */
+
+/* Y = A^T X exactly as tsvd_dense_mm with trans = 1 (same kernels, same split
+ * of the sum, same result), but without a workspace: the split-K partial sums
+ * live in one device array of TSVD_NOALLOC_SCRATCH_BYTES compiled into the
+ * library.  The paper has no counterpart; this exists for callers that cannot
+ * allocate device memory, e.g. code running inside an application whose own
+ * memory pool already holds the whole device, or latency-critical code that
+ * must never call cudaMalloc/cudaFree (they can synchronise the device).
+ *   - A: m x n row-major (lda), X: m x w (ldx), Y: n x w (ldy), all device
+ *     memory owned by the caller.
+ *   - Shapes whose partial sums would exceed TSVD_NOALLOC_SCRATCH_BYTES return
+ *     TSVD_ERR_UNSUPPORTED before any device work.
+ *   - The first call on a device looks up the array's device address with the
+ *     handle's device made current (cudaGetSymbolAddress); make that first call
+ *     before any stream capture.
+ *   - Every call on a device shares the one array: calls whose work overlaps on
+ *     the GPU (other streams, other threads) race on it and must be serialised
+ *     by the caller.  Nothing in it needs to start at zero.
+ *   - Each GPU that loads the library keeps the array until the process exits.
+ *   - Synchronises `stream` before returning. */
+#define TSVD_NOALLOC_SCRATCH_BYTES (16 * 1024 * 1024)
+int tsvd_dense_mm_t_noalloc(tsvd_handle* h, int64_t m, int64_t n, const double* A, int64_t lda,
+                            int w, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                            void* stream);
+
 #ifdef __cplusplus
 }
 #endif
