@@ -188,7 +188,8 @@ def run_reference(args, cfg):
 
 
 def run_case(case):
-    """One building block at the largest shape of the benchmark solve (inputs > L2)."""
+    """One building block at the largest shape of the benchmark solve (inputs > L2),
+    called three times; prints the CUDA-event time of each call."""
     import torch
     import paper_2403_06218_gb300 as tsvd
     g = torch.Generator(device="cuda").manual_seed(0)
@@ -196,16 +197,22 @@ def run_case(case):
         # n-side CGS-CQR2 of the last Lanczos step: q = 100,000, s = 15 * 64, b = 64
         P = tsvd.cgs_qr(torch.randn(100_000, 960, dtype=torch.float64, device="cuda", generator=g), 128)[0]
         Y = torch.randn(100_000, 64, dtype=torch.float64, device="cuda", generator=g)
-        for _ in range(2):
-            Q, H, R, bd = tsvd.cgs_cqr2(Y, P)
+        call = lambda: tsvd.cgs_cqr2(Y, P)  # noqa: E731
     else:
-        # projected matrix of one restart cycle: 1024 x 1024 lower block bidiagonal
+        # projected matrix of one restart cycle: 1024 x 1024 lower block bidiagonal (b = 64)
         B = torch.tril(torch.randn(1024, 1024, dtype=torch.float64, device="cuda", generator=g))
-        B = B - torch.tril(B, -65)
-        for _ in range(2):
-            tsvd.small_svd(B)
-    torch.cuda.synchronize()
-    print(json.dumps({"case": case, "ok": True}))
+        B = (B - torch.tril(B, -65) + 24.0 * torch.eye(1024, dtype=torch.float64, device="cuda")).contiguous()
+        call = lambda: tsvd.small_svd(B, nv=64)  # noqa: E731
+    times = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = call()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    info = {"sweeps": out[3]} if case == "svd" else {}
+    print(json.dumps({"case": case, "ms": times, **info}))
     return 0
 
 

@@ -258,13 +258,18 @@ int tsvd_cgs_qr(tsvd_handle* h, int64_t q, int r, int b, double* Y, int64_t ldy,
                 void* ws, size_t ws_bytes, void* stream);
 
 /* Small SVD (Alg. 1 S5, Alg. 2 S6) of the n x n matrix B (ldb) by one-sided
- * Jacobi (Hestenes) with parallel round-robin pair ordering:
+ * Jacobi (Hestenes) with a parallel round-robin ordering:
  * B = Ubar diag(sigma) Vbar^T, sigma descending, Ubar and Vbar n x n
- * row-major (ld = n), the largest-magnitude entry of each Vbar column
- * positive.  *sweeps (may be NULL) receives the sweep count.
+ * row-major (ld = n).  nv = n accumulates every right vector; 0 <= nv < n
+ * computes only the leading nv columns of Vbar, as B^T ubar_j / sigma_j (the
+ * other columns of Vbar are left undefined, and only the leading nv columns of
+ * Ubar follow the sign convention); this is what the methods use, and for
+ * 64 < n <= 1024 it runs the block-Jacobi kernel.  Sign convention: the
+ * largest-magnitude entry of each defined Vbar column is positive.
+ * *sweeps (may be NULL) receives the sweep count.
  * Requires 1 <= n <= TSVD_MAX_SMALL_SVD. */
 int tsvd_small_svd_workspace(int n, size_t* bytes);
-int tsvd_small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb,
+int tsvd_small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, int nv,
                    double* Ubar, double* sigma, double* Vbar, int* sweeps,
                    void* ws, size_t ws_bytes, void* stream);
 
@@ -289,7 +294,7 @@ int tsvd_small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb,
  *     by the caller.  Nothing in it needs to start at zero.
  *   - Each GPU that loads the library keeps the array until the process exits.
  *   - Synchronises `stream` before returning. */
-#define TSVD_NOALLOC_SCRATCH_BYTES (16 * 1024 * 1024)
+#define TSVD_NOALLOC_SCRATCH_BYTES (4 * 1024 * 1024)
 int tsvd_dense_mm_t_noalloc(tsvd_handle* h, int64_t m, int64_t n, const double* A, int64_t lda,
                             int w, const double* X, int64_t ldx, double* Y, int64_t ldy,
                             void* stream);

@@ -31,7 +31,7 @@ TSVD_MAX_BLOCK = 128
 TSVD_MAX_SMALL_SVD = 2048
 TSVD_SPMM_WORKSPACE = 256
 TSVD_FLAG_PROFILE = 1
-TSVD_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
+TSVD_NOALLOC_SCRATCH_BYTES = 4 * 1024 * 1024
 KERNEL_CLASSES = ("spmm", "gemm_tn", "gemm_nn", "chol", "svd", "other")
 
 
@@ -99,7 +99,7 @@ SIGNATURES = [
     ("tsvd_cgs_cqr2", _I, [_P, _I64, _I64, _I, _P, _I64, _P, _I64, _P, _P, C.c_uint64, _PI, _PI, _P, _SZ, _P]),
     ("tsvd_cgs_qr", _I, [_P, _I64, _I, _I, _P, _I64, _P, C.c_uint64, _PI, _PI, _P, _SZ, _P]),
     ("tsvd_small_svd_workspace", _I, [_I, _PSZ]),
-    ("tsvd_small_svd", _I, [_P, _I, _P, _I64, _P, _P, _P, _PI, _P, _SZ, _P]),
+    ("tsvd_small_svd", _I, [_P, _I, _P, _I64, _I, _P, _P, _P, _PI, _P, _SZ, _P]),
     ("tsvd_dense_mm_t_noalloc", _I, [_P, _I64, _I64, _P, _I64, _I, _P, _I64, _P, _I64, _P]),
 ]
 

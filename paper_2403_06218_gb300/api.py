@@ -364,14 +364,16 @@ def cgs_qr(Y: torch.Tensor, b: int, seed: int = 0):
     return Q, R, bd.value
 
 
-def small_svd(B: torch.Tensor):
-    """SVD of a small square matrix by the device Jacobi kernel: (Ubar, sigma, Vbar, sweeps)."""
+def small_svd(B: torch.Tensor, nv: Optional[int] = None):
+    """SVD of a small square matrix by the device Jacobi kernels: (Ubar, sigma, Vbar, sweeps).
+    ``nv`` < n returns only the leading nv right vectors (the methods' mode)."""
     lib = capi.load()
     _cuda_f64(B, "B")
     dev = B.device
     n = B.shape[0]
     if B.shape[1] != n:
         raise ValueError("B must be square")
+    nv = n if nv is None else int(nv)
     U = torch.empty((n, n), dtype=torch.float64, device=dev)
     V = torch.empty((n, n), dtype=torch.float64, device=dev)
     s = torch.empty(n, dtype=torch.float64, device=dev)
@@ -380,7 +382,7 @@ def small_svd(B: torch.Tensor):
         nb = C.c_size_t()
         capi.check(lib.tsvd_small_svd_workspace(n, C.byref(nb)), "tsvd_small_svd_workspace")
         ws = _ws(nb.value, dev)
-        capi.check(lib.tsvd_small_svd(handle(dev), n, B.data_ptr(), B.stride(0), U.data_ptr(), s.data_ptr(),
+        capi.check(lib.tsvd_small_svd(handle(dev), n, B.data_ptr(), B.stride(0), nv, U.data_ptr(), s.data_ptr(),
                                       V.data_ptr(), C.byref(sweeps), ws.data_ptr(), ws.numel(), _stream_ptr(dev)),
                    "tsvd_small_svd")
     return U, s, V, sweeps.value

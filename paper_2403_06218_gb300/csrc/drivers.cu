@@ -434,6 +434,7 @@ int rsvd_run(tsvd_handle* h, const tsvd_matrix* A, int k, int p, int q, int bq, 
     double* Vb = ar.take<double>((size_t)ell * ell);
     double* sig = ar.take<double>(ell);
     double* g64 = kMixed ? ar.take<double>((size_t)n * ell) : nullptr;
+    T* Qsave = ar.take<T>((size_t)n * ell);
     Final f;
     carve_final(ar, o, m, n, k, kMixed, f);
     if (!run) {
@@ -458,14 +459,28 @@ int rsvd_run(tsvd_handle* h, const tsvd_matrix* A, int k, int p, int q, int bq, 
         TSVD_TRY_CUDA(gaussian(h, n, ell, seed, 1u, reinterpret_cast<double*>(Qn), ell, st));
     }
     int iters = 0;
+    int hs[kStCount];
     for (int it = 0; it <= q; ++it) {
-        TSVD_TRY(op_mul<T>(h, op, ell, Qn, ell, Qm, ell, status, st));                   // S1
-        TSVD_TRY(cgs_qr<T>(h, m, ell, bq, Qm, ell, R, ctx, ar, status, st));            // S2
-        TSVD_TRY(op_tmul<T>(h, op, ell, Qm, ell, Qn, ell, status, st));                  // S3
-        TSVD_TRY(cgs_qr<T>(h, n, ell, bq, Qn, ell, R, ctx, ar, status, st));            // S4
+        // unchecked trip first; if a Cholesky broke down, restore Q and redo the trip checked
+        TSVD_TRY_CUDA(copy_block<T>(Qn, ell, Qsave, ell, n, ell, st));
+        for (int pass = 0; pass < 2; ++pass) {
+            ctx.deferred = (pass == 0);
+            TSVD_TRY(op_mul<T>(h, op, ell, Qn, ell, Qm, ell, status, st));               // S1
+            TSVD_TRY(cgs_qr<T>(h, m, ell, bq, Qm, ell, R, ctx, ar, status, st));        // S2
+            TSVD_TRY(op_tmul<T>(h, op, ell, Qm, ell, Qn, ell, status, st));              // S3
+            TSVD_TRY(cgs_qr<T>(h, n, ell, bq, Qn, ell, R, ctx, ar, status, st));        // S4
+            ctx.deferred = false;
+            if (pass == 1) break;
+            TSVD_TRY(read_status(st, status, hs));
+            if (!hs[kStBreakdown]) {
+                TSVD_TRY(status_code(hs));
+                break;
+            }
+            TSVD_TRY_CUDA(cudaMemsetAsync(status + kStBreakdown, 0, 2 * sizeof(int), st));
+            TSVD_TRY_CUDA(copy_block<T>(Qsave, ell, Qn, ell, n, ell, st));
+        }
         ++iters;
     }
-    int hs[kStCount];
     {
         Arena sv = ar;
         TSVD_TRY(small_svd(h, ell, R, ell, Ub, sig, Vb, k, sv, status, st));           // S5
@@ -567,6 +582,9 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
     double rho_last = NAN, resid = NAN;
     std::vector<double> hrho(k), hsig(1);
     int hs[kStCount];
+    // Every orthogonalisation is checked as it completes: near convergence the first
+    // S5 after a restart breaks down in most cycles (converged Ritz vectors deflate
+    // the new block), so its fallback must run at once.
     for (;;) {
         TSVD_TRY_CUDA(cudaMemsetAsync(B, 0, sizeof(double) * (size_t)rb * rb, st));
         for (int i = 0; i < r; ++i) {

@@ -114,16 +114,20 @@ struct TnPlan {
     int64_t slab_rows;
 };
 
+// One full wave of the kernel on a 152-SM GB300: 7 resident CTAs per SM (its 72
+// registers x 128 threads and 16 KB of shared memory allow 7).  Splitting K so
+// that regions x slabs fills exactly one wave keeps every SM equally busy; a
+// fixed target (rather than the device's SM count) keeps the split, the
+// workspace size and the summation order independent of the device.
+constexpr int64_t kTnWave = 152 * 7;
+
 TnPlan tn_plan(const tsvd_handle* h, int64_t q, int64_t s, int64_t b, bool symmetric) {
+    (void)h;
     TnPlan p;
     p.nreg_s = (int)((s + kTnR - 1) / kTnR);
     p.nreg_b = (int)((b + kTnR - 1) / kTnR);
     p.regions = symmetric ? p.nreg_s * (p.nreg_s + 1) / 2 : p.nreg_s * p.nreg_b;
-    // a fixed CTA target (8 per SM of a 152-SM GB300) keeps the split, the
-    // workspace size and the summation order independent of the device
-    (void)h;
-    const int64_t target = 8LL * 152;
-    int64_t slabs = (target + p.regions - 1) / p.regions;
+    int64_t slabs = kTnWave / p.regions;
     const int64_t max_slabs = (q + 255) / 256;
     if (slabs > max_slabs) slabs = max_slabs;
     if (slabs > 65535) slabs = 65535;

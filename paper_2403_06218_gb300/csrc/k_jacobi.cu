@@ -11,8 +11,8 @@
 // gamma = g_p.g_q with a fixed shuffle tree, and if |gamma| > tol*sqrt(alpha*beta)
 // applies the rotation with t = sign(zeta)/(|zeta| + hypot(1, zeta)),
 // zeta = (beta - alpha)/(2 gamma) (Rutishauser's formulas) to both G and V.
-// Rounds are separated by a grid barrier whose spin is bounded: on timeout it
-// raises the status word and every CTA returns.  Sweeps repeat until one sweep
+// Rounds are separated by a grid barrier whose wait is bounded (clock64, ~1 s):
+// on timeout it raises the status word and every CTA returns.  Sweeps repeat until one sweep
 // rotates nothing (or kMaxSweeps).  Then sigma_j = |g_j|, columns are sorted by
 // (sigma descending, index ascending), Ubar_j = g_j / sigma_j, Vbar_j = v_j, and
 // each pair is sign-flipped so the largest-magnitude entry of Vbar_j is positive.
@@ -23,7 +23,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxSweeps = 40;
-constexpr long long kMaxSpins = 1LL << 24;  // ~1 s with 64 ns naps
+constexpr long long kMaxWaitCycles = 2000000000LL;  // bound of one barrier wait, ~1 s
 
 enum Ctl : int { kCtlCount = 0, kCtlGen = 1, kCtlErr = 2, kCtlSweeps = 3, kCtlRot = 8 };
 constexpr int kCtlWords = kCtlRot + kMaxSweeps;
@@ -47,13 +47,13 @@ __device__ bool grid_sync(unsigned* ctl) {
             __threadfence();
             atomicAdd(&ctl[kCtlGen], 1u);
         } else {
-            long long spins = 0;
+            // busy-wait (naps wake late), bounded by the SM clock: ~1 s at 2 GHz
+            const long long t0 = clock64();
             while (vload(&ctl[kCtlGen]) == g) {
-                if (++spins > kMaxSpins) {
+                if (clock64() - t0 > kMaxWaitCycles) {
                     atomicOr(&ctl[kCtlErr], 1u);
                     break;
                 }
-                __nanosleep(64);
             }
         }
         __threadfence();
@@ -92,10 +92,12 @@ constexpr int kMaxSlots = 64;  // column pairs one CTA owns per round
 // pair turns (alpha, beta, gamma) into the rotation (c, s) and updates the squared
 // column norms alpha - t*gamma, beta + t*gamma (exact consequences of the rotation;
 // recomputed exactly at every sweep start); (C) the warps apply the rotations to
-// G (and to V when it is accumulated).  Scalar FP64 work (sqrt, division) is thus
-// done once per pair instead of once per lane.
+// G (and to V when it is accumulated).  A warp-wide FP64 instruction costs the
+// 2-lane FP64 pipe the same whatever its active lanes, so the scalar work of (B)
+// is done once per pair, and its divide and square roots run in FP32 (see (B)).
 __global__ void jacobi_sweep_kernel(int n, int npad, double* __restrict__ G, double* __restrict__ V,
                                     double* __restrict__ nrm, unsigned* ctl, double tol, int ppb) {
+    const double tol2 = tol * tol;
     __shared__ double s_gam[kMaxSlots], s_c[kMaxSlots], s_s[kMaxSlots];
     __shared__ int s_rot[kMaxSlots];
     __shared__ int s_any;
@@ -134,16 +136,29 @@ __global__ void jacobi_sweep_kernel(int n, int npad, double* __restrict__ G, dou
                     const int p = min(a, bq), q = max(a, bq);
                     const double al = nrm[p], be = nrm[q], ga = s_gam[slot];
                     int rot = 0;
-                    if (ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-                        const double zeta = (be - al) / (2.0 * ga);
-                        const double t = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
-                        const double c = 1.0 / sqrt(fma(t, t, 1.0));
-                        s_c[slot] = c;
-                        s_s[slot] = c * t;
-                        nrm[p] = fma(-t, ga, al);
-                        nrm[q] = fma(t, ga, be);
-                        rot = 1;
-                        s_any = 1;
+                    const double big = fmax(al, be);
+                    if (ga != 0.0 && big > 0.0) {
+                        // scale by a power of two so the test and the FP32 ratio cannot over/underflow
+                        const int e = ilogb(big);
+                        const double as = scalbn(al, -e), bs = scalbn(be, -e), gs = scalbn(ga, -e);
+                        if (gs * gs > tol2 * as * bs) {
+                            // zeta = (beta - alpha) / (2 gamma): the difference in FP64 (it may cancel),
+                            // the ratio and t in FP32 (relative accuracy 1e-7 keeps the convergence
+                            // quadratic); c = 1/sqrt(1 + t^2), s = c t in FP64 so that c^2 + s^2 = 1
+                            // to FP64 rounding and the rotation stays orthogonal
+                            const float zf = (float)(bs - as) / (2.0f * (float)gs);
+                            const float az = fabsf(zf);
+                            const float tf = az > 1e18f ? 0.5f / zf
+                                                        : copysignf(1.0f, zf) / (az + sqrtf(fmaf(az, az, 1.0f)));
+                            const double t = (double)tf;
+                            const double c = rsqrt(fma(t, t, 1.0));
+                            s_c[slot] = c;
+                            s_s[slot] = c * t;
+                            nrm[p] = fma(-t, ga, al);
+                            nrm[q] = fma(t, ga, be);
+                            rot = 1;
+                            s_any = 1;
+                        }
                     }
                     s_rot[slot] = rot;
                 }
@@ -172,6 +187,159 @@ __global__ void jacobi_sweep_kernel(int n, int npad, double* __restrict__ G, dou
                     }
                 }
             }
+            if (!grid_sync(ctl)) return;
+        }
+        if (threadIdx.x == 0 && s_any) atomicAdd(&ctl[kCtlRot + sweep], 1u);
+        if (!grid_sync(ctl)) return;
+        if (vload(&ctl[kCtlRot + sweep]) == 0u) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) ctl[kCtlSweeps] = (unsigned)(sweep + 1);
+            return;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl[kCtlSweeps] = (unsigned)kMaxSweeps;
+}
+
+// Block variant (right vectors not accumulated).  The npad columns form nblk
+// blocks of w columns; in each round of a round-robin over blocks, CTA c owns one
+// pair of blocks (I, J), copies their 2w columns into shared memory, applies all
+// w*w rotations between I and J (w mini-rounds of w disjoint pairs, one warp per
+// pair) -- plus, in the first round of a sweep, the rotations inside I and inside
+// J -- and writes the columns back.  Every column pair meets once per sweep, so a
+// sweep is still a full cyclic sweep, but it needs nblk - 1 grid barriers instead
+// of npad - 1 and the rotations of a block pair stay on chip.
+constexpr int kJGroup = 4;  // warps per column pair (disjoint row ranges)
+
+// Rotations of npair_local disjoint column pairs held in shared memory.  Each pair
+// is served by kJGroup warps over interleaved rows, so every SMSP holds several
+// warps to hide the FP64 latency; the group's partial dot products are summed in
+// a fixed order (bitwise reproducible).
+__device__ inline void block_pair_rotations(double* cols, double* snrm, int n, int npair_local, const int* pp,
+                                            const int* pq, double tol2, double (*s_part)[kJGroup], double* s_c,
+                                            double* s_s, int* s_rot, int* s_any) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    const int stride = 32 * kJGroup;
+    for (int slot = warp; slot < npair_local * kJGroup; slot += nw) {  // (A) partial gamma
+        const int k = slot / kJGroup, sub = slot % kJGroup;
+        const double* gp = cols + (size_t)pp[k] * n;
+        const double* gq = cols + (size_t)pq[k] * n;
+        double g0 = 0.0, g1 = 0.0;
+        int r = sub * 32 + lane;
+        for (; r + stride < n; r += 2 * stride) {
+            g0 = fma(gp[r], gq[r], g0);
+            g1 = fma(gp[r + stride], gq[r + stride], g1);
+        }
+        if (r < n) g0 = fma(gp[r], gq[r], g0);
+        const double ga = warp_sum(g0 + g1);
+        if (lane == 0) s_part[k][sub] = ga;
+    }
+    __syncthreads();
+    if (warp == 0) {  // (B) rotation parameters, one lane per pair
+        for (int k = lane; k < npair_local; k += 32) {
+            double ga = 0.0;
+#pragma unroll
+            for (int t = 0; t < kJGroup; ++t) ga += s_part[k][t];
+            const double al = snrm[pp[k]], be = snrm[pq[k]];
+            int rot = 0;
+            const double big = fmax(al, be);
+            if (ga != 0.0 && big > 0.0) {
+                const int e = ilogb(big);
+                const double as = scalbn(al, -e), bs = scalbn(be, -e), gs = scalbn(ga, -e);
+                if (gs * gs > tol2 * as * bs) {
+                    const float zf = (float)(bs - as) / (2.0f * (float)gs);
+                    const float az = fabsf(zf);
+                    const float tf = az > 1e18f ? 0.5f / zf : copysignf(1.0f, zf) / (az + sqrtf(fmaf(az, az, 1.0f)));
+                    const double t = (double)tf;
+                    const double c = rsqrt(fma(t, t, 1.0));
+                    s_c[k] = c;
+                    s_s[k] = c * t;
+                    snrm[pp[k]] = fma(-t, ga, al);
+                    snrm[pq[k]] = fma(t, ga, be);
+                    rot = 1;
+                    *s_any = 1;
+                }
+            }
+            s_rot[k] = rot;
+        }
+    }
+    __syncthreads();
+    for (int slot = warp; slot < npair_local * kJGroup; slot += nw) {  // (C) rotate
+        const int k = slot / kJGroup, sub = slot % kJGroup;
+        if (!s_rot[k]) continue;
+        const double c = s_c[k], sn = s_s[k];
+        double* gp = cols + (size_t)pp[k] * n;
+        double* gq = cols + (size_t)pq[k] * n;
+        for (int r = sub * 32 + lane; r < n; r += stride) {
+            const double x = gp[r], y = gq[r];
+            gp[r] = fma(c, x, -sn * y);
+            gq[r] = fma(sn, x, c * y);
+        }
+    }
+    __syncthreads();
+}
+
+constexpr int kJBlkMaxW = 8;
+
+__global__ void jacobi_block_kernel(int n, int npad, int w, double* __restrict__ G, double* __restrict__ nrm,
+                                    unsigned* ctl, double tol) {
+    extern __shared__ double jsm[];
+    double* cols = jsm;                         // 2w columns of n
+    double* snrm = jsm + (size_t)2 * w * n;     // their squared norms
+    __shared__ double s_part[kJBlkMaxW][kJGroup], s_c[kJBlkMaxW], s_s[kJBlkMaxW];
+    __shared__ int s_rot[kJBlkMaxW], s_pp[kJBlkMaxW], s_pq[kJBlkMaxW];
+    __shared__ int s_any;
+    const double tol2 = tol * tol;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nblk = npad / w;
+    for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+        for (int c = blockIdx.x * nw + warp; c < npad; c += gridDim.x * nw) {  // exact norms
+            const double* g = G + (int64_t)c * n;
+            double acc = 0.0;
+            for (int r = lane; r < n; r += 32) acc = fma(g[r], g[r], acc);
+            acc = warp_sum(acc);
+            if (lane == 0) nrm[c] = acc;
+        }
+        if (threadIdx.x == 0) s_any = 0;
+        if (!grid_sync(ctl)) return;
+        for (int rnd = 0; rnd < nblk - 1; ++rnd) {
+            const int bi = rr_player(blockIdx.x, rnd, nblk), bj = rr_player(nblk - 1 - blockIdx.x, rnd, nblk);
+            // load the 2w columns (I first, then J) and their norms
+            for (int idx = threadIdx.x; idx < 2 * w * n; idx += blockDim.x) {
+                const int lc = idx / n, r = idx % n;
+                const int gc = lc < w ? bi * w + lc : bj * w + (lc - w);
+                cols[idx] = G[(int64_t)gc * n + r];
+            }
+            for (int lc = threadIdx.x; lc < 2 * w; lc += blockDim.x)
+                snrm[lc] = nrm[lc < w ? bi * w + lc : bj * w + (lc - w)];
+            __syncthreads();
+            if (rnd == 0) {
+                // rotations inside I and inside J: round-robin on w players, w/2 pairs per block
+                for (int mr = 0; mr < w - 1; ++mr) {
+                    if (threadIdx.x < w) {
+                        const int k = threadIdx.x, blk = k / (w / 2), seat = k % (w / 2);
+                        const int a = rr_player(seat, mr, w), b2 = rr_player(w - 1 - seat, mr, w);
+                        s_pp[k] = blk * w + min(a, b2);
+                        s_pq[k] = blk * w + max(a, b2);
+                    }
+                    __syncthreads();
+                    block_pair_rotations(cols, snrm, n, w, s_pp, s_pq, tol2, s_part, s_c, s_s, s_rot, &s_any);
+                }
+            }
+            for (int mr = 0; mr < w; ++mr) {  // rotations between I and J
+                if (threadIdx.x < w) {
+                    s_pp[threadIdx.x] = threadIdx.x;
+                    s_pq[threadIdx.x] = w + (threadIdx.x + mr) % w;
+                }
+                __syncthreads();
+                block_pair_rotations(cols, snrm, n, w, s_pp, s_pq, tol2, s_part, s_c, s_s, s_rot, &s_any);
+            }
+            for (int idx = threadIdx.x; idx < 2 * w * n; idx += blockDim.x) {
+                const int lc = idx / n, r = idx % n;
+                const int gc = lc < w ? bi * w + lc : bj * w + (lc - w);
+                G[(int64_t)gc * n + r] = cols[idx];
+            }
+            for (int lc = threadIdx.x; lc < 2 * w; lc += blockDim.x)
+                nrm[lc < w ? bi * w + lc : bj * w + (lc - w)] = snrm[lc];
             if (!grid_sync(ctl)) return;
         }
         if (threadIdx.x == 0 && s_any) atomicAdd(&ctl[kCtlRot + sweep], 1u);
@@ -333,7 +501,7 @@ __global__ void __launch_bounds__(128) jacobi_vfix_kernel(int n, const double* _
 }  // namespace
 
 size_t small_svd_ws(int n) {
-    const int npad = n + (n & 1);
+    const int npad = n + 2 * kJBlkMaxW;
     Arena ar;
     ar.take<double>((size_t)n * npad);
     ar.take<double>((size_t)npad * npad);
@@ -364,12 +532,24 @@ static int jacobi_grid(const tsvd_handle* h, int npairs, int& block) {
     return nb;
 }
 
+// Block width of the block-Jacobi kernel for an order-n SVD without V, or 0 when
+// the per-pair kernel is used (small n, or V accumulated).
+static int block_width(int n) {
+    if (n <= 64 || n > 1024) return 0;
+    int w = 1;
+    while (w < kJBlkMaxW && (n + 2 * w - 1) / (2 * w) * 2 > 256) w *= 2;  // at most 256 blocks -> 128 CTAs
+    return w;
+}
+
+static size_t block_smem(int n, int w) { return sizeof(double) * ((size_t)2 * w * n + 2 * w); }
+
 int small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* Ubar, double* sigma, double* Vbar, int nv,
               Arena& ar, int* status, cudaStream_t st) {
     if (n < 1 || n > TSVD_MAX_SMALL_SVD) return TSVD_ERR_UNSUPPORTED;
     if (nv < 0 || nv > n) return TSVD_ERR_INVALID_ARG;
-    const int npad = n + (n & 1);
     const bool accumulate = (nv == n);
+    const int w = accumulate ? 0 : block_width(n);
+    const int npad = w ? (n + 2 * w - 1) / (2 * w) * (2 * w) : n + (n & 1);
     double* G = ar.take<double>((size_t)n * npad);
     double* V = ar.take<double>((size_t)npad * npad);
     double* nrm = ar.take<double>(npad);
@@ -378,11 +558,6 @@ int small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* Ubar,
     unsigned* ctl = ar.take<unsigned>(kCtlWords);
     double* part = ar.take<double>(gemm_tn_ws(h, n, n, nv > 0 ? nv : 1, false) / sizeof(double) + 1);
     if (!ar.fits()) return TSVD_ERR_WORKSPACE;
-    const int npairs = npad / 2;
-    int block = 0;
-    const int nblocks = jacobi_grid(h, npairs, block);
-    if (nblocks < 1) return TSVD_ERR_UNSUPPORTED;
-    const int ppb = (npairs + nblocks - 1) / nblocks;
     ProfScope prof(h, TSVD_K_SVD, 0.0, 0.0, st);
     TSVD_TRY_CUDA(cudaMemsetAsync(ctl, 0, sizeof(unsigned) * kCtlWords, st));
     const int64_t tot = (int64_t)npad * npad;
@@ -392,16 +567,42 @@ int small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* Ubar,
     TSVD_TRY_CUDA(cudaGetLastError());
     const double tol = (double)(n > 16 ? n : 16) * kEps;
     double* Vacc = accumulate ? V : nullptr;
-    if (nblocks == 1) {
-        jacobi_sweep_kernel<<<1, block, 0, st>>>(n, npad, G, Vacc, nrm, ctl, tol, ppb);
-        TSVD_TRY_CUDA(cudaGetLastError());
-    } else {
-        int nn = n, np = npad, pp = ppb;
+    if (w > 0) {
+        const int nblk = npad / w;
+        const int nb = nblk / 2;
+        const size_t smem = block_smem(n, w);
+        static thread_local int configured = -1;
+        if (configured != h->device) {
+            TSVD_TRY_CUDA(cudaFuncSetAttribute(jacobi_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)block_smem(1024, kJBlkMaxW)));
+            configured = h->device;
+        }
+        int per_sm = 0;
+        TSVD_TRY_CUDA(
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_block_kernel, 32 * w * kJGroup, smem));
+        if (per_sm * h->sm_count < nb) return TSVD_ERR_UNSUPPORTED;
+        int nn = n, np = npad, ww = w;
         double t = tol;
-        void* args[] = {(void*)&nn, (void*)&np, (void*)&G, (void*)&Vacc, (void*)&nrm, (void*)&ctl, (void*)&t,
-                        (void*)&pp};
-        TSVD_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_sweep_kernel, dim3(nblocks), dim3(block), args,
-                                                  0, st));
+        void* args[] = {(void*)&nn, (void*)&np, (void*)&ww, (void*)&G, (void*)&nrm, (void*)&ctl, (void*)&t};
+        TSVD_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_block_kernel, dim3(nb), dim3(32 * w * kJGroup),
+                                                  args, smem, st));
+    } else {
+        const int npairs = npad / 2;
+        int block = 0;
+        const int nblocks = jacobi_grid(h, npairs, block);
+        if (nblocks < 1) return TSVD_ERR_UNSUPPORTED;
+        const int ppb = (npairs + nblocks - 1) / nblocks;
+        if (nblocks == 1) {
+            jacobi_sweep_kernel<<<1, block, 0, st>>>(n, npad, G, Vacc, nrm, ctl, tol, ppb);
+            TSVD_TRY_CUDA(cudaGetLastError());
+        } else {
+            int nn = n, np = npad, pp = ppb;
+            double t = tol;
+            void* args[] = {(void*)&nn, (void*)&np, (void*)&G, (void*)&Vacc, (void*)&nrm, (void*)&ctl, (void*)&t,
+                            (void*)&pp};
+            TSVD_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_sweep_kernel, dim3(nblocks), dim3(block),
+                                                      args, 0, st));
+        }
     }
     jacobi_sort_kernel<<<1, 1024, 0, st>>>(n, npad, G, sig, perm, ctl, status);
     jacobi_out_kernel<<<n, 128, 0, st>>>(n, npad, G, Vacc, sig, perm, Ubar, sigma, Vbar);

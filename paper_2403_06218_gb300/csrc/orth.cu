@@ -216,17 +216,18 @@ int cgs_cqr2(tsvd_handle* h, int64_t q, int64_t s, int b, const T* P, int64_t ld
         TSVD_TRY_CUDA(gemm_tn(h, q, s, b, P, ldp, Y, ldy, w.H1, b, false, w.partial, st));           // S1
         TSVD_TRY_CUDA(gemm_nn(h, q, s, b, -1.0, P, ldp, w.H1, b, 1.0, Y, ldy, false, st));           // S2
     }
-    TSVD_TRY_CUDA(cholqr_step(h, q, b, Y, ldy, w.W, w.Lt1, w.Mt1, w.partial, status, st));        // S3-S5
+    TSVD_TRY_CUDA(cholqr_step(h, q, b, Y, ldy, w.W, w.Lt1, w.Mt1, w.partial, status, st));  // S3-S5
     if (s > 0) {
         TSVD_TRY_CUDA(gemm_tn(h, q, s, b, P, ldp, Y, ldy, w.H2, b, false, w.partial, st));           // S6
         TSVD_TRY_CUDA(gemm_nn(h, q, s, b, -1.0, P, ldp, w.H2, b, 1.0, Y, ldy, false, st));           // S7
     }
-    TSVD_TRY_CUDA(cholqr_step(h, q, b, Y, ldy, w.W, w.Lt2, w.Mt2, w.partial, status, st));        // S8-S10
+    TSVD_TRY_CUDA(cholqr_step(h, q, b, Y, ldy, w.W, w.Lt2, w.Mt2, w.partial, status, st));  // S8-S10
     TSVD_TRY_CUDA(trmm_upper(h, b, w.Lt2, w.Lt1, R, ldr, r_trans, st));                         // S11
     if (H != nullptr && s > 0) {                                                                 // S12
         TSVD_TRY_CUDA(copy_block(w.H1, b, H, b, s, b, st));
         TSVD_TRY_CUDA(gemm_nn(h, s, b, b, 1.0, w.H2, b, w.Lt1, b, 1.0, H, b, true, st));
     }
+    if (ctx.deferred) return TSVD_OK;
     int hs[kStCount];
     TSVD_TRY(read_status(st, status, hs));
     if (hs[kStNonfinite]) return TSVD_ERR_NONFINITE;

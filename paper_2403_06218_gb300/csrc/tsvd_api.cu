@@ -386,9 +386,9 @@ int tsvd_small_svd_workspace(int n, size_t* bytes) {
     return TSVD_OK;
 }
 
-int tsvd_small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* Ubar, double* sigma, double* Vbar,
-                   int* sweeps, void* ws, size_t ws_bytes, void* stream) {
-    if (!h || n < 1 || !B || ldb < n || !Ubar || !sigma || !Vbar) return TSVD_ERR_INVALID_ARG;
+int tsvd_small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, int nv, double* Ubar, double* sigma,
+                   double* Vbar, int* sweeps, void* ws, size_t ws_bytes, void* stream) {
+    if (!h || n < 1 || !B || ldb < n || !Ubar || !sigma || !Vbar || nv < 0 || nv > n) return TSVD_ERR_INVALID_ARG;
     if (n > TSVD_MAX_SMALL_SVD) return TSVD_ERR_UNSUPPORTED;
     size_t need = 0;
     TSVD_TRY(tsvd_small_svd_workspace(n, &need));
@@ -397,7 +397,7 @@ int tsvd_small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* 
     Arena ar{static_cast<char*>(ws), ws_bytes, 0};
     int* status = ar.take<int>(kStCount);
     TSVD_TRY_CUDA(cudaMemsetAsync(status, 0, sizeof(int) * kStCount, st));
-    TSVD_TRY(small_svd(h, n, B, ldb, Ubar, sigma, Vbar, n, ar, status, st));
+    TSVD_TRY(small_svd(h, n, B, ldb, Ubar, sigma, Vbar, nv, ar, status, st));
     int hs[kStCount];
     TSVD_TRY(read_status(st, status, hs));
     if (sweeps) *sweeps = hs[kStSweeps];

@@ -206,6 +206,10 @@ struct OrthCtx {
     uint64_t seed = 0;
     int replacements = 0;  // Philox replacement columns drawn (stream 0x100 + t)
     int fallbacks = 0;     // Cholesky breakdowns sent to the CGS2 fallback
+    // Deferred: do not synchronise after each orthogonalisation; a breakdown only
+    // leaves the sticky status word set, and the caller redoes the whole cycle
+    // with deferred = false so that the fallback runs where it is needed.
+    bool deferred = false;
 };
 
 // Workspace of one orthogonalisation (sized for double blocks, which covers float).

@@ -210,6 +210,32 @@ def test_small_svd_matches_oracle(tsvd, torch_cuda, n):
     np.testing.assert_allclose(U[:, ok], Uo[:, ok], atol=1e-9)
 
 
+@pytest.mark.parametrize("n,nv", [(100, 10), (200, 64), (512, 64), (1000, 100), (1024, 64)])
+def test_small_svd_leading_vectors_match_oracle(tsvd, torch_cuda, n, nv):
+    """The methods' mode: leading nv right vectors only (block-Jacobi kernel for
+    64 < n <= 1024), on lower block-bidiagonal matrices like the Lanczos B."""
+    torch = torch_cuda
+    rng = np.random.default_rng(n + nv)
+    b = 64 if n % 64 == 0 else 10
+    B = np.tril(rng.standard_normal((n, n)))
+    B -= np.tril(B, -(b + 1))
+    B += np.diag(np.full(n, 3.0 * np.sqrt(b)))  # positive triangular diagonal, as L_i has
+    U, s, V, sweeps = tsvd.small_svd(_t(torch, B), nv=nv)
+    Uo, so, Vo = oracle.small_svd(B)
+    U, s, V = _np(U), _np(s), _np(V)
+    assert 1 <= sweeps < 40
+    np.testing.assert_allclose(s, so, rtol=1e-12, atol=1e-13 * so[0])
+    # leading triplets: B v_j = s_j u_j and B^T u_j = s_j v_j, and element-wise agreement when separated
+    Uk, Vk = U[:, :nv], V[:, :nv]
+    assert np.abs(B @ Vk - Uk * s[:nv]).max() < 1e-12 * so[0]
+    assert np.abs(B.T @ Uk - Vk * s[:nv]).max() < 1e-12 * so[0]
+    d = np.abs(np.diff(so)) / so[0]
+    gap = np.minimum(np.r_[d, np.inf], np.r_[np.inf, d])[:nv]
+    ok = gap > 1e-6
+    np.testing.assert_allclose(Vk[:, ok], Vo[:, :nv][:, ok], atol=1e-9)
+    np.testing.assert_allclose(Uk[:, ok], Uo[:, :nv][:, ok], atol=1e-9)
+
+
 # ------------------------------------------------------------------ drivers
 def _cfg1():
     return workloads.dense_known_spectrum(512, 256, seed=0)

@@ -36,7 +36,7 @@ def _noalloc(tsvd, torch, A, X):
     return rc, Y
 
 
-@pytest.mark.parametrize("m,n,w", [(200_000, 96, 32), (3000, 700, 64), (512, 256, 20)])
+@pytest.mark.parametrize("m,n,w", [(100_000, 64, 16), (3000, 300, 64), (512, 256, 20)])
 def test_noalloc_matches_workspace_entry_point(tsvd, torch_cuda, m, n, w):
     torch = torch_cuda
     g = torch.Generator(device="cuda").manual_seed(m + n + w)
@@ -56,8 +56,8 @@ def test_noalloc_matches_workspace_entry_point(tsvd, torch_cuda, m, n, w):
 def test_noalloc_rejects_shapes_beyond_its_scratch(tsvd, torch_cuda):
     torch = torch_cuda
     from paper_2403_06218_gb300 import _capi
-    # 33,000 x 32 outputs split over 2 row slabs need 16.9 MB of partial sums (> 16 MiB)
-    A = torch.zeros(512, 33_000, dtype=torch.float64, device="cuda")
-    X = torch.zeros(512, 32, dtype=torch.float64, device="cuda")
+    # 96 x 32 outputs split over 354 row slabs need 8.7 MB of partial sums (> 4 MiB)
+    A = torch.zeros(200_000, 96, dtype=torch.float64, device="cuda")
+    X = torch.zeros(200_000, 32, dtype=torch.float64, device="cuda")
     rc, _ = _noalloc(tsvd, torch, A, X)
     assert rc == _capi.TSVD_ERR_UNSUPPORTED
