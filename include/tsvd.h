@@ -223,6 +223,14 @@ int tsvd_dense_mm(tsvd_handle* h, int trans, int64_t m, int64_t n, const double*
                   int w, const double* X, int64_t ldx, double* Y, int64_t ldy,
                   void* ws, size_t ws_bytes, void* stream);
 
+/* The same products in FP32 (the mixed-precision form's kernels): A, X and Y
+ * float32, products accumulated in FP32 within a row slab, and for trans = 1
+ * the slabs' partial sums added in FP64 in a fixed order.  The workspace is
+ * the one tsvd_dense_mm_workspace reports (it covers both element types). */
+int tsvd_dense_mm_f32(tsvd_handle* h, int trans, int64_t m, int64_t n, const float* A, int64_t lda,
+                      int w, const float* X, int64_t ldx, float* Y, int64_t ldy,
+                      void* ws, size_t ws_bytes, void* stream);
+
 /* Workspace bytes for the orthogonalisation entry points below on a q-row
  * block of width b against s earlier columns. */
 int tsvd_orth_workspace(int64_t q, int64_t s, int b, size_t* bytes);

@@ -94,6 +94,7 @@ SIGNATURES = [
     ("tsvd_spmm", _I, [_P, _I64, _I64, _I64, _P, _P, _P, _I, _P, _I64, _P, _I64, _P, _SZ, _P]),
     ("tsvd_dense_mm_workspace", _I, [_I, _I64, _I64, _I, _PSZ]),
     ("tsvd_dense_mm", _I, [_P, _I, _I64, _I64, _P, _I64, _I, _P, _I64, _P, _I64, _P, _SZ, _P]),
+    ("tsvd_dense_mm_f32", _I, [_P, _I, _I64, _I64, _P, _I64, _I, _P, _I64, _P, _I64, _P, _SZ, _P]),
     ("tsvd_orth_workspace", _I, [_I64, _I64, _I, _PSZ]),
     ("tsvd_cholqr2", _I, [_P, _I64, _I, _P, _I64, _P, C.c_uint64, _PI, _PI, _P, _SZ, _P]),
     ("tsvd_cgs_cqr2", _I, [_P, _I64, _I64, _I, _P, _I64, _P, _I64, _P, _P, C.c_uint64, _PI, _PI, _P, _SZ, _P]),

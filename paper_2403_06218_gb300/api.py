@@ -286,21 +286,28 @@ def spmm(A: CsrMatrix, X: torch.Tensor) -> torch.Tensor:
 
 
 def dense_mm(A: torch.Tensor, X: torch.Tensor, trans: bool = False) -> torch.Tensor:
-    """op(A) X for dense row-major A on the GPU."""
+    """op(A) X for dense row-major A on the GPU: FP64 operands (tsvd_dense_mm), or
+    FP32 operands (tsvd_dense_mm_f32, the mixed-precision form's kernels)."""
     lib = capi.load()
-    _cuda_f64(A, "A")
-    _cuda_f64(X, "X")
+    f32 = A.dtype == torch.float32
+    if f32:
+        for t, name in ((A, "A"), (X, "X")):
+            if not (t.is_cuda and t.dtype == torch.float32 and t.dim() == 2 and t.stride(1) == 1):
+                raise TypeError(f"{name} must be a 2-D float32 CUDA tensor with unit column stride")
+    else:
+        _cuda_f64(A, "A")
+        _cuda_f64(X, "X")
     dev = A.device
     m, n = A.shape
     w = X.shape[1]
-    Y = torch.empty(((n if trans else m), w), dtype=torch.float64, device=dev)
+    Y = torch.empty(((n if trans else m), w), dtype=A.dtype, device=dev)
+    fn, name = (lib.tsvd_dense_mm_f32, "tsvd_dense_mm_f32") if f32 else (lib.tsvd_dense_mm, "tsvd_dense_mm")
     with torch.cuda.device(dev):
         nb = C.c_size_t()
         capi.check(lib.tsvd_dense_mm_workspace(int(trans), m, n, w, C.byref(nb)), "tsvd_dense_mm_workspace")
         ws = _ws(nb.value, dev)
-        capi.check(lib.tsvd_dense_mm(handle(dev), int(trans), m, n, A.data_ptr(), A.stride(0), w, X.data_ptr(),
-                                     X.stride(0), Y.data_ptr(), max(w, 1), ws.data_ptr(), ws.numel(),
-                                     _stream_ptr(dev)), "tsvd_dense_mm")
+        capi.check(fn(handle(dev), int(trans), m, n, A.data_ptr(), A.stride(0), w, X.data_ptr(), X.stride(0),
+                      Y.data_ptr(), max(w, 1), ws.data_ptr(), ws.numel(), _stream_ptr(dev)), name)
     return Y
 
 

@@ -115,8 +115,10 @@ int op_tmul64(tsvd_handle* h, Op<T>& op, int w, const double* X, int64_t ldx, do
 size_t tn_partial_max(tsvd_handle* h, int64_t q, int64_t s, int wmax) {
     size_t pb = 0;
     for (int w = 1; w <= wmax; ++w) {
-        const size_t v = gemm_tn_ws(h, q, s, w, false);
-        if (v > pb) pb = v;
+        for (int eb : {4, 8}) {
+            const size_t v = gemm_tn_ws(h, q, s, w, false, eb);
+            if (v > pb) pb = v;
+        }
     }
     return pb;
 }

@@ -94,19 +94,36 @@ __global__ void __launch_bounds__(128) gemm_tn_kernel(int64_t q, int64_t s, int6
     }
 }
 
-// C[i][j] = sum over slabs (fixed order) of partial[slab][i][j]; symmetric reads
-// the upper element for both halves.
+// C[i][j] = sum over slabs of partial[slab][i][j] in a fixed order: thread
+// (x, y) of a 32 x 8 block sums slabs y, y + 8, ... of element x, then the 8
+// partial sums are added in y order.  Symmetric reads the upper element for both
+// halves.
 template <typename TC>
-__global__ void gemm_tn_reduce_kernel(int64_t s, int64_t b, int slabs, const double* __restrict__ partial,
-                                      int64_t slab_stride, TC* __restrict__ C, int64_t ldc, int symmetric) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= s * b) return;
-    int64_t i = idx / b, j = idx % b;
-    const int64_t ii = (symmetric && i > j) ? j : i;
-    const int64_t jj = (symmetric && i > j) ? i : j;
+__global__ void __launch_bounds__(256) gemm_tn_reduce_kernel(int64_t s, int64_t b, int slabs,
+                                                             const double* __restrict__ partial, int64_t slab_stride,
+                                                             TC* __restrict__ C, int64_t ldc, int symmetric) {
+    __shared__ double red[8][33];
+    const int64_t idx = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    const bool in = idx < s * b;
+    int64_t i = 0, j = 0, src = 0;
+    if (in) {
+        i = idx / b;
+        j = idx % b;
+        const int64_t ii = (symmetric && i > j) ? j : i;
+        const int64_t jj = (symmetric && i > j) ? i : j;
+        src = ii * b + jj;
+    }
     double acc = 0.0;
-    for (int sl = 0; sl < slabs; ++sl) acc += partial[(int64_t)sl * slab_stride + ii * b + jj];
-    C[i * ldc + j] = (TC)acc;
+    if (in)
+        for (int sl = threadIdx.y; sl < slabs; sl += 8) acc += partial[(int64_t)sl * slab_stride + src];
+    red[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y == 0 && in) {
+        double t = red[0][threadIdx.x];
+#pragma unroll
+        for (int y = 1; y < 8; ++y) t += red[y][threadIdx.x];
+        C[i * ldc + j] = (TC)t;
+    }
 }
 
 struct TnPlan {
@@ -114,20 +131,21 @@ struct TnPlan {
     int64_t slab_rows;
 };
 
-// One full wave of the kernel on a 152-SM GB300: 7 resident CTAs per SM (its 72
-// registers x 128 threads and 16 KB of shared memory allow 7).  Splitting K so
-// that regions x slabs fills exactly one wave keeps every SM equally busy; a
-// fixed target (rather than the device's SM count) keeps the split, the
-// workspace size and the summation order independent of the device.
+// One full wave of the kernel on a 152-SM GB300: 7 resident CTAs per SM for the
+// FP64 kernel (its 72 registers x 128 threads and 16 KB of shared memory allow 7),
+// 16 for the 64-thread FP32 kernel.  Splitting K so that regions x slabs fills
+// exactly one wave keeps every SM equally busy; a fixed target (rather than the
+// device's SM count) keeps the split, the workspace size and the summation order
+// independent of the device.
 constexpr int64_t kTnWave = 152 * 7;
+constexpr int64_t kTnWaveF32 = 152 * 16;
 
-TnPlan tn_plan(const tsvd_handle* h, int64_t q, int64_t s, int64_t b, bool symmetric) {
-    (void)h;
+TnPlan tn_plan(int64_t q, int64_t s, int64_t b, bool symmetric, int elem_bytes) {
     TnPlan p;
     p.nreg_s = (int)((s + kTnR - 1) / kTnR);
     p.nreg_b = (int)((b + kTnR - 1) / kTnR);
     p.regions = symmetric ? p.nreg_s * (p.nreg_s + 1) / 2 : p.nreg_s * p.nreg_b;
-    int64_t slabs = kTnWave / p.regions;
+    int64_t slabs = (elem_bytes == 4 ? kTnWaveF32 : kTnWave) / p.regions;
     const int64_t max_slabs = (q + 255) / 256;
     if (slabs > max_slabs) slabs = max_slabs;
     if (slabs > 65535) slabs = 65535;
@@ -452,8 +470,9 @@ int colres_groups(int64_t q) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
-size_t gemm_tn_ws(tsvd_handle* h, int64_t q, int64_t s, int64_t b, bool symmetric) {
-    const TnPlan p = tn_plan(h, q, s, b, symmetric);
+size_t gemm_tn_ws(tsvd_handle* h, int64_t q, int64_t s, int64_t b, bool symmetric, int elem_bytes) {
+    (void)h;
+    const TnPlan p = tn_plan(q, s, b, symmetric, elem_bytes);
     if (p.slabs == 1 && !symmetric) return 0;
     return align256(sizeof(double) * (size_t)p.slabs * (size_t)s * (size_t)b);
 }
@@ -462,7 +481,8 @@ template <typename TI, typename TC>
 cudaError_t gemm_tn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, const TI* X, int64_t ldx, const TI* Z,
                     int64_t ldz, TC* C, int64_t ldc, bool symmetric, double* partial, cudaStream_t st) {
     if (s == 0 || b == 0) return cudaSuccess;
-    const TnPlan p = tn_plan(h, q, s, b, symmetric);
+    constexpr bool kF32 = std::is_same<TI, float>::value;
+    const TnPlan p = tn_plan(q, s, b, symmetric, (int)sizeof(TI));
     if (q == 0) {
         for (int64_t i = 0; i < s; ++i) {
             cudaError_t e = cudaMemsetAsync(C + i * ldc, 0, sizeof(TC) * b, st);
@@ -477,17 +497,26 @@ cudaError_t gemm_tn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, const TI* X
                    (double)sizeof(TI) * (double)q * (symmetric ? b : s + b) + (double)sizeof(TC) * s * b, st);
     if (p.slabs == 1 && !symmetric) {
         h->launches++;
+        if constexpr (kF32)
+            return launch_gemm_tn_f32<TC>(grid, st, q, s, b, X, ldx, Z, ldz, C, ldc, 0, p.slab_rows, 0, p.nreg_s,
+                                          p.nreg_b);
         gemm_tn_kernel<TI, TC><<<grid, 128, 0, st>>>(q, s, b, X, ldx, Z, ldz, C, ldc, 0, p.slab_rows, 0, p.nreg_s,
                                                      p.nreg_b);
         return cudaGetLastError();
     }
     const int64_t stride = s * b;
     h->launches += 2;
-    gemm_tn_kernel<TI, double><<<grid, 128, 0, st>>>(q, s, b, X, ldx, Z, ldz, partial, b, stride, p.slab_rows,
-                                                     symmetric ? 1 : 0, p.nreg_s, p.nreg_b);
+    if constexpr (kF32) {
+        cudaError_t e = launch_gemm_tn_f32<double>(grid, st, q, s, b, X, ldx, Z, ldz, partial, b, stride, p.slab_rows,
+                                                   symmetric ? 1 : 0, p.nreg_s, p.nreg_b);
+        if (e != cudaSuccess) return e;
+    } else {
+        gemm_tn_kernel<TI, double><<<grid, 128, 0, st>>>(q, s, b, X, ldx, Z, ldz, partial, b, stride, p.slab_rows,
+                                                         symmetric ? 1 : 0, p.nreg_s, p.nreg_b);
+    }
     const int64_t tot = s * b;
-    gemm_tn_reduce_kernel<TC><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(s, b, p.slabs, partial, stride, C, ldc,
-                                                                            symmetric ? 1 : 0);
+    gemm_tn_reduce_kernel<TC><<<(unsigned)((tot + 31) / 32), dim3(32, 8), 0, st>>>(s, b, p.slabs, partial, stride, C,
+                                                                                  ldc, symmetric ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -507,6 +536,9 @@ cudaError_t gemm_nn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, double alph
                    (double)sizeof(TX) * q * s + (double)sizeof(TM) * s * b +
                        (double)sizeof(TY) * q * b * (beta != 0.0 ? 2 : 1), st);
     h->launches++;
+    if constexpr (std::is_same<TX, float>::value) {
+        if (b <= 128) return launch_gemm_nn_f32<TM, TY>(st, q, s, b, alpha, X, ldx, M, ldm, beta, Y, ldy, upper);
+    }
     if (b <= 32) {
         gemm_nn_kernel<8, TX, TM, TY><<<grid, 128, 0, st>>>(q, s, b, alpha, X, ldx, M, ldm, beta, Y, ldy, upper ? 1 : 0);
     } else if (b <= 64) {

@@ -80,14 +80,15 @@ OrthWs<T> carve(tsvd_handle* h, Arena& ar, int64_t q, int64_t s, int b) {
     w.H1 = ar.take<double>(sb);
     w.H2 = ar.take<double>(sb);
     // split-K partial sums for every product shape used below (incl. the fallback's widths)
-    size_t pbytes = gemm_tn_ws(h, q, b, b, true);
+    const int eb = (int)sizeof(T);
+    size_t pbytes = gemm_tn_ws(h, q, b, b, true, eb);
     auto upd = [&](size_t v) { if (v > pbytes) pbytes = v; };
     if (s > 0) {
-        upd(gemm_tn_ws(h, q, s, b, false));
-        upd(gemm_tn_ws(h, q, s, 1, false));
+        upd(gemm_tn_ws(h, q, s, b, false, eb));
+        upd(gemm_tn_ws(h, q, s, 1, false, eb));
     }
-    for (int j = 1; j <= b; ++j) upd(gemm_tn_ws(h, q, j, 1, false));
-    upd(gemm_tn_ws(h, q, 1, 1, true));
+    for (int j = 1; j <= b; ++j) upd(gemm_tn_ws(h, q, j, 1, false, eb));
+    upd(gemm_tn_ws(h, q, 1, 1, true, eb));
     w.partial = ar.take<double>(pbytes / sizeof(double) + 1);
     w.save = ar.take<T>((size_t)q * b);
     w.fcol = ar.take<T>((size_t)q);

@@ -7,6 +7,8 @@
 #include <new>
 #include <vector>
 
+#include <algorithm>
+
 #include "tsvd_internal.cuh"
 
 namespace tsvd {
@@ -290,7 +292,7 @@ int tsvd_dense_mm_workspace(int trans, int64_t m, int64_t n, int w, size_t* byte
     hh.sm_count = 152;
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&hh.sm_count, cudaDevAttrMultiProcessorCount, dev);
-    *bytes = trans ? gemm_tn_ws(&hh, m, n, w, false) : 0;
+    *bytes = trans ? std::max(gemm_tn_ws(&hh, m, n, w, false, 8), gemm_tn_ws(&hh, m, n, w, false, 4)) : 0;
     return TSVD_OK;
 }
 
@@ -305,6 +307,21 @@ int tsvd_dense_mm(tsvd_handle* h, int trans, int64_t m, int64_t n, const double*
         TSVD_TRY_CUDA((gemm_tn<double, double>(h, m, n, w, A, lda, X, ldx, Y, ldy, false, static_cast<double*>(ws), st)));
     else
         TSVD_TRY_CUDA((gemm_nn<double, double, double>(h, m, n, w, 1.0, A, lda, X, ldx, 0.0, Y, ldy, false, st)));
+    TSVD_TRY_CUDA(cudaStreamSynchronize(st));
+    return TSVD_OK;
+}
+
+int tsvd_dense_mm_f32(tsvd_handle* h, int trans, int64_t m, int64_t n, const float* A, int64_t lda, int w,
+                      const float* X, int64_t ldx, float* Y, int64_t ldy, void* ws, size_t ws_bytes, void* stream) {
+    if (!h || m < 0 || n < 0 || w < 0 || lda < n || !A || !X || !Y) return TSVD_ERR_INVALID_ARG;
+    if (ldx < w || ldy < w) return TSVD_ERR_INVALID_ARG;
+    size_t need = trans ? gemm_tn_ws(h, m, n, w, false, 4) : 0;
+    TSVD_TRY(check_ws(ws, ws_bytes, need));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (trans)
+        TSVD_TRY_CUDA((gemm_tn<float, float>(h, m, n, w, A, lda, X, ldx, Y, ldy, false, static_cast<double*>(ws), st)));
+    else
+        TSVD_TRY_CUDA((gemm_nn<float, float, float>(h, m, n, w, 1.0, A, lda, X, ldx, 0.0, Y, ldy, false, st)));
     TSVD_TRY_CUDA(cudaStreamSynchronize(st));
     return TSVD_OK;
 }

@@ -5,6 +5,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <type_traits>
 #include <vector>
 
 #include "tsvd.h"
@@ -142,7 +143,16 @@ cudaError_t convert_to_float(tsvd_handle* h, int64_t n, const double* x, float* 
 // symmetric: X == Z and s == b; only the upper half is computed and mirrored.
 // TI in {double, float} is the input and in-slab accumulation type; split-K
 // partial sums are FP64; TC is the output type.
-size_t gemm_tn_ws(tsvd_handle* h, int64_t q, int64_t s, int64_t b, bool symmetric);
+// Split-K scratch of gemm_tn for inputs of elem_bytes (8: FP64 inputs, 4: FP32 inputs).
+size_t gemm_tn_ws(tsvd_handle* h, int64_t q, int64_t s, int64_t b, bool symmetric, int elem_bytes = 8);
+// Register-tiled FP32 kernels (k_f32.cu) behind gemm_tn<float, *> and gemm_nn<float, *, *>.
+template <typename TW>
+cudaError_t launch_gemm_tn_f32(dim3 grid, cudaStream_t st, int64_t q, int64_t s, int64_t b, const float* X,
+                               int64_t ldx, const float* Z, int64_t ldz, TW* out, int64_t ldo, int64_t slab_stride,
+                               int64_t slab_rows, int symmetric, int nreg_s, int nreg_b);
+template <typename TM, typename TY>
+cudaError_t launch_gemm_nn_f32(cudaStream_t st, int64_t q, int64_t s, int64_t b, double alpha, const float* X,
+                               int64_t ldx, const TM* M, int64_t ldm, double beta, TY* Y, int64_t ldy, bool upper);
 template <typename TI, typename TC>
 cudaError_t gemm_tn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, const TI* X, int64_t ldx,
                     const TI* Z, int64_t ldz, TC* C, int64_t ldc, bool symmetric,

@@ -121,6 +121,29 @@ def test_dense_mm_matches_numpy(tsvd, torch_cuda, m, n, w):
     assert np.all(np.abs(Y2 - A.T @ X2) <= 2 * m * EPS * (np.abs(A.T) @ np.abs(X2)))
 
 
+@pytest.mark.parametrize("m,n,w", [(512, 256, 20), (777, 333, 64), (100, 1000, 128), (64, 64, 1),
+                                   (4097, 65, 33), (100_000, 64, 64)])
+def test_dense_mm_f32_within_fp32_bound(tsvd, torch_cuda, m, n, w):
+    """FP32 products (the mixed form's register-tiled kernels) against the exact
+    product of the same FP32 values: |Y - op(A) X| <= (k + 1) u (|op(A)| |X|),
+    u = 2^-24, k the inner dimension (Higham's gamma_k bound for a dot product,
+    plus the final rounding to FP32)."""
+    torch = torch_cuda
+    rng = np.random.default_rng(m + n)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    X1 = rng.standard_normal((n, w)).astype(np.float32)
+    X2 = rng.standard_normal((m, w)).astype(np.float32)
+    Y1 = _np(tsvd.dense_mm(torch.from_numpy(A).cuda(), torch.from_numpy(X1).cuda(), trans=False))
+    Y2 = _np(tsvd.dense_mm(torch.from_numpy(A).cuda(), torch.from_numpy(X2).cuda(), trans=True))
+    assert Y1.dtype == np.float32 and Y2.dtype == np.float32
+    A64 = A.astype(np.float64)
+    u = 2.0 ** -24
+    ref1 = A64 @ X1.astype(np.float64)
+    ref2 = A64.T @ X2.astype(np.float64)
+    assert np.all(np.abs(Y1 - ref1) <= (n + 1) * u * (np.abs(A64) @ np.abs(X1.astype(np.float64))))
+    assert np.all(np.abs(Y2 - ref2) <= (m + 1) * u * (np.abs(A64.T) @ np.abs(X2.astype(np.float64))))
+
+
 # ------------------------------------------------------------------ orthogonalisation
 def _cond_block(rng, q, b, cond):
     U, _ = np.linalg.qr(rng.standard_normal((q, b)))
