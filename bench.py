@@ -39,11 +39,51 @@ WORKLOADS = {
     "dense512-lanczos": dict(kind="dense", m=512, n=256, seed=0, method="blanczos",
                              k=10, b=16, r=4, tol=1e-6, max_restarts=50, oracle_cycles=2),
     "dense512-rsvd": dict(kind="dense", m=512, n=256, seed=0, method="rsvd", k=10, p=10, q=2),
+    # 20,000 x 20,000 dense, sigma_i = 1/(1+i)^1.5, Householder-product factors (built on the device)
+    "dense20k-lanczos": dict(kind="dense-hh", m=20_000, n=20_000, seed=2, method="blanczos",
+                             k=100, b=128, r=4, tol=1e-6, max_restarts=300, oracle_cycles=None),
+    "dense20k-lanczos-mixed": dict(kind="dense-hh", m=20_000, n=20_000, seed=2, method="blanczos",
+                                   k=100, b=128, r=4, tol=1e-6, max_restarts=300, oracle_cycles=None,
+                                   precision="mixed"),
 }
 
 METRIC = "time-to-k-triplets at residual <=1e-6 (s); SpMM/GEMM fraction of HBM/tensor roofline"
 SM_COUNT = 152
 FP64_FLOPS_PER_CLK_PER_SM = 4  # 2 DFMA lanes per SM (measured 2.06 DFMA/clk/SM), 2 flops each
+FP32_FLOPS_PER_CLK_PER_SM = 256  # 128 FFMA lanes per SM, 2 flops each
+
+
+def _roofline(cfg, dom, ms_cls, fl_cls, by_cls, ln_cls):
+    """Bound, achieved and peak of kernel class ``dom`` from its algorithmic flops or
+    bytes and its event-timed duration."""
+    from paper_2403_06218_gb300._capi import KERNEL_CLASSES
+    peaks = _measured_peaks()
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    hbm = float(peaks.get("hbm_gbs", 6790.3))
+    fp64_peak = SM_COUNT * FP64_FLOPS_PER_CLK_PER_SM * mhz * 1e6 / 1e12
+    fp32_peak = SM_COUNT * FP32_FLOPS_PER_CLK_PER_SM * mhz * 1e6 / 1e12
+    mixed = cfg.get("precision") == "mixed"
+    name = KERNEL_CLASSES[dom]
+    t = ms_cls[dom] * 1e-3
+    out = {"kernel": name, "launches": ln_cls[dom], "avg_launch_ms": ms_cls[dom] / max(1, ln_cls[dom]),
+           "flops_per_launch": fl_cls[dom] / max(1, ln_cls[dom]),
+           "bytes_per_launch": by_cls[dom] / max(1, ln_cls[dom]), "traffic": None}
+    hbm_bound = name == "a_products" and (cfg["kind"] == "csr" or mixed)
+    if hbm_bound:
+        ach = by_cls[dom] / t / 1e9 if t > 0 else 0.0
+        out.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
+                   peak_note="MEASURED_PEAKS.json hbm_gbs (of measured)")
+    elif mixed and name in ("gemm_tn", "gemm_nn"):
+        ach = fl_cls[dom] / t / 1e12 if t > 0 else 0.0
+        out.update(bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak,
+                   peak_note="FP32 pipe: 152 SMs x 256 flop/clk x max SM clock (derived)")
+    else:
+        ach = fl_cls[dom] / t / 1e12 if t > 0 else 0.0
+        out.update(bound="alu", achieved=ach, peak=fp64_peak, unit="TFLOP/s", frac=ach / fp64_peak,
+                   peak_note="FP64 pipe: 152 SMs x 4 flop/clk x max SM clock (derived; 1.19 TFLOP/s measured "
+                             "by a DFMA loop)")
+    out["hbm_frac_of_measured"] = (by_cls[dom] / t / 1e9) / hbm if t > 0 else None
+    return out
 
 
 def _measured_peaks():
@@ -58,6 +98,10 @@ def _make_matrix(cfg, rank):
     import workloads
     if cfg["kind"] == "csr":
         return workloads.csr_uniform(cfg["m"], cfg["n"], cfg["d"], seed=cfg["seed"] + rank)
+    if cfg["kind"] == "dense-hh":
+        A, _ = workloads.dense_householder_spectrum_torch(cfg["m"], cfg["n"], seed=cfg["seed"] + rank,
+                                                          device="cuda")
+        return A
     A, _, _, _ = workloads.dense_known_spectrum(cfg["m"], cfg["n"], seed=cfg["seed"] + rank)
     return A
 
@@ -151,6 +195,11 @@ def run_reference(args, cfg):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    if cfg["kind"] == "dense-hh":
+        print(json.dumps({"impl": "reference", "unavailable": "the FP64 oracle is not run on the 20,000 x 20,000 "
+                          "dense workload (its matrix is built on the device; one oracle restart cycle there is "
+                          "minutes of host time)"}), flush=True)
+        return 0
     A = _make_matrix(cfg, 0)
     cores = _cpu_cores()
     if cfg["method"] == "blanczos":
@@ -198,6 +247,22 @@ def run_case(case):
         P = tsvd.cgs_qr(torch.randn(100_000, 960, dtype=torch.float64, device="cuda", generator=g), 128)[0]
         Y = torch.randn(100_000, 64, dtype=torch.float64, device="cuda", generator=g)
         call = lambda: tsvd.cgs_cqr2(Y, P)  # noqa: E731
+    elif case in ("tc", "f32", "f64"):
+        # dense A Q of the 20,000 x 20,000 workload with a 128-column block: split-BF16 tensor
+        # cores (tc), FP32 CUDA cores (f32) or FP64 (f64)
+        A = torch.randn(20_000, 20_000, dtype=torch.float64, device="cuda", generator=g)
+        X = torch.randn(20_000, 128, dtype=torch.float64, device="cuda", generator=g)
+        if case == "tc":
+            P = tsvd.bf16x3_split(A)
+            del A
+            X32 = X.float()
+            call = lambda: tsvd.mm_bf16x6(P, X32)  # noqa: E731
+        elif case == "f32":
+            A32, X32 = A.float(), X.float()
+            del A
+            call = lambda: tsvd.dense_mm(A32, X32)  # noqa: E731
+        else:
+            call = lambda: tsvd.dense_mm(A, X)  # noqa: E731
     else:
         # projected matrix of one restart cycle: 1024 x 1024 lower block bidiagonal (b = 64)
         B = torch.tril(torch.randn(1024, 1024, dtype=torch.float64, device="cuda", generator=g))
@@ -212,6 +277,10 @@ def run_case(case):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     info = {"sweeps": out[3]} if case == "svd" else {}
+    if case in ("tc", "f32", "f64"):
+        best = min(times) * 1e-3
+        info = {"tflops": 2.0 * 20_000 * 20_000 * 128 / best / 1e12,
+                "gbs": {"tc": 6.0, "f32": 4.0, "f64": 8.0}[case] * 20_000 * 20_000 / best / 1e9}
     print(json.dumps({"case": case, "ms": times, **info}))
     return 0
 
@@ -224,7 +293,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--workload", default="sparse100k-lanczos", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default=None, choices=("orth", "svd"),
+    ap.add_argument("--case", default=None, choices=("orth", "svd", "tc", "f32", "f64"),
                     help="run one building block at its benchmark shape (for profiler captures) and exit")
     args = ap.parse_args(argv)
     cfg = WORKLOADS[args.workload]
@@ -255,20 +324,25 @@ def main(argv=None):
         A_dev = tsvd.CsrMatrix.from_scipy(A_host)
         A_pinned = tsvd.CsrMatrix.from_scipy(A_host, device="cpu", pin_memory=True)
         h2d = 12 * A_host.nnz + 4 * (A_host.shape[0] + 1)
+    elif cfg["kind"] == "dense-hh":
+        A_dev = A_host
+        A_pinned = A_dev.cpu().pin_memory()
+        A_host = None  # built on the device; the oracle baseline is not run at this size
+        h2d = 8 * A_dev.numel()
     else:
         A_dev = torch.from_numpy(A_host).cuda()
         A_pinned = torch.from_numpy(A_host).pin_memory()
         h2d = 8 * A_host.size
-    m, n = A_host.shape
+    m, n = cfg["m"], cfg["n"]
     d2h = 8 * (m + n) * cfg["k"] + 8 * cfg["k"]
     seed = cfg["seed"] + rank
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
-    for _ in range(args.warmup):  # profiled too, so the timed steps reuse the library's pooled CUDA events
-        res = _solve(tsvd, cfg, A_dev, seed, profile=True)
+    for i in range(args.warmup):  # the last one profiled, so the library's CUDA event pool is warm
+        res = _solve(tsvd, cfg, A_dev, seed, profile=(i == args.warmup - 1))
     torch.cuda.synchronize()
 
-    # ---- timed region: K solves, A resident in HBM ----
+    # ---- timed region: K solves, A resident in HBM, no per-kernel events ----
     infos = []
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -278,7 +352,7 @@ def main(argv=None):
         e0.record(st)
         for _ in range(args.steps):
             _flush_l2(torch, flush)
-            res = _solve(tsvd, cfg, A_dev, seed, profile=True)
+            res = _solve(tsvd, cfg, A_dev, seed)
             infos.append(res.info)
         e1.record(st)
         torch.cuda.synchronize()
@@ -290,6 +364,16 @@ def main(argv=None):
         ms_total = float(t.item())
     ms_step = ms_total / args.steps
     clocks = clk.summary()
+
+    # ---- the same K solves with CUDA events around every kernel class, on the
+    # launching stream (event recording around each launch slows the host's refill of
+    # the queue after the per-orthogonalisation status reads, so these steps give the
+    # per-kernel durations and the timed steps above give the solve time) ----
+    pinfos = []
+    for _ in range(args.steps):
+        _flush_l2(torch, flush)
+        pinfos.append(_solve(tsvd, cfg, A_dev, seed, profile=True).info)
+    torch.cuda.synchronize()
 
     # ---- end to end through the C ABI with host buffers ----
     e2e_steps = max(1, min(args.steps, 2))
@@ -307,26 +391,20 @@ def main(argv=None):
 
     # ---- roofline of the dominant kernel class (CUDA events on the launching stream) ----
     from paper_2403_06218_gb300._capi import KERNEL_CLASSES
-    ms_cls = [sum(i["prof_ms"][c] for i in infos) for c in range(6)]
-    fl_cls = [sum(i["prof_flops"][c] for i in infos) for c in range(6)]
-    by_cls = [sum(i["prof_bytes"][c] for i in infos) for c in range(6)]
-    ln_cls = [sum(i["prof_launches"][c] for i in infos) for c in range(6)]
+    ms_cls = [sum(i["prof_ms"][c] for i in pinfos) for c in range(6)]
+    fl_cls = [sum(i["prof_flops"][c] for i in pinfos) for c in range(6)]
+    by_cls = [sum(i["prof_bytes"][c] for i in pinfos) for c in range(6)]
+    ln_cls = [sum(i["prof_launches"][c] for i in pinfos) for c in range(6)]
+    ms_prof = sum(i["ms_total"] for i in pinfos)
     dom = max(range(5), key=lambda c: ms_cls[c])
-    peaks = _measured_peaks()
-    fp64_peak = SM_COUNT * FP64_FLOPS_PER_CLK_PER_SM * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-    achieved = fl_cls[dom] / (ms_cls[dom] * 1e-3) / 1e12 if ms_cls[dom] > 0 else 0.0
-    roofline = {
-        "kernel": KERNEL_CLASSES[dom], "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-        "frac": achieved / fp64_peak, "traffic": None,
-        "peak_note": "FP64 pipe: 152 SMs x 4 flop/clk x max SM clock (derived; 1.19 TFLOP/s measured by a DFMA loop)",
-        "launches": ln_cls[dom], "avg_launch_ms": ms_cls[dom] / max(1, ln_cls[dom]),
-        "bytes_per_launch": by_cls[dom] / max(1, ln_cls[dom]),
-        "hbm_frac_of_measured": (by_cls[dom] / (ms_cls[dom] * 1e-3) / 1e9) / float(peaks.get("hbm_gbs", 6790.3))
-        if ms_cls[dom] > 0 else None,
-        "share_of_step": ms_cls[dom] / ms_total,
-        "classes": {KERNEL_CLASSES[c]: {"launches": ln_cls[c], "ms": ms_cls[c], "tflops": (fl_cls[c] / (ms_cls[c] * 1e-3) / 1e12)
-                                        if ms_cls[c] > 0 else None} for c in range(6)},
-    }
+    roofline = _roofline(cfg, dom, ms_cls, fl_cls, by_cls, ln_cls)
+    roofline["share_of_step"] = ms_cls[dom] / ms_prof if ms_prof > 0 else None
+    roofline["profiled_steps"] = len(pinfos)
+    roofline["classes"] = {
+        KERNEL_CLASSES[c]: {"launches": ln_cls[c], "ms": ms_cls[c],
+                            "tflops": fl_cls[c] / (ms_cls[c] * 1e-3) / 1e12 if ms_cls[c] > 0 else None,
+                            "gbs": by_cls[c] / (ms_cls[c] * 1e-3) / 1e9 if ms_cls[c] > 0 else None}
+        for c in range(6)}
 
     line = {
         "metric": METRIC, "value": ms_step / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -336,6 +414,7 @@ def main(argv=None):
                    "parallelism": f"replicas{world}", "l2": "flushed before every step (256 MiB write)"},
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
+        "ms_per_step_profiled": ms_prof / max(1, len(pinfos)),
         "clocks": clocks,
         "roofline": roofline,
         "solve": {"cycles": infos[-1]["iterations"], "restarts": infos[-1]["restarts"],
@@ -343,7 +422,7 @@ def main(argv=None):
                   "svd_sweeps": infos[-1]["svd_sweeps"], "ms_transpose": infos[-1]["ms_transpose"]},
     }
 
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and A_host is not None:
         # the oracle as it stands on the host cores: one restart cycle of the same
         # solve on the full matrix, scaled by the cycles the solve needed
         cycles = int(infos[-1]["iterations"]) if cfg["method"] == "blanczos" else 1

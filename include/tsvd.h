@@ -90,11 +90,14 @@ typedef struct tsvd_matrix {
 #define TSVD_FLAG_PROFILE  1   /* time every kernel class with CUDA events (tsvd_info.prof_*) */
 
 /* Kernel classes reported by TSVD_FLAG_PROFILE (index into tsvd_info.prof_*). */
-#define TSVD_K_SPMM     0   /* CSR SpMM with A or A^T (Table 1 SpMM)                      */
+#define TSVD_K_APROD    0   /* products with A or A^T: CSR SpMM (Table 1 SpMM), dense GEMM
+                               with A, split-BF16 tensor-core products                    */
+#define TSVD_K_SPMM     TSVD_K_APROD
 #define TSVD_K_GEMM_TN  1   /* X^T Z: Gram matrices and projections P^T Q (Algs. 4, 5)    */
 #define TSVD_K_GEMM_NN  2   /* X M: updates Q - P H, Q L^{-T}, Ritz/restart products      */
 #define TSVD_K_CHOL     3   /* Cholesky + triangular inverse of a Gram matrix             */
-#define TSVD_K_SVD      4   /* small Jacobi SVD                                            */
+#define TSVD_K_SVD      4   /* small Jacobi SVD (flops: 12 n per rotation, 18 n with V,
+                               n(n-1)/2 rotations a sweep, times the sweeps it took)    */
 #define TSVD_K_OTHER    5   /* start block, transpose build, residuals, copies            */
 #define TSVD_K_COUNT    6
 
@@ -230,6 +233,31 @@ int tsvd_dense_mm(tsvd_handle* h, int trans, int64_t m, int64_t n, const double*
 int tsvd_dense_mm_f32(tsvd_handle* h, int trans, int64_t m, int64_t n, const float* A, int64_t lda,
                       int w, const float* X, int64_t ldx, float* Y, int64_t ldy,
                       void* ws, size_t ws_bytes, void* stream);
+
+/* Tensor-core products of the mixed form for dense A.  A (or A^T) is stored
+ * once as three BF16 pieces, A = A0 + A1 + A2 to 24 significant bits, and the
+ * block X as three pieces too; Y = sum of the six terms A_i X_j with i + j <= 2
+ * computed by tcgen05 BF16 MMAs with FP32 accumulation.  The dropped terms are
+ * O(2^-24) relative, so Y is as accurate as an FP32 product of the same values
+ * (|Y - P X| <= c u |P| |X| with u = 2^-24 and c a small multiple of the inner
+ * dimension).  These are the products A Q and A^T Q of Alg. 1 S1/S3 and Alg. 2
+ * S2/S4 in the mixed form; the paper itself computes them in FP64.
+ *   tsvd_bf16x3_bytes: bytes of the pieces of a rows x cols matrix (layout
+ *     [3][rows][ld] BF16, ld = cols rounded up to a multiple of 8).
+ *   tsvd_bf16x3_split: pieces of A (trans = 0; rows = m, cols = n) or of A^T
+ *     (trans = 1; rows = n, cols = m) for FP64 A (m x n, lda) into `pieces`
+ *     (device, caller-owned, tsvd_bf16x3_bytes(rows, cols) bytes).
+ *   tsvd_mm_bf16x6: Y (rows x w, ldy, FP32) = P X with P given by its pieces
+ *     (rows x cols) and X (cols x w, ldx, FP32).  Any w >= 0 (done in panels of
+ *     128 columns).  Returns TSVD_ERR_TIMEOUT if a bounded wait in the kernel
+ *     gave up (Y is then undefined).  Synchronises `stream` before returning. */
+int tsvd_bf16x3_bytes(int64_t rows, int64_t cols, size_t* bytes);
+int tsvd_bf16x3_split(tsvd_handle* h, int trans, int64_t m, int64_t n, const double* A, int64_t lda,
+                      void* pieces, void* stream);
+int tsvd_mm_bf16x6_workspace(int64_t rows, int64_t cols, int w, size_t* bytes);
+int tsvd_mm_bf16x6(tsvd_handle* h, int64_t rows, int64_t cols, const void* pieces, int w,
+                   const float* X, int64_t ldx, float* Y, int64_t ldy,
+                   void* ws, size_t ws_bytes, void* stream);
 
 /* Workspace bytes for the orthogonalisation entry points below on a q-row
  * block of width b against s earlier columns. */

@@ -32,7 +32,7 @@ TSVD_MAX_SMALL_SVD = 2048
 TSVD_SPMM_WORKSPACE = 256
 TSVD_FLAG_PROFILE = 1
 TSVD_NOALLOC_SCRATCH_BYTES = 4 * 1024 * 1024
-KERNEL_CLASSES = ("spmm", "gemm_tn", "gemm_nn", "chol", "svd", "other")
+KERNEL_CLASSES = ("a_products", "gemm_tn", "gemm_nn", "chol", "svd", "other")
 
 
 class TsvdMatrix(C.Structure):
@@ -95,6 +95,10 @@ SIGNATURES = [
     ("tsvd_dense_mm_workspace", _I, [_I, _I64, _I64, _I, _PSZ]),
     ("tsvd_dense_mm", _I, [_P, _I, _I64, _I64, _P, _I64, _I, _P, _I64, _P, _I64, _P, _SZ, _P]),
     ("tsvd_dense_mm_f32", _I, [_P, _I, _I64, _I64, _P, _I64, _I, _P, _I64, _P, _I64, _P, _SZ, _P]),
+    ("tsvd_bf16x3_bytes", _I, [_I64, _I64, _PSZ]),
+    ("tsvd_bf16x3_split", _I, [_P, _I, _I64, _I64, _P, _I64, _P, _P]),
+    ("tsvd_mm_bf16x6_workspace", _I, [_I64, _I64, _I, _PSZ]),
+    ("tsvd_mm_bf16x6", _I, [_P, _I64, _I64, _P, _I, _P, _I64, _P, _I64, _P, _SZ, _P]),
     ("tsvd_orth_workspace", _I, [_I64, _I64, _I, _PSZ]),
     ("tsvd_cholqr2", _I, [_P, _I64, _I, _P, _I64, _P, C.c_uint64, _PI, _PI, _P, _SZ, _P]),
     ("tsvd_cgs_cqr2", _I, [_P, _I64, _I64, _I, _P, _I64, _P, _I64, _P, _P, C.c_uint64, _PI, _PI, _P, _SZ, _P]),

@@ -311,6 +311,61 @@ def dense_mm(A: torch.Tensor, X: torch.Tensor, trans: bool = False) -> torch.Ten
     return Y
 
 
+@dataclasses.dataclass
+class Bf16x3:
+    """Three BF16 pieces of a rows x cols matrix (A = A0 + A1 + A2), as stored by
+    tsvd_bf16x3_split: ``data`` is the device buffer [3][rows][ld] (ld = cols
+    rounded up to a multiple of 8)."""
+    data: torch.Tensor
+    rows: int
+    cols: int
+
+    @property
+    def ld(self) -> int:
+        return (self.cols + 7) // 8 * 8
+
+    def pieces(self) -> torch.Tensor:
+        """The pieces as a (3, rows, cols) bfloat16 tensor (a view of ``data``)."""
+        n = 3 * self.rows * self.ld
+        return self.data[: 2 * n].view(torch.bfloat16).view(3, self.rows, self.ld)[:, :, : self.cols]
+
+
+def bf16x3_split(A: torch.Tensor, trans: bool = False) -> Bf16x3:
+    """BF16 pieces of FP64 A (or of A^T) for the tensor-core products."""
+    lib = capi.load()
+    _cuda_f64(A, "A")
+    dev = A.device
+    m, n = A.shape
+    rows, cols = (n, m) if trans else (m, n)
+    nb = C.c_size_t()
+    capi.check(lib.tsvd_bf16x3_bytes(rows, cols, C.byref(nb)), "tsvd_bf16x3_bytes")
+    buf = _ws(nb.value, dev)
+    with torch.cuda.device(dev):
+        capi.check(lib.tsvd_bf16x3_split(handle(dev), int(trans), m, n, A.data_ptr(), A.stride(0), buf.data_ptr(),
+                                         _stream_ptr(dev)), "tsvd_bf16x3_split")
+    return Bf16x3(buf, rows, cols)
+
+
+def mm_bf16x6(P: Bf16x3, X: torch.Tensor) -> torch.Tensor:
+    """Y = P X on the tensor cores (six BF16 cross terms, FP32 accumulation); X FP32."""
+    lib = capi.load()
+    if not (X.is_cuda and X.dtype == torch.float32 and X.dim() == 2 and X.stride(1) == 1):
+        raise TypeError("X must be a 2-D float32 CUDA tensor with unit column stride")
+    if X.shape[0] != P.cols:
+        raise ValueError("X must have P.cols rows")
+    dev = X.device
+    w = X.shape[1]
+    Y = torch.empty((P.rows, w), dtype=torch.float32, device=dev)
+    nb = C.c_size_t()
+    capi.check(lib.tsvd_mm_bf16x6_workspace(P.rows, P.cols, w, C.byref(nb)), "tsvd_mm_bf16x6_workspace")
+    ws = _ws(nb.value, dev)
+    with torch.cuda.device(dev):
+        capi.check(lib.tsvd_mm_bf16x6(handle(dev), P.rows, P.cols, P.data.data_ptr(), w, X.data_ptr(), X.stride(0),
+                                      Y.data_ptr(), max(w, 1), ws.data_ptr(), ws.numel(), _stream_ptr(dev)),
+                   "tsvd_mm_bf16x6")
+    return Y
+
+
 def _orth_ws(q, s, b, dev):
     nb = C.c_size_t()
     capi.check(capi.load().tsvd_orth_workspace(q, s, b, C.byref(nb)), "tsvd_orth_workspace")

@@ -1,7 +1,8 @@
 // RandSVD (Alg. 1) and LancSVD (Alg. 2) on the device, for both precisions:
 //   T = double: the FP64 method of the paper;
 //   T = float : the mixed-precision form.  A and every tall block (Q, Qbar, the
-//               Lanczos bases) are FP32 and the products accumulate in FP32,
+//               Lanczos bases) are FP32 and the products accumulate in FP32
+//               (dense A: split-BF16 tensor-core products of FP32 accuracy),
 //               while every Gram matrix, Cholesky factor, R, B and the small SVD
 //               stay FP64.  The returned triplets come from an FP64 Rayleigh-Ritz
 //               step: the Ritz vectors are re-orthonormalised in FP64, the k x k
@@ -12,6 +13,7 @@
 // breakdown flags after each orthogonalisation, the Lanczos estimate once per
 // cycle, the explicit residual).  When m < n both methods run on A^T and swap U
 // and V on return (Sec. 2).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -63,6 +65,11 @@ struct Op {
     const double* dA64 = nullptr;
     int64_t lda64 = 0;
     double* partial = nullptr;  // split-K scratch of dense A^T X
+    // mixed form, dense A: BF16 pieces of A and of A^T for the tensor-core products
+    bool tc = false;
+    const void* pA = nullptr;
+    const void* pAt = nullptr;
+    void* tcws = nullptr;
 };
 
 // Y (op.m x w) = op(A) X ; in precision TV with values V (sparse) or D (dense).
@@ -77,6 +84,7 @@ int apply(tsvd_handle* h, bool sparse, bool trans_of_A, int64_t M, int64_t N, in
         else
             TSVD_TRY_CUDA(launch_spmm<TV>(h, N, M, nnz, trp, tci, tva, w, X, ldx, Y, ldy, status, st));
     } else {
+        ProfClass pc(h, TSVD_K_APROD);
         if (!trans_of_A)
             TSVD_TRY_CUDA((gemm_nn<TV, TV, TV>(h, M, N, w, 1.0, dA, lda, X, ldx, 0.0, Y, ldy, false, st)));
         else
@@ -89,12 +97,26 @@ int apply(tsvd_handle* h, bool sparse, bool trans_of_A, int64_t M, int64_t N, in
 template <typename T>
 int op_mul(tsvd_handle* h, Op<T>& op, int w, const T* X, int64_t ldx, T* Y, int64_t ldy, int* status,
            cudaStream_t st) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (op.tc) {
+            TSVD_TRY_CUDA(op.transposed ? tc_mm(h, op.N, op.M, op.pAt, w, X, ldx, Y, ldy, op.tcws, status, st)
+                                        : tc_mm(h, op.M, op.N, op.pA, w, X, ldx, Y, ldy, op.tcws, status, st));
+            return TSVD_OK;
+        }
+    }
     return apply<T>(h, op.sparse, op.transposed, op.M, op.N, op.nnz, op.rp, op.ci, op.va, op.trp, op.tci, op.tva,
                     op.dA, op.lda, op.partial, w, X, ldx, Y, ldy, status, st);
 }
 template <typename T>
 int op_tmul(tsvd_handle* h, Op<T>& op, int w, const T* X, int64_t ldx, T* Y, int64_t ldy, int* status,
             cudaStream_t st) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (op.tc) {
+            TSVD_TRY_CUDA(op.transposed ? tc_mm(h, op.M, op.N, op.pA, w, X, ldx, Y, ldy, op.tcws, status, st)
+                                        : tc_mm(h, op.N, op.M, op.pAt, w, X, ldx, Y, ldy, op.tcws, status, st));
+            return TSVD_OK;
+        }
+    }
     return apply<T>(h, op.sparse, !op.transposed, op.M, op.N, op.nnz, op.rp, op.ci, op.va, op.trp, op.tci, op.tva,
                     op.dA, op.lda, op.partial, w, X, ldx, Y, ldy, status, st);
 }
@@ -249,17 +271,25 @@ int setup_op(tsvd_handle* h, const tsvd_matrix* A, int wmax, Arena& ar, Op<T>& o
         if (kF64) {
             op.dA = (const T*)op.dA64;
             op.lda = op.lda64;
-        } else if (!in64) {
-            op.dA = (const T*)a;
-            op.lda = lda;
         } else {
-            T* d = ar.take<T>((size_t)M * N);
+            // mixed form: the products run on the tensor cores from BF16 pieces of A and
+            // A^T (24 significant bits, as many as the FP32 values carry)
+            op.tc = true;
+            void* pa = ar.take<char>(bf16x3_bytes(M, N));
+            void* pat = ar.take<char>(bf16x3_bytes(N, M));
+            op.tcws = ar.take<char>(std::max(tc_mm_ws(M, N, wmax), tc_mm_ws(N, M, wmax)));
             if (run) {
                 if (!ar.fits()) return TSVD_ERR_WORKSPACE;
-                TSVD_TRY_CUDA((convert2d<double, T>(h, M, N, op.dA64, op.lda64, d, N, st)));
+                if (in64) {
+                    TSVD_TRY_CUDA(bf16x3_split<double>(h, M, N, (const double*)a, lda, false, pa, st));
+                    TSVD_TRY_CUDA(bf16x3_split<double>(h, M, N, (const double*)a, lda, true, pat, st));
+                } else {
+                    TSVD_TRY_CUDA(bf16x3_split<float>(h, M, N, (const float*)a, lda, false, pa, st));
+                    TSVD_TRY_CUDA(bf16x3_split<float>(h, M, N, (const float*)a, lda, true, pat, st));
+                }
             }
-            op.dA = d;
-            op.lda = N;
+            op.pA = pa;
+            op.pAt = pat;
         }
         op.partial = ar.take<double>(tn_partial_max(h, M, N, wmax) / sizeof(double) + 1);
     }
@@ -496,6 +526,7 @@ int rsvd_run(tsvd_handle* h, const tsvd_matrix* A, int k, int p, int q, int bq, 
     TSVD_TRY(read_status(st, status, hs));
     TSVD_TRY(status_code(hs));
     const int sweeps = hs[kStSweeps];
+    prof_set_last_flops(h, TSVD_K_SVD, jacobi_flops(ell, k, sweeps));
     TSVD_TRY(finish_outputs<T>(h, o, op, k, dU, dV, dsig, f, sigma, U, V, st));
     const double ms_total = total->stop();
     double resid = NAN;
@@ -614,6 +645,7 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
         TSVD_TRY(read_status(st, status, hs));
         TSVD_TRY(status_code(hs));
         sweeps = hs[kStSweeps];
+        prof_set_last_flops(h, TSVD_K_SVD, jacobi_flops(rb, k > b ? k : b, sweeps));
         double rmax = 0.0;
         for (int j = 0; j < k; ++j) rmax = std::fmax(rmax, hrho[j]);
         rho_last = hsig[0] > 0.0 ? rmax / hsig[0] : NAN;

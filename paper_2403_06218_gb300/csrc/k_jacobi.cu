@@ -515,6 +515,11 @@ size_t small_svd_ws(int n) {
         if (v > part) part = v;
     }
     ar.take<char>(part + sizeof(double));
+    // re-orthonormalisation of the computed right vectors (block CGS-QR, blocks of 128)
+    const int bw = n < TSVD_MAX_BLOCK ? n : TSVD_MAX_BLOCK;
+    ar.take<double>((size_t)n * n);
+    ar.take<double>((size_t)(n - bw) * bw);
+    ar.take<char>(orth_ws(nullptr, n, n - bw, bw));
     return ar.off;
 }
 
@@ -558,61 +563,72 @@ int small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* Ubar,
     unsigned* ctl = ar.take<unsigned>(kCtlWords);
     double* part = ar.take<double>(gemm_tn_ws(h, n, n, nv > 0 ? nv : 1, false) / sizeof(double) + 1);
     if (!ar.fits()) return TSVD_ERR_WORKSPACE;
-    ProfScope prof(h, TSVD_K_SVD, 0.0, 0.0, st);
-    TSVD_TRY_CUDA(cudaMemsetAsync(ctl, 0, sizeof(unsigned) * kCtlWords, st));
-    const int64_t tot = (int64_t)npad * npad;
-    h->launches += 4;
-    jacobi_init_kernel<<<(unsigned)((tot + 255) / 256 < 4096 ? (tot + 255) / 256 : 4096), 256, 0, st>>>(
-        n, npad, B, ldb, G, V);
-    TSVD_TRY_CUDA(cudaGetLastError());
-    const double tol = (double)(n > 16 ? n : 16) * kEps;
-    double* Vacc = accumulate ? V : nullptr;
-    if (w > 0) {
-        const int nblk = npad / w;
-        const int nb = nblk / 2;
-        const size_t smem = block_smem(n, w);
-        static thread_local int configured = -1;
-        if (configured != h->device) {
-            TSVD_TRY_CUDA(cudaFuncSetAttribute(jacobi_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)block_smem(1024, kJBlkMaxW)));
-            configured = h->device;
-        }
-        int per_sm = 0;
-        TSVD_TRY_CUDA(
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_block_kernel, 32 * w * kJGroup, smem));
-        if (per_sm * h->sm_count < nb) return TSVD_ERR_UNSUPPORTED;
-        int nn = n, np = npad, ww = w;
-        double t = tol;
-        void* args[] = {(void*)&nn, (void*)&np, (void*)&ww, (void*)&G, (void*)&nrm, (void*)&ctl, (void*)&t};
-        TSVD_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_block_kernel, dim3(nb), dim3(32 * w * kJGroup),
-                                                  args, smem, st));
-    } else {
-        const int npairs = npad / 2;
-        int block = 0;
-        const int nblocks = jacobi_grid(h, npairs, block);
-        if (nblocks < 1) return TSVD_ERR_UNSUPPORTED;
-        const int ppb = (npairs + nblocks - 1) / nblocks;
-        if (nblocks == 1) {
-            jacobi_sweep_kernel<<<1, block, 0, st>>>(n, npad, G, Vacc, nrm, ctl, tol, ppb);
-            TSVD_TRY_CUDA(cudaGetLastError());
-        } else {
-            int nn = n, np = npad, pp = ppb;
+    {  // the Jacobi sweeps (the right-vector products below are timed as products)
+        ProfScope prof(h, TSVD_K_SVD, 0.0, 0.0, st);
+        TSVD_TRY_CUDA(cudaMemsetAsync(ctl, 0, sizeof(unsigned) * kCtlWords, st));
+        const int64_t tot = (int64_t)npad * npad;
+        h->launches += 4;
+        jacobi_init_kernel<<<(unsigned)((tot + 255) / 256 < 4096 ? (tot + 255) / 256 : 4096), 256, 0, st>>>(
+            n, npad, B, ldb, G, V);
+        TSVD_TRY_CUDA(cudaGetLastError());
+        const double tol = (double)(n > 16 ? n : 16) * kEps;
+        double* Vacc = accumulate ? V : nullptr;
+        if (w > 0) {
+            const int nblk = npad / w;
+            const int nb = nblk / 2;
+            const size_t smem = block_smem(n, w);
+            static thread_local int configured = -1;
+            if (configured != h->device) {
+                TSVD_TRY_CUDA(cudaFuncSetAttribute(jacobi_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)block_smem(1024, kJBlkMaxW)));
+                configured = h->device;
+            }
+            int per_sm = 0;
+            TSVD_TRY_CUDA(
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_block_kernel, 32 * w * kJGroup, smem));
+            if (per_sm * h->sm_count < nb) return TSVD_ERR_UNSUPPORTED;
+            int nn = n, np = npad, ww = w;
             double t = tol;
-            void* args[] = {(void*)&nn, (void*)&np, (void*)&G, (void*)&Vacc, (void*)&nrm, (void*)&ctl, (void*)&t,
-                            (void*)&pp};
-            TSVD_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_sweep_kernel, dim3(nblocks), dim3(block),
-                                                      args, 0, st));
+            void* args[] = {(void*)&nn, (void*)&np, (void*)&ww, (void*)&G, (void*)&nrm, (void*)&ctl, (void*)&t};
+            TSVD_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_block_kernel, dim3(nb), dim3(32 * w * kJGroup),
+                                                      args, smem, st));
+        } else {
+            const int npairs = npad / 2;
+            int block = 0;
+            const int nblocks = jacobi_grid(h, npairs, block);
+            if (nblocks < 1) return TSVD_ERR_UNSUPPORTED;
+            const int ppb = (npairs + nblocks - 1) / nblocks;
+            if (nblocks == 1) {
+                jacobi_sweep_kernel<<<1, block, 0, st>>>(n, npad, G, Vacc, nrm, ctl, tol, ppb);
+                TSVD_TRY_CUDA(cudaGetLastError());
+            } else {
+                int nn = n, np = npad, pp = ppb;
+                double t = tol;
+                void* args[] = {(void*)&nn, (void*)&np, (void*)&G, (void*)&Vacc, (void*)&nrm, (void*)&ctl, (void*)&t,
+                                (void*)&pp};
+                TSVD_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_sweep_kernel, dim3(nblocks), dim3(block),
+                                                          args, 0, st));
+            }
         }
+        jacobi_sort_kernel<<<1, 1024, 0, st>>>(n, npad, G, sig, perm, ctl, status);
+        jacobi_out_kernel<<<n, 128, 0, st>>>(n, npad, G, Vacc, sig, perm, Ubar, sigma, Vbar);
+        TSVD_TRY_CUDA(cudaGetLastError());
     }
-    jacobi_sort_kernel<<<1, 1024, 0, st>>>(n, npad, G, sig, perm, ctl, status);
-    jacobi_out_kernel<<<n, 128, 0, st>>>(n, npad, G, Vacc, sig, perm, Ubar, sigma, Vbar);
-    TSVD_TRY_CUDA(cudaGetLastError());
     if (!accumulate && nv > 0) {
         // right vectors of the leading nv triplets: vbar_j = B^T ubar_j / sigma_j
         TSVD_TRY_CUDA(gemm_tn(h, n, n, nv, B, ldb, Ubar, n, Vbar, n, false, part, st));
         h->launches++;
         jacobi_vfix_kernel<<<nv, 128, 0, st>>>(n, sigma, Ubar, Vbar);
         TSVD_TRY_CUDA(cudaGetLastError());
+        // The columns of Ubar are orthonormal to the sweep tolerance tau, those of
+        // B^T Ubar Sigma^-1 only to tau sigma_1 / sigma_j: one block CGS-QR (Alg. 3)
+        // pass restores orthonormal right vectors (R = I + O(tau sigma_1 / sigma_nv)).
+        OrthCtx vctx;
+        vctx.seed = 0x5eedULL;
+        double* Rv = ar.take<double>((size_t)nv * nv);
+        if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+        TSVD_TRY(cgs_qr<double>(h, n, nv, nv < TSVD_MAX_BLOCK ? nv : TSVD_MAX_BLOCK, Vbar, n, Rv, vctx, ar, status,
+                                st));
     }
     return TSVD_OK;
 }

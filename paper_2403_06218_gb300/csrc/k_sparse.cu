@@ -395,7 +395,7 @@ cudaError_t launch_spmm(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz, const
     if (m == 0 || w == 0) return cudaSuccess;
     // compulsory traffic: the CSR arrays, X and Y once each
     const double es = (double)sizeof(T);
-    ProfScope prof(h, TSVD_K_SPMM, 2.0 * nnz * w,
+    ProfScope prof(h, TSVD_K_APROD, 2.0 * nnz * w,
                    (4.0 + es) * nnz + 4.0 * (m + 1) + es * (double)n * w + es * (double)m * w, st);
     const unsigned blocks = (unsigned)((m + 7) / 8);
     const bool v2 = (ldx % 2 == 0) && (ldy % 2 == 0) && ((reinterpret_cast<uintptr_t>(X) & (2 * sizeof(T) - 1)) == 0) &&

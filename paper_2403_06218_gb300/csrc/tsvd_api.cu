@@ -326,6 +326,44 @@ int tsvd_dense_mm_f32(tsvd_handle* h, int trans, int64_t m, int64_t n, const flo
     return TSVD_OK;
 }
 
+int tsvd_bf16x3_bytes(int64_t rows, int64_t cols, size_t* bytes) {
+    if (!bytes || rows < 0 || cols < 0) return TSVD_ERR_INVALID_ARG;
+    *bytes = bf16x3_bytes(rows, cols);
+    return TSVD_OK;
+}
+
+int tsvd_bf16x3_split(tsvd_handle* h, int trans, int64_t m, int64_t n, const double* A, int64_t lda, void* pieces,
+                      void* stream) {
+    if (!h || m < 0 || n < 0 || lda < n || (m * n > 0 && (!A || !pieces))) return TSVD_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    TSVD_TRY_CUDA(bf16x3_split<double>(h, m, n, A, lda, trans != 0, pieces, st));
+    TSVD_TRY_CUDA(cudaStreamSynchronize(st));
+    return TSVD_OK;
+}
+
+int tsvd_mm_bf16x6_workspace(int64_t rows, int64_t cols, int w, size_t* bytes) {
+    if (!bytes || rows < 0 || cols < 0 || w < 0) return TSVD_ERR_INVALID_ARG;
+    *bytes = align256(sizeof(int) * kStCount) + tc_mm_ws(rows, cols, w);
+    return TSVD_OK;
+}
+
+int tsvd_mm_bf16x6(tsvd_handle* h, int64_t rows, int64_t cols, const void* pieces, int w, const float* X,
+                   int64_t ldx, float* Y, int64_t ldy, void* ws, size_t ws_bytes, void* stream) {
+    if (!h || rows < 0 || cols < 0 || w < 0 || ldx < w || ldy < w) return TSVD_ERR_INVALID_ARG;
+    if (rows * (int64_t)w > 0 && (!Y || (cols > 0 && (!pieces || !X)))) return TSVD_ERR_INVALID_ARG;
+    size_t need = 0;
+    TSVD_TRY(tsvd_mm_bf16x6_workspace(rows, cols, w, &need));
+    TSVD_TRY(check_ws(ws, ws_bytes, need));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int* status = static_cast<int*>(ws);
+    TSVD_TRY_CUDA(cudaMemsetAsync(status, 0, sizeof(int) * kStCount, st));
+    void* rest = static_cast<uint8_t*>(ws) + align256(sizeof(int) * kStCount);
+    TSVD_TRY_CUDA(tc_mm(h, rows, cols, pieces, w, X, ldx, Y, ldy, rest, status, st));
+    int hs[kStCount];
+    TSVD_TRY(read_status(st, status, hs));
+    return hs[kStTimeout] ? TSVD_ERR_TIMEOUT : TSVD_OK;
+}
+
 int tsvd_orth_workspace(int64_t q, int64_t s, int b, size_t* bytes) {
     if (!bytes || q < 0 || s < 0 || b < 1) return TSVD_ERR_INVALID_ARG;
     tsvd_handle hh{};

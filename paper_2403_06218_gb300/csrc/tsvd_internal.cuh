@@ -23,6 +23,7 @@ struct tsvd_handle {
     int jacobi_coop_blocks;  // co-resident CTAs of the cooperative Jacobi kernel
     int64_t launches;        // kernels enqueued through this handle (running total)
     bool profiling = false;
+    int prof_class = -1;     // when >= 0, the class every ProfScope records (see ProfClass)
     std::vector<tsvd_prof_rec> recs;
     std::vector<cudaEvent_t> pool;
 };
@@ -62,7 +63,7 @@ class ProfScope {
     ProfScope(tsvd_handle* h, int cls, double flops, double bytes, cudaStream_t st)
         : h_(h && h->profiling ? h : nullptr), st_(st) {
         if (!h_) return;
-        rec_.cls = cls;
+        rec_.cls = h_->prof_class >= 0 ? h_->prof_class : cls;
         rec_.flops = flops;
         rec_.bytes = bytes;
         rec_.e0 = get();
@@ -90,6 +91,29 @@ class ProfScope {
     cudaStream_t st_;
     tsvd_prof_rec rec_{};
 };
+
+// Files every launch in its lifetime under one class (products with A that
+// reuse the GEMM kernels count as products with A).
+struct ProfClass {
+    tsvd_handle* h;
+    int prev;
+    ProfClass(tsvd_handle* hh, int cls) : h(hh), prev(hh->prof_class) { h->prof_class = cls; }
+    ~ProfClass() { h->prof_class = prev; }
+};
+
+// Sets the flop count of the latest record of a class (work known only after
+// the launch, e.g. the Jacobi sweeps).
+inline void prof_set_last_flops(tsvd_handle* h, int cls, double flops) {
+    if (!h->profiling) return;
+    for (auto it = h->recs.rbegin(); it != h->recs.rend(); ++it)
+        if (it->cls == cls) {
+            it->flops = flops;
+            return;
+        }
+}
+inline double jacobi_flops(int n, int nv, int sweeps) {
+    return (double)sweeps * (nv >= n ? 18.0 : 12.0) * n * (0.5 * n * (n - 1.0));
+}
 
 // Sums the recorded events into info->prof_* (the stream must be synchronised).
 void prof_collect(tsvd_handle* h, tsvd_info* info);
@@ -150,6 +174,18 @@ template <typename TW>
 cudaError_t launch_gemm_tn_f32(dim3 grid, cudaStream_t st, int64_t q, int64_t s, int64_t b, const float* X,
                                int64_t ldx, const float* Z, int64_t ldz, TW* out, int64_t ldo, int64_t slab_stride,
                                int64_t slab_rows, int symmetric, int nreg_s, int nreg_b);
+// Split-BF16 tensor-core products (k_tc.cu).  Pieces of a rows x cols matrix are
+// stored [3][rows][bf16x3_ld(cols)] as BF16.
+int64_t bf16x3_ld(int64_t cols);
+size_t bf16x3_bytes(int64_t rows, int64_t cols);
+// Pieces of S (rows x cols) or, with trans, of S^T.
+template <typename T>
+cudaError_t bf16x3_split(tsvd_handle* h, int64_t rows, int64_t cols, const T* S, int64_t lds, bool trans, void* out,
+                         cudaStream_t st);
+// Y (rows x w, FP32) = P X, P given by its pieces (rows x cols), X cols x w (FP32).
+size_t tc_mm_ws(int64_t rows, int64_t cols, int w);
+cudaError_t tc_mm(tsvd_handle* h, int64_t rows, int64_t cols, const void* pieces, int w, const float* X, int64_t ldx,
+                  float* Y, int64_t ldy, void* ws, int* status, cudaStream_t st);
 template <typename TM, typename TY>
 cudaError_t launch_gemm_nn_f32(cudaStream_t st, int64_t q, int64_t s, int64_t b, double alpha, const float* X,
                                int64_t ldx, const TM* M, int64_t ldm, double beta, TY* Y, int64_t ldy, bool upper);

@@ -10,3 +10,4 @@ def subspace_sin(X, X0):
     X = np.asarray(X, dtype=np.float64)
     X0 = np.asarray(X0, dtype=np.float64)
     return float(np.linalg.norm(X - X0 @ (X0.T @ X), 2))
+

@@ -342,3 +342,21 @@ def test_workload_generators():
     A, s, U0, V0 = workloads.dense_known_spectrum(64, 32, seed=4)
     np.testing.assert_allclose(np.linalg.svd(A, compute_uv=False), s, rtol=1e-13)
     np.testing.assert_allclose(s, 2.0 ** (-np.arange(32) / 8))
+
+
+def test_householder_workload_has_its_spectrum_and_vectors():
+    """The large dense workload's generator: singular values exactly sigma, singular
+    vectors the leading columns of the reflector products, and the device twin of
+    the construction (tests/helpers.py) gives the same matrix."""
+    m, n = 300, 200
+    A, s, Uv, Vv = workloads.dense_householder_spectrum(m, n, seed=2, L=16)
+    np.testing.assert_allclose(s, 1.0 / (1.0 + np.arange(n)) ** 1.5)
+    np.testing.assert_allclose(np.linalg.svd(A, compute_uv=False), s, rtol=1e-12, atol=1e-15)
+    HU = workloads.reflect_left(np.eye(m), Uv)
+    HV = workloads.reflect_left(np.eye(n), Vv)
+    assert np.abs(HU.T @ HU - np.eye(m)).max() < 1e-13
+    np.testing.assert_allclose(A, (HU[:, :n] * s) @ HV.T, atol=1e-14)
+    # A v_j = sigma_j u_j for the generator's own vectors
+    assert np.abs(A @ HV[:, :5] - HU[:, :5] * s[:5]).max() < 1e-14
+    At, _ = workloads.dense_householder_spectrum_torch(m, n, seed=2, L=16, device="cpu")
+    assert np.abs(At.numpy() - A).max() < 1e-14

@@ -14,6 +14,11 @@ Workloads (sizes as in the paper's experiments and the library's benchmark):
   Sec. 4.1 (Table 2), which are not available here.
 * ``csr_power_law``: rows with Zipf-distributed degrees and Zipf column
   popularity, U(0,1) values (heavy rows and heavy columns).
+* ``dense_householder_spectrum``: A = H_U diag(sigma) H_V^T with H_U, H_V
+  products of L seeded Householder reflectors (the large dense workload, whose
+  factors are orthogonal "via Householder products"); default sigma_i =
+  1/(1+i)^1.5.  ``householder_factors`` gives the reflectors so that a device
+  can materialise the same A.
 """
 
 from __future__ import annotations
@@ -140,3 +145,67 @@ def csr_power_law(m: int, n: int, target_nnz: int, seed: int = 3, deg_exp: float
     indptr[1:] = np.cumsum(have)
     vals = rng.random(keys.size).astype(dtype)
     return sp.csr_matrix((vals, (keys % n).astype(np.int32), indptr), shape=(m, n))
+
+
+def householder_factors(m: int, n: int, seed: int = 2, L: int = 16):
+    """Unit vectors of the seeded reflectors: rows u_1..u_L (length m) and v_1..v_L
+    (length n), each a normalised N(0,1) draw (u's first, then v's)."""
+    rng = np.random.default_rng(seed)
+    Uv = rng.standard_normal((L, m))
+    Uv /= np.linalg.norm(Uv, axis=1, keepdims=True)
+    Vv = rng.standard_normal((L, n))
+    Vv /= np.linalg.norm(Vv, axis=1, keepdims=True)
+    return Uv, Vv
+
+
+def reflect_left(X: np.ndarray, Uv: np.ndarray) -> np.ndarray:
+    """H_U X with H_U = (I - 2 u_1 u_1^T) ... (I - 2 u_L u_L^T): the reflectors are
+    applied from u_L to u_1.  In place on a copy."""
+    X = np.array(X, dtype=np.float64, copy=True)
+    for u in Uv[::-1]:
+        X -= 2.0 * np.outer(u, u @ X)
+    return X
+
+
+def dense_householder_spectrum(m: int, n: int, seed: int = 2, sigma=None, L: int = 16):
+    """Dense A = H_U S H_V^T (m x n, FP64, C-contiguous): S is m x n with diagonal
+    sigma (default sigma_i = 1/(1+i)^1.5, i = 0..min(m,n)-1), H_U and H_V the
+    reflector products of ``householder_factors``.  The singular values are sigma
+    and the singular vectors are the leading columns of H_U and H_V.
+
+    Returns (A, sigma, Uv, Vv)."""
+    r = min(m, n)
+    sigma = spectrum_power(r) if sigma is None else np.asarray(sigma, dtype=np.float64)
+    Uv, Vv = householder_factors(m, n, seed, L)
+    S = np.zeros((m, n))
+    S[np.arange(r), np.arange(r)] = sigma
+    # (H_U S) H_V^T = ((H_V (H_U S)^T))^T since H_V is symmetric
+    A = reflect_left(reflect_left(S, Uv).T, Vv).T
+    return np.ascontiguousarray(A), sigma, Uv, Vv
+
+
+def reflect_left_torch(X, Uv):
+    """Device twin of ``reflect_left`` for a torch tensor X (modified in place)."""
+    for i in range(Uv.shape[0] - 1, -1, -1):
+        u = Uv[i]
+        X.addr_(u, u @ X, alpha=-2.0)
+    return X
+
+
+def dense_householder_spectrum_torch(m: int, n: int, seed: int = 2, sigma=None, L: int = 16, device="cuda"):
+    """The matrix of ``dense_householder_spectrum`` built with torch on ``device``
+    (same reflectors, same formula; for sizes where numpy would take minutes).
+
+    Returns (A, sigma) with A a C-contiguous float64 torch tensor."""
+    import torch
+    r = min(m, n)
+    sigma = spectrum_power(r) if sigma is None else np.asarray(sigma, dtype=np.float64)
+    Uv, Vv = householder_factors(m, n, seed, L)
+    S = torch.zeros((m, n), dtype=torch.float64, device=device)
+    idx = torch.arange(r, device=device)
+    S[idx, idx] = torch.as_tensor(sigma, dtype=torch.float64, device=device)
+    reflect_left_torch(S, torch.as_tensor(Uv, device=device))
+    At = S.T.contiguous()
+    del S
+    reflect_left_torch(At, torch.as_tensor(Vv, device=device))
+    return At.T.contiguous(), sigma
