@@ -209,10 +209,12 @@ int tsvd_csr_transpose(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz,
                        void* ws, size_t ws_bytes, void* stream);
 
 /* Y = A X for CSR A (m x n): X is n x w (ldx), Y is m x w (ldy), Table 1 SpMM.
- * Each y_i sums its row's entries in CSR order.  ws holds the status words
- * (TSVD_SPMM_WORKSPACE bytes); an entry whose column lies outside [0, n) is
- * skipped and reported as TSVD_ERR_INVALID_ARG. */
-#define TSVD_SPMM_WORKSPACE 256
+ * Each y_i sums its row's entries in CSR order; a row longer than 1024 entries
+ * is summed in chunks of 1024 whose partial sums are added in chunk order
+ * (deterministic).  ws (tsvd_spmm_workspace bytes) holds the status words and
+ * the chunk plan; an entry whose column lies outside [0, n) is skipped and
+ * reported as TSVD_ERR_INVALID_ARG. */
+int tsvd_spmm_workspace(int64_t m, int64_t nnz, int w, size_t* bytes);
 int tsvd_spmm(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz,
               const int32_t* row_ptr, const int32_t* col_idx, const double* val,
               int w, const double* X, int64_t ldx, double* Y, int64_t ldy,

@@ -29,7 +29,6 @@ TSVD_METHOD_RSVD = 0
 TSVD_METHOD_BLANCZOS = 1
 TSVD_MAX_BLOCK = 128
 TSVD_MAX_SMALL_SVD = 2048
-TSVD_SPMM_WORKSPACE = 256
 TSVD_FLAG_PROFILE = 1
 TSVD_NOALLOC_SCRATCH_BYTES = 4 * 1024 * 1024
 KERNEL_CLASSES = ("a_products", "gemm_tn", "gemm_nn", "chol", "svd", "other")
@@ -91,6 +90,7 @@ SIGNATURES = [
     ("tsvd_gaussian_block", _I, [_I64, _I64, C.c_uint64, C.c_uint32, _P, _I64, _P]),
     ("tsvd_csr_transpose_workspace", _I, [_I64, _I64, _I64, _PSZ]),
     ("tsvd_csr_transpose", _I, [_P, _I64, _I64, _I64, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    ("tsvd_spmm_workspace", _I, [_I64, _I64, _I, _PSZ]),
     ("tsvd_spmm", _I, [_P, _I64, _I64, _I64, _P, _P, _P, _I, _P, _I64, _P, _I64, _P, _SZ, _P]),
     ("tsvd_dense_mm_workspace", _I, [_I, _I64, _I64, _I, _PSZ]),
     ("tsvd_dense_mm", _I, [_P, _I, _I64, _I64, _P, _I64, _I, _P, _I64, _P, _I64, _P, _SZ, _P]),

@@ -270,15 +270,19 @@ def csr_transpose(A: CsrMatrix) -> CsrMatrix:
 
 
 def spmm(A: CsrMatrix, X: torch.Tensor) -> torch.Tensor:
-    """Y = A X for CSR A on the GPU."""
+    """Y = A X for CSR A (FP64 values) on the GPU."""
     lib = capi.load()
     _cuda_f64(X, "X")
+    if A.val.dtype != torch.float64:
+        raise TypeError("spmm takes FP64 CSR values")
     dev = X.device
     m, n = A.shape
     w = X.shape[1]
     Y = torch.empty((m, w), dtype=torch.float64, device=dev)
     with torch.cuda.device(dev):
-        ws = _ws(capi.TSVD_SPMM_WORKSPACE, dev)
+        nb = C.c_size_t()
+        capi.check(lib.tsvd_spmm_workspace(m, A.nnz, w, C.byref(nb)), "tsvd_spmm_workspace")
+        ws = _ws(nb.value, dev)
         capi.check(lib.tsvd_spmm(handle(dev), m, n, A.nnz, A.row_ptr.data_ptr(), A.col_idx.data_ptr(),
                                  A.val.data_ptr(), w, X.data_ptr(), X.stride(0), Y.data_ptr(), max(w, 1),
                                  ws.data_ptr(), ws.numel(), _stream_ptr(dev)), "tsvd_spmm")

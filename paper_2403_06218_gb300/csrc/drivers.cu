@@ -66,6 +66,7 @@ struct Op {
     int64_t lda64 = 0;
     double* partial = nullptr;  // split-K scratch of dense A^T X
     // mixed form, dense A: BF16 pieces of A and of A^T for the tensor-core products
+    SpmmPlan plan_a, plan_at;  // long-row split plans of CSR(A) and CSR(A^T)
     bool tc = false;
     const void* pA = nullptr;
     const void* pAt = nullptr;
@@ -75,14 +76,14 @@ struct Op {
 // Y (op.m x w) = op(A) X ; in precision TV with values V (sparse) or D (dense).
 template <typename TV>
 int apply(tsvd_handle* h, bool sparse, bool trans_of_A, int64_t M, int64_t N, int64_t nnz, const int32_t* rp,
-          const int32_t* ci, const TV* va, const int32_t* trp, const int32_t* tci, const TV* tva, const TV* dA,
-          int64_t lda, double* partial, int w, const TV* X, int64_t ldx, TV* Y, int64_t ldy, int* status,
-          cudaStream_t st) {
+          const int32_t* ci, const TV* va, const int32_t* trp, const int32_t* tci, const TV* tva,
+          const SpmmPlan* pa, const SpmmPlan* pat, const TV* dA, int64_t lda, double* partial, int w, const TV* X,
+          int64_t ldx, TV* Y, int64_t ldy, int* status, cudaStream_t st) {
     if (sparse) {
         if (!trans_of_A)
-            TSVD_TRY_CUDA(launch_spmm<TV>(h, M, N, nnz, rp, ci, va, w, X, ldx, Y, ldy, status, st));
+            TSVD_TRY_CUDA(launch_spmm<TV>(h, M, N, nnz, rp, ci, va, w, X, ldx, Y, ldy, status, st, pa));
         else
-            TSVD_TRY_CUDA(launch_spmm<TV>(h, N, M, nnz, trp, tci, tva, w, X, ldx, Y, ldy, status, st));
+            TSVD_TRY_CUDA(launch_spmm<TV>(h, N, M, nnz, trp, tci, tva, w, X, ldx, Y, ldy, status, st, pat));
     } else {
         ProfClass pc(h, TSVD_K_APROD);
         if (!trans_of_A)
@@ -105,7 +106,7 @@ int op_mul(tsvd_handle* h, Op<T>& op, int w, const T* X, int64_t ldx, T* Y, int6
         }
     }
     return apply<T>(h, op.sparse, op.transposed, op.M, op.N, op.nnz, op.rp, op.ci, op.va, op.trp, op.tci, op.tva,
-                    op.dA, op.lda, op.partial, w, X, ldx, Y, ldy, status, st);
+                    &op.plan_a, &op.plan_at, op.dA, op.lda, op.partial, w, X, ldx, Y, ldy, status, st);
 }
 template <typename T>
 int op_tmul(tsvd_handle* h, Op<T>& op, int w, const T* X, int64_t ldx, T* Y, int64_t ldy, int* status,
@@ -118,20 +119,22 @@ int op_tmul(tsvd_handle* h, Op<T>& op, int w, const T* X, int64_t ldx, T* Y, int
         }
     }
     return apply<T>(h, op.sparse, !op.transposed, op.M, op.N, op.nnz, op.rp, op.ci, op.va, op.trp, op.tci, op.tva,
-                    op.dA, op.lda, op.partial, w, X, ldx, Y, ldy, status, st);
+                    &op.plan_a, &op.plan_at, op.dA, op.lda, op.partial, w, X, ldx, Y, ldy, status, st);
 }
 // op(A) X and op(A)^T X with the FP64 values (final Rayleigh-Ritz step and residuals).
 template <typename T>
 int op_mul64(tsvd_handle* h, Op<T>& op, int w, const double* X, int64_t ldx, double* Y, int64_t ldy, int* status,
              cudaStream_t st) {
     return apply<double>(h, op.sparse, op.transposed, op.M, op.N, op.nnz, op.rp, op.ci, op.va64, op.trp, op.tci,
-                         op.tva64, op.dA64, op.lda64, op.partial, w, X, ldx, Y, ldy, status, st);
+                         op.tva64, &op.plan_a, &op.plan_at, op.dA64, op.lda64, op.partial, w, X, ldx, Y, ldy, status,
+                         st);
 }
 template <typename T>
 int op_tmul64(tsvd_handle* h, Op<T>& op, int w, const double* X, int64_t ldx, double* Y, int64_t ldy, int* status,
               cudaStream_t st) {
     return apply<double>(h, op.sparse, !op.transposed, op.M, op.N, op.nnz, op.rp, op.ci, op.va64, op.trp, op.tci,
-                         op.tva64, op.dA64, op.lda64, op.partial, w, X, ldx, Y, ldy, status, st);
+                         op.tva64, &op.plan_a, &op.plan_at, op.dA64, op.lda64, op.partial, w, X, ldx, Y, ldy, status,
+                         st);
 }
 
 size_t tn_partial_max(tsvd_handle* h, int64_t q, int64_t s, int wmax) {
@@ -242,6 +245,14 @@ int setup_op(tsvd_handle* h, const tsvd_matrix* A, int wmax, Arena& ar, Op<T>& o
             }
             op.va = v;
             op.tva = tv;
+        }
+        // long-row split plans (partials sized for FP64, which covers FP32)
+        if (run) {
+            TSVD_TRY(spmm_plan(h, M, nnz, op.rp, wmax, sizeof(double), ar, &op.plan_a, st));
+            TSVD_TRY(spmm_plan(h, N, nnz, op.trp, wmax, sizeof(double), ar, &op.plan_at, st));
+        } else {
+            ar.take<char>(spmm_plan_ws(M, nnz, wmax, sizeof(double)));
+            ar.take<char>(spmm_plan_ws(N, nnz, wmax, sizeof(double)));
         }
     } else {
         const void* a = A->val;

@@ -2,11 +2,19 @@
 // Alg. 1 S1/S3, Alg. 2 S2/S4) and the one-time build of CSR(A^T) that turns the
 // A^T products into the same row-oriented kernel.
 //
-// FP64 on GB300 is bound by the FP64 pipe (2 DFMA/clk/SM), not by HBM: one
-// warp owns one row, lanes own consecutive column pairs of the dense block
-// (16-byte loads of each gathered X row), the row's (col, val) pairs are read
-// 32 at a time cooperatively and broadcast with shuffles.  Every y_ij is
-// accumulated in CSR order with FMA, so the result is deterministic.
+// A sub-warp of G lanes owns one row; each lane gathers a 16-byte slice of every
+// X row the row touches (float4 / double2), so G = w / (16 / sizeof(T)) lanes
+// cover a block of w columns and narrow blocks put several rows in a warp.  The
+// gathers (nnz w sizeof(T) bytes, from L2 for a block that fits there) bound the
+// kernel, not the compulsory HBM bytes: measured ~13 TB/s of gathered data on
+// GB300.  FP64 is also close to the FP64 pipe's rate (2 DFMA/clk/SM).  Every y_ij
+// is accumulated in CSR order with FMA, so the result is deterministic.
+//
+// Long rows (power-law degrees; CSR(A^T) of a matrix with popular columns holds
+// rows of up to ~10^6 entries) would leave one warp working long after the rest.
+// A plan built once per matrix cuts every row longer than kSpmmChunk entries into
+// chunks of kSpmmChunk: one warp per chunk writes a partial row, and a second
+// kernel adds each row's partials in chunk order (still deterministic).
 #include <climits>
 
 #include "tsvd_internal.cuh"
@@ -16,123 +24,135 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-template <typename T>
-struct Vec2;
+
+// VW consecutive values of the SpMM element type, loaded as one vector.
+template <typename T, int VW>
+struct VecLoad;
 template <>
-struct Vec2<double> {
-    using type = double2;
+struct VecLoad<double, 2> {
+    __device__ static void get(const double* p, double* o) {
+        const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+        o[0] = v.x;
+        o[1] = v.y;
+    }
 };
 template <>
-struct Vec2<float> {
-    using type = float2;
+struct VecLoad<float, 4> {
+    __device__ static void get(const float* p, float* o) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        o[0] = v.x;
+        o[1] = v.y;
+        o[2] = v.z;
+        o[3] = v.w;
+    }
+};
+template <typename T>
+struct VecLoad<T, 1> {
+    __device__ static void get(const T* p, T* o) { o[0] = __ldg(p); }
 };
 
-// NV = number of 2-element vectors per lane per column panel (panel width 64*NV).
-template <typename T, int NV>
-__global__ void __launch_bounds__(256) spmm_v2_kernel(int64_t m, int64_t n, const int32_t* __restrict__ rp,
-                                                      const int32_t* __restrict__ ci,
-                                                      const T* __restrict__ va, int w,
-                                                      const T* __restrict__ X, int64_t ldx,
-                                                      T* __restrict__ Y, int64_t ldy, int* status) {
-    using V2 = typename Vec2<T>::type;
-    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (row >= m) return;
-    const int beg = rp[row], end = rp[row + 1];
-    for (int c0 = 0; c0 < w; c0 += 64 * NV) {
-        T ax[NV], ay[NV];
+// One output row y = sum over the entries [beg, end) of a_e x_{col(e)}, written to
+// out[0 .. w), by a sub-warp of G lanes: lane sl owns VW consecutive columns of each
+// panel of VW G columns and gathers them with one vector load per entry (the
+// entry's (col, val) is read by all G lanes: a broadcast).  Each y_ij is
+// accumulated in CSR order with FMA, so the result is deterministic.
+template <typename T, int VW, int G>
+__device__ inline void spmm_segment(int64_t beg, int64_t end, int64_t n, const int32_t* __restrict__ ci,
+                                    const T* __restrict__ va, int w, const T* __restrict__ X, int64_t ldx,
+                                    T* __restrict__ out, int* status, int sl) {
+    for (int c0 = 0; c0 < w; c0 += VW * G) {
+        const int col = c0 + VW * sl;
+        if (col >= w) continue;  // lanes past the last column of a narrow panel
+        const bool full = col + VW <= w;
+        T acc[VW];
 #pragma unroll
-        for (int t = 0; t < NV; ++t) ax[t] = ay[t] = T(0);
-        for (int e0 = beg; e0 < end; e0 += 32) {
-            const int e = e0 + lane;
-            int myc = 0;
-            T mya = T(0);
-            if (e < end) {
-                myc = ci[e];
-                mya = va[e];
+        for (int q = 0; q < VW; ++q) acc[q] = T(0);
+        for (int64_t e = beg; e < end; ++e) {
+            const int c = __ldg(ci + e);
+            const T a = __ldg(va + e);
+            if ((uint64_t)(int64_t)c >= (uint64_t)n) {  // skipped, and reported
+                if (sl == 0) atomicOr(&status[kStBadCsr], 1);
+                continue;
             }
-            const int cnt = min(32, end - e0);
-            for (int j = 0; j < cnt; ++j) {
-                const int c = __shfl_sync(kFull, myc, j);
-                const T a = __shfl_sync(kFull, mya, j);
-                if ((uint64_t)(int64_t)c >= (uint64_t)n) {
-                    if (lane == 0) atomicOr(&status[kStBadCsr], 1);
-                    continue;
-                }
-                const T* xr = X + (int64_t)c * ldx + c0;
+            const T* xr = X + (int64_t)c * ldx + col;
+            T x[VW];
+            if (full) {
+                VecLoad<T, VW>::get(xr, x);
+            } else {
 #pragma unroll
-                for (int t = 0; t < NV; ++t) {
-                    const int col = 2 * lane + 64 * t;
-                    if (c0 + col + 1 < w) {
-                        const V2 x = *reinterpret_cast<const V2*>(xr + col);
-                        ax[t] = fma(a, x.x, ax[t]);
-                        ay[t] = fma(a, x.y, ay[t]);
-                    } else if (c0 + col < w) {
-                        ax[t] = fma(a, xr[col], ax[t]);
-                    }
-                }
+                for (int q = 0; q < VW; ++q) x[q] = (col + q < w) ? __ldg(xr + q) : T(0);
             }
+#pragma unroll
+            for (int q = 0; q < VW; ++q) acc[q] = fma(a, x[q], acc[q]);
         }
-        T* yr = Y + row * ldy + c0;
 #pragma unroll
-        for (int t = 0; t < NV; ++t) {
-            const int col = 2 * lane + 64 * t;
-            if (c0 + col + 1 < w) {
-                V2 v;
-                v.x = ax[t];
-                v.y = ay[t];
-                *reinterpret_cast<V2*>(yr + col) = v;
-            } else if (c0 + col < w) {
-                yr[col] = ax[t];
-            }
-        }
+        for (int q = 0; q < VW; ++q)
+            if (col + q < w) out[col + q] = acc[q];
     }
 }
 
-// Scalar variant for unaligned blocks: lane owns columns lane + 32 t.
-template <typename T>
-__global__ void __launch_bounds__(256) spmm_scalar_kernel(int64_t m, int64_t n, const int32_t* __restrict__ rp,
-                                                          const int32_t* __restrict__ ci,
-                                                          const T* __restrict__ va, int w,
-                                                          const T* __restrict__ X, int64_t ldx,
-                                                          T* __restrict__ Y, int64_t ldy, int* status) {
-    const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
+// Sub-warp of G lanes per row; rows longer than `split` entries are left to the chunk kernels.
+template <typename T, int VW, int G>
+__global__ void __launch_bounds__(256) spmm_rows_kernel(int64_t m, int64_t n, const int32_t* __restrict__ rp,
+                                                        const int32_t* __restrict__ ci, const T* __restrict__ va,
+                                                        int w, const T* __restrict__ X, int64_t ldx,
+                                                        T* __restrict__ Y, int64_t ldy, int64_t split, int* status) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int sl = threadIdx.x % G;
     if (row >= m) return;
-    const int beg = rp[row], end = rp[row + 1];
-    for (int c0 = 0; c0 < w; c0 += 128) {
-        T acc[4] = {T(0), T(0), T(0), T(0)};
-        for (int e0 = beg; e0 < end; e0 += 32) {
-            const int e = e0 + lane;
-            int myc = 0;
-            T mya = T(0);
-            if (e < end) {
-                myc = ci[e];
-                mya = va[e];
-            }
-            const int cnt = min(32, end - e0);
-            for (int j = 0; j < cnt; ++j) {
-                const int c = __shfl_sync(kFull, myc, j);
-                const T a = __shfl_sync(kFull, mya, j);
-                if ((uint64_t)(int64_t)c >= (uint64_t)n) {
-                    if (lane == 0) atomicOr(&status[kStBadCsr], 1);
-                    continue;
-                }
-                const T* xr = X + (int64_t)c * ldx + c0;
-#pragma unroll
-                for (int t = 0; t < 4; ++t) {
-                    const int col = lane + 32 * t;
-                    if (c0 + col < w) acc[t] = fma(a, xr[col], acc[t]);
-                }
-            }
-        }
-        T* yr = Y + row * ldy + c0;
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int col = lane + 32 * t;
-            if (c0 + col < w) yr[col] = acc[t];
-        }
+    const int64_t beg = rp[row], end = rp[row + 1];
+    if (end - beg > split) return;
+    spmm_segment<T, VW, G>(beg, end, n, ci, va, w, X, ldx, Y + row * ldy, status, sl);
+}
+
+// Sub-warp per chunk of a long row: entries [rp[row] + j C, min(rp[row + 1], rp[row] + (j+1) C))
+// into partial[chunk][0 .. w).
+template <typename T, int VW, int G>
+__global__ void __launch_bounds__(256) spmm_chunks_kernel(int64_t nchunks, const int4* __restrict__ chunks,
+                                                          int64_t n, const int32_t* __restrict__ rp,
+                                                          const int32_t* __restrict__ ci, const T* __restrict__ va,
+                                                          int w, const T* __restrict__ X, int64_t ldx,
+                                                          T* __restrict__ partial, int64_t ldp, int* status) {
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int sl = threadIdx.x % G;
+    if (c >= nchunks) return;
+    const int4 d = chunks[c];
+    const int64_t beg = (int64_t)rp[d.x] + (int64_t)d.y * kSpmmChunk;
+    const int64_t end = min((int64_t)rp[d.x + 1], beg + kSpmmChunk);
+    spmm_segment<T, VW, G>(beg, end, n, ci, va, w, X, ldx, partial + c * ldp, status, sl);
+}
+
+// Y[row] = sum of the row's chunk partials in chunk order (the first chunk's warp does the row).
+template <typename T>
+__global__ void __launch_bounds__(256) spmm_chunk_sum_kernel(int64_t nchunks, const int4* __restrict__ chunks,
+                                                             int w, const T* __restrict__ partial, int64_t ldp,
+                                                             T* __restrict__ Y, int64_t ldy) {
+    const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (c >= nchunks) return;
+    const int4 d = chunks[c];
+    if (d.y != 0) return;
+    for (int col = lane; col < w; col += 32) {
+        T acc = T(0);
+        for (int t = 0; t < d.z; ++t) acc += partial[(c + t) * ldp + col];
+        Y[(int64_t)d.x * ldy + col] = acc;
     }
+}
+
+// Plan: chunks of each row longer than kSpmmChunk entries.
+__global__ void spmm_plan_count_kernel(int64_t m, const int32_t* __restrict__ rp, int32_t* __restrict__ cnt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int64_t len = (int64_t)rp[i + 1] - rp[i];
+    cnt[i] = len > kSpmmChunk ? (int32_t)((len + kSpmmChunk - 1) / kSpmmChunk) : 0;
+}
+
+__global__ void spmm_plan_fill_kernel(int64_t m, const int32_t* __restrict__ cnt, const int32_t* __restrict__ off,
+                                      int4* __restrict__ chunks) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int32_t k = cnt[i];
+    for (int32_t j = 0; j < k; ++j) chunks[off[i] + j] = make_int4((int)i, j, k, 0);
 }
 
 // ---- CSR transpose ---------------------------------------------------------
@@ -388,37 +408,109 @@ cudaError_t convert_to_float(tsvd_handle* h, int64_t n, const double* x, float* 
     return cudaGetLastError();
 }
 
+template <typename T, int VW, int G>
+static void spmm_launch_all(int64_t m, int64_t n, const int32_t* rp, const int32_t* ci, const T* va, int w, const T* X,
+                            int64_t ldx, T* Y, int64_t ldy, const SpmmPlan* plan, int* status, cudaStream_t st) {
+    const bool split = plan && plan->nchunks > 0;
+    const int64_t per_block = 256 / G;
+    spmm_rows_kernel<T, VW, G><<<(unsigned)((m + per_block - 1) / per_block), 256, 0, st>>>(
+        m, n, rp, ci, va, w, X, ldx, Y, ldy, split ? (int64_t)kSpmmChunk : INT64_MAX, status);
+    if (!split) return;
+    T* part = static_cast<T*>(plan->partial);
+    const int64_t ldp = spmm_partial_ld(w);
+    spmm_chunks_kernel<T, VW, G><<<(unsigned)((plan->nchunks + per_block - 1) / per_block), 256, 0, st>>>(
+        plan->nchunks, plan->chunks, n, rp, ci, va, w, X, ldx, part, ldp, status);
+    spmm_chunk_sum_kernel<T><<<(unsigned)((plan->nchunks + 7) / 8), 256, 0, st>>>(plan->nchunks, plan->chunks, w,
+                                                                                  part, ldp, Y, ldy);
+}
+
+// Lanes per row: enough 16-byte slices to cover w, at most a warp (wider blocks loop over panels).
+template <typename T, int VW>
+static void spmm_dispatch(int64_t m, int64_t n, const int32_t* rp, const int32_t* ci, const T* va, int w, const T* X,
+                          int64_t ldx, T* Y, int64_t ldy, const SpmmPlan* plan, int* status, cudaStream_t st) {
+    const int slices = (w + VW - 1) / VW;
+    if (slices <= 4)
+        spmm_launch_all<T, VW, 4>(m, n, rp, ci, va, w, X, ldx, Y, ldy, plan, status, st);
+    else if (slices <= 8)
+        spmm_launch_all<T, VW, 8>(m, n, rp, ci, va, w, X, ldx, Y, ldy, plan, status, st);
+    else if (slices <= 16)
+        spmm_launch_all<T, VW, 16>(m, n, rp, ci, va, w, X, ldx, Y, ldy, plan, status, st);
+    else
+        spmm_launch_all<T, VW, 32>(m, n, rp, ci, va, w, X, ldx, Y, ldy, plan, status, st);
+}
+
 template <typename T>
 cudaError_t launch_spmm(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr,
                         const int32_t* col_idx, const T* val, int w, const T* X, int64_t ldx, T* Y,
-                        int64_t ldy, int* status, cudaStream_t st) {
+                        int64_t ldy, int* status, cudaStream_t st, const SpmmPlan* plan) {
     if (m == 0 || w == 0) return cudaSuccess;
+    if (plan && plan->nchunks > 0 && w > plan->wmax) return cudaErrorInvalidValue;
     // compulsory traffic: the CSR arrays, X and Y once each
     const double es = (double)sizeof(T);
     ProfScope prof(h, TSVD_K_APROD, 2.0 * nnz * w,
                    (4.0 + es) * nnz + 4.0 * (m + 1) + es * (double)n * w + es * (double)m * w, st);
-    const unsigned blocks = (unsigned)((m + 7) / 8);
-    const bool v2 = (ldx % 2 == 0) && (ldy % 2 == 0) && ((reinterpret_cast<uintptr_t>(X) & (2 * sizeof(T) - 1)) == 0) &&
-                    ((reinterpret_cast<uintptr_t>(Y) & (2 * sizeof(T) - 1)) == 0);
-    h->launches++;
-    if (v2 && w <= 64) {
-        spmm_v2_kernel<T, 1><<<blocks, 256, 0, st>>>(m, n, row_ptr, col_idx, val, w, X, ldx, Y, ldy, status);
-    } else if (v2 && w <= 128) {
-        spmm_v2_kernel<T, 2><<<blocks, 256, 0, st>>>(m, n, row_ptr, col_idx, val, w, X, ldx, Y, ldy, status);
-    } else if (v2) {
-        spmm_v2_kernel<T, 4><<<blocks, 256, 0, st>>>(m, n, row_ptr, col_idx, val, w, X, ldx, Y, ldy, status);
-    } else {
-        spmm_scalar_kernel<T><<<blocks, 256, 0, st>>>(m, n, row_ptr, col_idx, val, w, X, ldx, Y, ldy, status);
-    }
+    // 16-byte gathers need 16-byte aligned X rows
+    const bool v16 = (ldx * sizeof(T)) % 16 == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+    h->launches += (plan && plan->nchunks > 0) ? 3 : 1;
+    if (v16)
+        spmm_dispatch<T, 16 / sizeof(T)>(m, n, row_ptr, col_idx, val, w, X, ldx, Y, ldy, plan, status, st);
+    else
+        spmm_dispatch<T, 1>(m, n, row_ptr, col_idx, val, w, X, ldx, Y, ldy, plan, status, st);
     return cudaGetLastError();
+}
+
+size_t spmm_plan_ws(int64_t m, int64_t nnz, int wmax, size_t elem) {
+    const int64_t maxc = spmm_max_chunks(nnz);
+    Arena ar;
+    ar.take<int32_t>(m + 1);                                     // chunks per row
+    ar.take<int32_t>(m + 1);                                     // their exclusive scan
+    ar.take<int32_t>(m + 1);                                     // scan cursor (unused copy)
+    ar.take<int32_t>((m + kScanTile - 1) / kScanTile + 1);       // tile sums
+    ar.take<int4>(maxc + 1);                                     // chunk descriptors
+    ar.take<char>(elem * (size_t)(maxc + 1) * spmm_partial_ld(wmax));  // partial rows
+    return ar.off;
+}
+
+int spmm_plan(tsvd_handle* h, int64_t m, int64_t nnz, const int32_t* rp, int wmax, size_t elem, Arena& ar,
+              SpmmPlan* plan, cudaStream_t st) {
+    const int64_t maxc = spmm_max_chunks(nnz);
+    int32_t* cnt = ar.take<int32_t>(m + 1);
+    int32_t* off = ar.take<int32_t>(m + 1);
+    int32_t* cur = ar.take<int32_t>(m + 1);
+    int32_t* bsum = ar.take<int32_t>((m + kScanTile - 1) / kScanTile + 1);
+    int4* chunks = ar.take<int4>(maxc + 1);
+    void* partial = ar.take<char>(elem * (size_t)(maxc + 1) * spmm_partial_ld(wmax));
+    if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+    plan->nchunks = 0;
+    plan->chunks = chunks;
+    plan->partial = partial;
+    plan->wmax = wmax;
+    if (m == 0 || nnz <= kSpmmChunk) return TSVD_OK;
+    ProfScope prof(h, TSVD_K_OTHER, 0.0, 0.0, st);
+    const int64_t nb = (m + kScanTile - 1) / kScanTile;
+    h->launches += 5;
+    spmm_plan_count_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(m, rp, cnt);
+    scan_tile_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(m, cnt, off, bsum);
+    scan_sums_kernel<<<1, 1024, 0, st>>>(nb, bsum);
+    scan_add_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(m, off, bsum, cur);
+    spmm_plan_fill_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(m, cnt, off, chunks);
+    TSVD_TRY_CUDA(cudaGetLastError());
+    // number of chunks = off[m-1] + cnt[m-1]
+    int32_t last[2] = {0, 0};
+    TSVD_TRY_CUDA(cudaMemcpyAsync(&last[0], off + (m - 1), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    TSVD_TRY_CUDA(cudaMemcpyAsync(&last[1], cnt + (m - 1), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    TSVD_TRY_CUDA(cudaStreamSynchronize(st));
+    plan->nchunks = (int64_t)last[0] + last[1];
+    if (plan->nchunks > maxc) return TSVD_ERR_INVALID_ARG;  // row_ptr inconsistent with nnz
+    return TSVD_OK;
 }
 
 template cudaError_t launch_spmm<double>(tsvd_handle*, int64_t, int64_t, int64_t, const int32_t*, const int32_t*,
                                          const double*, int, const double*, int64_t, double*, int64_t, int*,
-                                         cudaStream_t);
+                                         cudaStream_t, const SpmmPlan*);
 template cudaError_t launch_spmm<float>(tsvd_handle*, int64_t, int64_t, int64_t, const int32_t*, const int32_t*,
                                         const float*, int, const float*, int64_t, float*, int64_t, int*,
-                                        cudaStream_t);
+                                        cudaStream_t, const SpmmPlan*);
 
 size_t csr_transpose_ws(int64_t m, int64_t n, int64_t nnz) {
     (void)m;

@@ -271,16 +271,27 @@ int tsvd_csr_transpose(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz, const 
     return TSVD_OK;
 }
 
+int tsvd_spmm_workspace(int64_t m, int64_t nnz, int w, size_t* bytes) {
+    if (!bytes || m < 0 || nnz < 0 || w < 0) return TSVD_ERR_INVALID_ARG;
+    *bytes = align256(sizeof(int) * kStCount) + spmm_plan_ws(m, nnz, w, sizeof(double));
+    return TSVD_OK;
+}
+
 int tsvd_spmm(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
               const double* val, int w, const double* X, int64_t ldx, double* Y, int64_t ldy, void* ws,
               size_t ws_bytes, void* stream) {
     if (!h || m < 0 || n < 0 || nnz < 0 || w < 0 || ldx < w || ldy < w || !row_ptr) return TSVD_ERR_INVALID_ARG;
     if (m * (int64_t)w > 0 && (!X || !Y)) return TSVD_ERR_INVALID_ARG;
-    TSVD_TRY(check_ws(ws, ws_bytes, TSVD_SPMM_WORKSPACE));
+    size_t need = 0;
+    TSVD_TRY(tsvd_spmm_workspace(m, nnz, w, &need));
+    TSVD_TRY(check_ws(ws, ws_bytes, need));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int* status = static_cast<int*>(ws);
     TSVD_TRY_CUDA(cudaMemsetAsync(status, 0, sizeof(int) * kStCount, st));
-    TSVD_TRY_CUDA(launch_spmm<double>(h, m, n, nnz, row_ptr, col_idx, val, w, X, ldx, Y, ldy, status, st));
+    Arena ar{static_cast<char*>(ws), ws_bytes, align256(sizeof(int) * kStCount)};
+    SpmmPlan plan;
+    TSVD_TRY(spmm_plan(h, m, nnz, row_ptr, w, sizeof(double), ar, &plan, st));
+    TSVD_TRY_CUDA(launch_spmm<double>(h, m, n, nnz, row_ptr, col_idx, val, w, X, ldx, Y, ldy, status, st, &plan));
     int hs[kStCount];
     TSVD_TRY(read_status(st, status, hs));
     return hs[kStBadCsr] ? TSVD_ERR_INVALID_ARG : TSVD_OK;

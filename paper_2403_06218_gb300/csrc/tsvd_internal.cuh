@@ -149,10 +149,28 @@ int read_status(cudaStream_t st, const int* d_status, int* h_status /* kStCount 
 // y = A x, CSR A (m rows), x (w columns, ldx), y (ldy).  Entries whose column
 // is outside [0, n) are skipped and flag kStBadCsr.
 // T = double (FP64 path) or float (mixed path: FP32 values and blocks).
+// Split plan of a CSR matrix for SpMM: rows longer than kSpmmChunk entries are cut
+// into chunks of kSpmmChunk (descriptor {row, chunk index in the row, chunks of
+// the row, 0}, ordered by row), each summed by its own warp into `partial`.
+constexpr int64_t kSpmmChunk = 1024;
+inline int64_t spmm_max_chunks(int64_t nnz) { return 2 * (nnz / kSpmmChunk) + 1; }
+inline int64_t spmm_partial_ld(int w) { return (w + 1) & ~1; }
+struct SpmmPlan {
+    int64_t nchunks = 0;  // host copy of the chunk count
+    const int4* chunks = nullptr;
+    void* partial = nullptr;  // (nchunks) x spmm_partial_ld(wmax) values of the SpMM type
+    int wmax = 0;
+};
+size_t spmm_plan_ws(int64_t m, int64_t nnz, int wmax, size_t elem);
+// Builds the plan of row_ptr (m rows, nnz entries) in `ar`; synchronises `st` once
+// to read the chunk count.
+int spmm_plan(tsvd_handle* h, int64_t m, int64_t nnz, const int32_t* rp, int wmax, size_t elem, Arena& ar,
+              SpmmPlan* plan, cudaStream_t st);
 template <typename T>
 cudaError_t launch_spmm(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr,
                         const int32_t* col_idx, const T* val, int w, const T* X,
-                        int64_t ldx, T* Y, int64_t ldy, int* status, cudaStream_t st);
+                        int64_t ldx, T* Y, int64_t ldy, int* status, cudaStream_t st,
+                        const SpmmPlan* plan = nullptr);
 
 size_t csr_transpose_ws(int64_t m, int64_t n, int64_t nnz);
 template <typename T>

@@ -86,14 +86,27 @@ def _zipf_truncated(rng, size, a, lo, hi):
     return (np.searchsorted(cdf, rng.random(size), side="right") + lo).astype(np.int64)
 
 
+def _unique_sorted(keys: np.ndarray) -> np.ndarray:
+    """Sorted distinct values of an int64 array (sort, then drop repeats)."""
+    keys = np.sort(keys)
+    if keys.size > 1:
+        keep = np.empty(keys.size, dtype=bool)
+        keep[0] = True
+        np.not_equal(keys[1:], keys[:-1], out=keep[1:])
+        keys = keys[keep]
+    return keys
+
+
 def _trim_to_degree(rng, keys, n, deg):
-    """Keeps, for every row, at most deg[row] of its keys (a seeded random subset)."""
+    """Keeps, for every row, at most deg[row] of its keys (the ones with the smallest
+    seeded random priorities); keys = row * n + col, sorted."""
     m = deg.size
     r = keys // n
     have = np.bincount(r, minlength=m)
     if not np.any(have > deg):
         return keys
-    order = np.lexsort((rng.random(keys.size), r))
+    pri = rng.integers(0, 2 ** 31, size=keys.size, dtype=np.int64)
+    order = np.argsort(r * (2 ** 31) + pri)
     ks, rs = keys[order], r[order]
     start = np.searchsorted(rs, np.arange(m))
     rank = np.arange(ks.size) - start[rs]
@@ -130,7 +143,7 @@ def csr_power_law(m: int, n: int, target_nnz: int, seed: int = 3, deg_exp: float
     cnt = 2 * deg + 4
     rows = np.repeat(np.arange(m, dtype=np.int64), cnt)
     cols = perm[np.minimum(np.searchsorted(cdf, rng.random(rows.size), side="right"), n - 1)]
-    keys = _trim_to_degree(rng, np.unique(rows * n + cols), n, deg)
+    keys = _trim_to_degree(rng, _unique_sorted(rows * n + cols), n, deg)
     for _ in range(50):
         need = deg - np.bincount(keys // n, minlength=m)
         short = np.nonzero(need > 0)[0]
@@ -139,7 +152,7 @@ def csr_power_law(m: int, n: int, target_nnz: int, seed: int = 3, deg_exp: float
         extra = need[short] + need[short] // 8 + 4
         rows = np.repeat(short, extra)
         new = rows * n + rng.integers(0, n, size=rows.size)
-        keys = _trim_to_degree(rng, np.unique(np.concatenate([keys, new])), n, deg)
+        keys = _trim_to_degree(rng, _unique_sorted(np.concatenate([keys, new])), n, deg)
     have = np.bincount(keys // n, minlength=m)
     indptr = np.zeros(m + 1, dtype=np.int64)
     indptr[1:] = np.cumsum(have)
