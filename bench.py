@@ -4,7 +4,9 @@ One step = one full LancSVD solve (Alg. 2: start block, CSR(A^T) build, every
 restart cycle of SpMM / SpMM^T / CGS-CQR2 / Jacobi SVD, the residual checks and
 the Ritz vectors) on a synthetic 100,000 x 100,000 CSR matrix with exactly 10
 uniformly drawn distinct columns per row and N(0,1) values (seed 1), k = b = 64,
-r = 16 blocks, FP64.  A is resident in HBM before the timed region.
+r = 16 blocks, FP64.  The default workload restarts thick (128 Ritz pairs kept);
+``--workload sparse100k-lanczos`` runs the paper's basic restart on the same
+matrix.  A is resident in HBM before the timed region.
 
 Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead
 (host cores, bounded sample).  Multi-GPU (torchrun): independent replicas, one
@@ -14,6 +16,7 @@ problem per rank (seed 1 + rank), no collective on the data path.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import statistics
@@ -34,6 +37,10 @@ WORKLOADS = {
     "sparse100k-lanczos-mixed": dict(kind="csr", m=100_000, n=100_000, d=10, seed=1, method="blanczos",
                                      k=64, b=64, r=16, tol=1e-6, max_restarts=50, oracle_cycles=9,
                                      precision="mixed"),
+    # the same solve with thick restart (128 Ritz pairs kept, 14 new blocks per later cycle)
+    "sparse100k-lanczos-thick": dict(kind="csr", m=100_000, n=100_000, d=10, seed=1, method="blanczos",
+                                     k=64, b=64, r=16, tol=1e-6, max_restarts=50, oracle_cycles=3,
+                                     restart_keep=128),
     "sparse100k-rsvd": dict(kind="csr", m=100_000, n=100_000, d=10, seed=1, method="rsvd",
                             k=64, p=64, q=3),
     "dense512-lanczos": dict(kind="dense", m=512, n=256, seed=0, method="blanczos",
@@ -116,7 +123,8 @@ def _solve(tsvd, cfg, A, seed, profile=False, output="device"):
     prec = cfg.get("precision", "fp64")
     if cfg["method"] == "blanczos":
         return tsvd.blanczos(A, cfg["k"], cfg["b"], cfg["r"], seed=seed, tol=cfg["tol"],
-                             max_restarts=cfg["max_restarts"], profile=profile, output=output, precision=prec)
+                             max_restarts=cfg["max_restarts"], profile=profile, output=output, precision=prec,
+                             restart_keep=cfg.get("restart_keep", 0))
     return tsvd.rsvd(A, cfg["k"], cfg["p"], cfg["q"], seed=seed, profile=profile, output=output, precision=prec)
 
 
@@ -125,14 +133,19 @@ def _oracle_solve(cfg, A, seed, cycles=None):
     if cfg["method"] == "blanczos":
         if cycles is None:
             return oracle.blanczos(A, cfg["k"], cfg["b"], cfg["r"], seed=seed, tol=cfg["tol"],
-                                   max_restarts=cfg["max_restarts"])
-        return oracle.blanczos(A, cfg["k"], cfg["b"], cfg["r"], seed=seed, tol=0.0, max_restarts=cycles - 1)
+                                   max_restarts=cfg["max_restarts"], keep=cfg.get("restart_keep", 0))
+        return oracle.blanczos(A, cfg["k"], cfg["b"], cfg["r"], seed=seed, tol=0.0, max_restarts=cycles - 1,
+                               keep=cfg.get("restart_keep", 0))
     return oracle.rsvd(A, cfg["k"], cfg["p"], cfg["q"], seed=seed)
 
 
 class ClockSampler:
-    """nvidia-smi clock and throttle-reason samples during the timed region."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clock and throttle-reason samples during the timed region.
+
+    The sampler starts before the warm-up steps (nvidia-smi's own start-up takes
+    driver time that would otherwise land in the first timed step) and only the
+    samples stamped inside [mark_start, mark_end] are summarised."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -140,6 +153,13 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
 
     def __enter__(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
@@ -163,26 +183,30 @@ class ClockSampler:
     def summary(self):
         if self.path is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm, smax, reasons = [], [], set()
+        rows = []
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[2]), float(parts[3]),
+                             {nm for nm, v in zip(names, parts[6:10]) if v.lower() == "active"}))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
         os.unlink(self.path)
-        if not sm:
+        inside = [r for r in rows if self.t0 is not None and self.t1 is not None and self.t0 <= r[0] <= self.t1]
+        window = "timed region"
+        if not inside:
+            inside, window = rows, "whole run (no sample fell inside the timed region)"
+        if not inside:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [r[1] for r in inside]
+        reasons = set().union(*[r[3] for r in inside])
         loaded = [v for v in sm if v > 0.5 * max(sm)] or sm
-        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": sorted(reasons), "samples": len(sm), "window": window}
 
 
 def _flush_l2(torch, buf):
@@ -296,7 +320,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--workload", default="sparse100k-lanczos", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="sparse100k-lanczos-thick", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", default=None, choices=("orth", "svd", "tc", "f32", "f64"),
                     help="run one building block at its benchmark shape (for profiler captures) and exit")
@@ -345,17 +369,18 @@ def main(argv=None):
     seed = cfg["seed"] + rank
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
-    for i in range(args.warmup):  # the last one profiled, so the library's CUDA event pool is warm
-        res = _solve(tsvd, cfg, A_dev, seed, profile=(i == args.warmup - 1))
-    torch.cuda.synchronize()
-
-    # ---- timed region: K solves, A resident in HBM, no per-kernel events ----
-    infos = []
-    st = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        for i in range(args.warmup):  # the last one profiled, so the library's CUDA event pool is warm
+            res = _solve(tsvd, cfg, A_dev, seed, profile=(i == args.warmup - 1))
+        torch.cuda.synchronize()
+
+        # ---- timed region: K solves, A resident in HBM, no per-kernel events ----
+        infos = []
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         torch.cuda.synchronize()
+        clk.mark_start()
         e0.record(st)
         for _ in range(args.steps):
             _flush_l2(torch, flush)
@@ -363,6 +388,7 @@ def main(argv=None):
             infos.append(res.info)
         e1.record(st)
         torch.cuda.synchronize()
+        clk.mark_end()
         barrier()
     ms_total = e0.elapsed_time(e1)
     if dist is not None:

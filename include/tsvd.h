@@ -113,7 +113,11 @@ typedef struct tsvd_opts {
                                   where m' >= n' are the dimensions after the m<n transpose */
     void* stream;            /* cudaStream_t */
     int32_t precision;       /* TSVD_PREC_FP64 (default) or TSVD_PREC_MIXED */
-    int32_t reserved;
+    int32_t restart_keep;    /* LancSVD restart: 0 (default) = the paper's basic restart from the
+                                b leading left Ritz vectors; s > 0 = thick restart keeping the s
+                                leading Ritz pairs (k <= s, s + b <= r b) and continuing from
+                                the residual block, with (r b - s) / b new blocks per cycle;
+                                FP64 method only (TSVD_ERR_UNSUPPORTED with TSVD_PREC_MIXED) */
 } tsvd_opts;
 
 /* Per-call report.  Phase times are CUDA-event milliseconds on `stream`. */

@@ -387,7 +387,7 @@ def rsvd(A, k: int, p: int, q: int, seed: int = 0, qr_block: int = 0,
 
 def blanczos(A, k: int, b: int, r: int, seed: int = 0, tol: float = 1e-6,
              max_restarts: int = 50, start_block: Optional[np.ndarray] = None,
-             return_state: bool = False):
+             return_state: bool = False, keep: int = 0):
     """Alg. 2 (LancSVD): block Golub-Kahan-Lanczos with full two-sided block
     re-orthogonalisation (reading G6) and basic restart (Golub, Luk, Overton 1981).
 
@@ -396,42 +396,71 @@ def blanczos(A, k: int, b: int, r: int, seed: int = 0, tol: float = 1e-6,
     ``start_block`` (m x b) replaces the Philox draw when given.  Returns
     (sigma[k], U[m x k], V[n x k], OracleInfo) and, with ``return_state``, the
     last cycle's (P, Pbar, B, Rr, Qbar_{r+1}) in the orientation m >= n.
+
+    ``keep`` = s > 0 selects the thick (augmented) restart that the paper names as
+    future work (Sec. 5; Baglama and Reichel's augmented restarting): a cycle
+    ending with A P = Pbar B + Qbar R E^T and B = Ubar S Vbar^T keeps the s leading
+    Ritz pairs, P~ = P Vbar_s and Pbar~ = Pbar Ubar_s, for which
+        A P~ = Pbar~ S_s + Qbar G,   A^T Pbar~ = P~ S_s,   G = R E^T Vbar_s,
+    and continues the same recurrence from the residual block Qbar: the next right
+    block is A^T Qbar orthogonalised against P~ (its coefficients there are G^T),
+    then the usual steps.  The new cycle's basis is [P~, Q'_1 ... Q'_r'] and
+    [Pbar~, Qbar, Qbar'_2 ...] with r' = (r b - s) / b blocks, and its B is
+        [ S_s   0    0  ... ]
+        [ G     L'_1 0  ... ]
+        [ 0     R'_1 L'_2 ..]   (block lower bidiagonal after the first s columns),
+    so the same Ritz, residual-estimate and output steps apply.  The first cycle
+    is the basic method's.
     """
     op = as_operator(A)
     m, n = op.m, op.n
     rb = r * b
     if not (b >= 1 and r >= 1 and 1 <= k <= rb <= n):
         raise ValueError("need b, r >= 1 and 1 <= k <= r*b <= min(m, n)")
+    if keep and not (k <= keep and keep + b <= rb):
+        raise ValueError("thick restart needs k <= keep and keep + b <= r*b")
     ctx = _Ctx(seed=seed)
     info = OracleInfo(transposed=op.t)
     Omega = gaussian_block(m, b, seed, STREAM_LANCZOS_START) if start_block is None \
         else np.array(start_block, dtype=np.float64, copy=True)
     Qbar1, _ = cholqr2(Omega, ctx)                               # S1
+    s0 = 0                        # Ritz pairs kept from the previous cycle (thick restart)
+    Pk = Pbk = Sk = Qlast = None
     while True:
-        P = np.zeros((n, rb))
-        Pbar = np.zeros((m, rb))
-        B = np.zeros((rb, rb))
-        Pbar[:, :b] = Qbar1
-        Rr = Qlast = None
-        for i in range(r):
-            c0, c1 = i * b, (i + 1) * b
+        nblk = r if s0 == 0 else (rb - s0) // b
+        d = s0 + nblk * b
+        P = np.zeros((n, d))
+        Pbar = np.zeros((m, d))
+        B = np.zeros((d, d))
+        if s0 == 0:
+            Pbar[:, :b] = Qbar1
+        else:
+            P[:, :s0] = Pk
+            Pbar[:, :s0] = Pbk
+            B[:s0, :s0] = np.diag(Sk)
+            Pbar[:, s0:s0 + b] = Qlast
+        Rr = None
+        for i in range(nblk):
+            c0, c1 = s0 + i * b, s0 + (i + 1) * b
             Qi = op.tmul(Pbar[:, c0:c1])                          # S2
-            if i == 0:
+            if c0 == 0:
                 Qi, T = cholqr2(Qi, ctx)                          # S3a
             else:
-                Qi, _, T = cgs_cqr2(Qi, P[:, :c0], ctx)           # S3b
+                Qi, H, T = cgs_cqr2(Qi, P[:, :c0], ctx)           # S3b
+                if i == 0:                                        # coupling with the kept pairs
+                    B[c0:c1, :s0] = H.T
             P[:, c0:c1] = Qi
             B[c0:c1, c0:c1] = T.T                                 # L_i
             Qn = op.mul(Qi)                                       # S4
             Qn, _, Ri = cgs_cqr2(Qn, Pbar[:, :c1], ctx)           # S5
-            if i + 1 < r:
+            if i + 1 < nblk:
                 Pbar[:, c1:c1 + b] = Qn
                 B[c1:c1 + b, c0:c1] = Ri                          # R_i
             else:
                 Rr, Qlast = Ri, Qn
         info.iterations += 1
         Ub, s, Vb = small_svd(B)                                  # S6
-        rho = np.linalg.norm(Rr @ Vb[rb - b:rb, :k], axis=0)      # G21
+        rho = np.linalg.norm(Rr @ Vb[d - b:d, :k], axis=0)        # G21
         info.rho_hist.append(float(np.max(rho) / s[0]) if s[0] > 0 else float("nan"))
         done = info.rho_hist[-1] <= tol
         if done or info.restarts >= max_restarts:
@@ -443,7 +472,11 @@ def blanczos(A, k: int, b: int, r: int, seed: int = 0, tol: float = 1e-6,
                 info.converged = bool(info.resid_max <= tol)
                 break
         info.restarts += 1
-        Qbar1, _ = cholqr2(Pbar @ Ub[:, :b], ctx)                 # S7 (reading G18)
+        if keep:
+            Pk, Pbk, Sk = P @ Vb[:, :keep], Pbar @ Ub[:, :keep], s[:keep].copy()
+            s0 = keep
+        else:
+            Qbar1, _ = cholqr2(Pbar @ Ub[:, :b], ctx)             # S7 (reading G18)
     U, V = _output_signs(U, V)
     info.breakdowns = ctx.fallbacks
     if op.t:

@@ -48,7 +48,7 @@ class TsvdOpts(C.Structure):
         ("tol", C.c_double), ("max_restarts", C.c_int32), ("qr_block", C.c_int32),
         ("output_location", C.c_int32), ("flags", C.c_int32),
         ("start_block", C.c_void_p), ("stream", C.c_void_p),
-        ("precision", C.c_int32), ("reserved", C.c_int32),
+        ("precision", C.c_int32), ("restart_keep", C.c_int32),
     ]
 
 

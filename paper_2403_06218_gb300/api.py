@@ -168,7 +168,7 @@ _PRECISIONS = {"fp64": capi.TSVD_PREC_FP64, "mixed": capi.TSVD_PREC_MIXED}
 
 
 def _run_driver(fn_name, method, A, k, a, c, seed, tol, max_restarts, qr_block, start_block, output, device,
-                profile=False, precision="fp64"):
+                profile=False, precision="fp64", restart_keep=0):
     lib = capi.load()
     desc, keep, dev = _desc(A)
     if dev is None:
@@ -183,6 +183,7 @@ def _run_driver(fn_name, method, A, k, a, c, seed, tol, max_restarts, qr_block, 
     if precision not in _PRECISIONS:
         raise ValueError(f"precision must be one of {sorted(_PRECISIONS)}")
     opts.precision = _PRECISIONS[precision]
+    opts.restart_keep = int(restart_keep)
     if start_block is not None:
         if not (isinstance(start_block, torch.Tensor) and start_block.is_cuda and start_block.dtype == torch.float64
                 and start_block.is_contiguous()):
@@ -214,13 +215,14 @@ def _run_driver(fn_name, method, A, k, a, c, seed, tol, max_restarts, qr_block, 
 
 def blanczos(A, k: int, b: int, r: int, seed: int = 0, tol: float = 1e-6, max_restarts: int = 50,
              start_block: Optional[torch.Tensor] = None, output: str = "device", device=None,
-             profile: bool = False, precision: str = "fp64") -> SvdResult:
+             profile: bool = False, precision: str = "fp64", restart_keep: int = 0) -> SvdResult:
     """LancSVD (Alg. 2): k triplets with blocks of width b, r blocks per restart cycle.
     ``profile`` times every kernel class with CUDA events (``info['prof_*']``);
     ``precision="mixed"`` selects the FP32-product form with FP64 small algebra
-    and a final FP64 Rayleigh-Ritz step."""
+    and a final FP64 Rayleigh-Ritz step; ``restart_keep=s > 0`` selects the thick
+    restart that keeps the s leading Ritz pairs (0: the paper's basic restart)."""
     return _run_driver("tsvd_blanczos", capi.TSVD_METHOD_BLANCZOS, A, k, b, r, seed, tol, max_restarts, 0,
-                       start_block, output, device, profile, precision)
+                       start_block, output, device, profile, precision, restart_keep)
 
 
 def rsvd(A, k: int, p: int, q: int, seed: int = 0, qr_block: int = 0, start_block: Optional[torch.Tensor] = None,

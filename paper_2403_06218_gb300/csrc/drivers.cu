@@ -585,9 +585,14 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
     float ms_t = 0.f;
     TSVD_TRY(setup_op<T>(h, A, b > k ? b : k, ar, op, status, st, run, A->format == TSVD_CSR ? &ms_t : nullptr));
     const int64_t m = op.m, n = op.n;
+    const int keep = o->restart_keep;                   // thick restart when > 0
+    const int nv = std::max(std::max(k, b), keep);      // right vectors the small SVD must return
     T* P = ar.take<T>((size_t)n * rb);
     T* Pbar = ar.take<T>((size_t)m * rb);
     T* Qnext = ar.take<T>((size_t)m * b);
+    T* Pk = keep ? ar.take<T>((size_t)n * keep) : nullptr;    // P Vbar_s, Pbar Ubar_s
+    T* Pbk = keep ? ar.take<T>((size_t)m * keep) : nullptr;
+    double* Hk = keep ? ar.take<double>((size_t)keep * b) : nullptr;  // coefficients of A^T Qbar on P Vbar_s
     double* B = ar.take<double>((size_t)rb * rb);
     double* Ub = ar.take<double>((size_t)rb * rb);
     double* Vb = ar.take<double>((size_t)rb * rb);
@@ -629,15 +634,24 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
     // Every orthogonalisation is checked as it completes: near convergence the first
     // S5 after a restart breaks down in most cycles (converged Ritz vectors deflate
     // the new block), so its fallback must run at once.
+    // s0 = Ritz pairs carried into the current cycle (thick restart), d = its dimension:
+    // basis [P~ (s0), Q_1 .. Q_nblk], [Pbar~ (s0), Qbar_1 .. Qbar_nblk], B d x d with
+    // diag(S_s0) and the coupling block G below it (see the thick-restart reading)
+    int s0 = 0;
     for (;;) {
-        TSVD_TRY_CUDA(cudaMemsetAsync(B, 0, sizeof(double) * (size_t)rb * rb, st));
-        for (int i = 0; i < r; ++i) {
-            const int c0 = i * b;
+        const int nblk = s0 == 0 ? r : (rb - s0) / b;
+        const int d = s0 + nblk * b;
+        if (s0 == 0) TSVD_TRY_CUDA(cudaMemsetAsync(B, 0, sizeof(double) * (size_t)rb * rb, st));
+        for (int i = 0; i < nblk; ++i) {
+            const int c0 = s0 + i * b;
             T* Qi = P + c0;
             TSVD_TRY(op_tmul<T>(h, op, b, Pbar + c0, rb, Qi, rb, status, st));                    // S2
             double* Lii = B + (int64_t)c0 * rb + c0;
-            TSVD_TRY(cgs_cqr2<T>(h, n, c0, b, P, rb, Qi, rb, nullptr, Lii, rb, true, ctx, ar, status, st));  // S3
-            const bool last = (i + 1 == r);
+            const bool couple = (i == 0 && s0 > 0);
+            TSVD_TRY(cgs_cqr2<T>(h, n, c0, b, P, rb, Qi, rb, couple ? Hk : nullptr, Lii, rb, true, ctx, ar, status,
+                                 st));                                                                // S3
+            if (couple) TSVD_TRY_CUDA(put_transposed(h, s0, b, Hk, b, B + (int64_t)c0 * rb, rb, st));  // G
+            const bool last = (i + 1 == nblk);
             T* dst = last ? Qnext : Pbar + c0 + b;
             const int64_t ldd = last ? b : rb;
             TSVD_TRY(op_mul<T>(h, op, b, Qi, rb, dst, ldd, status, st));                             // S4
@@ -648,22 +662,22 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
         ++cycles;
         {
             Arena sv = ar;
-            TSVD_TRY(small_svd(h, rb, B, rb, Ub, sig, Vb, k > b ? k : b, sv, status, st));          // S6
+            TSVD_TRY(small_svd(h, d, B, rb, Ub, sig, Vb, nv, sv, status, st));                      // S6
         }
-        TSVD_TRY_CUDA(lanczos_rho(h, b, k, Rr, Vb + (int64_t)(rb - b) * rb, rb, rho, st));
+        TSVD_TRY_CUDA(lanczos_rho(h, b, k, Rr, Vb + (int64_t)(d - b) * d, d, rho, st));
         TSVD_TRY_CUDA(cudaMemcpyAsync(hrho.data(), rho, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
         TSVD_TRY_CUDA(cudaMemcpyAsync(hsig.data(), sig, sizeof(double), cudaMemcpyDeviceToHost, st));
         TSVD_TRY(read_status(st, status, hs));
         TSVD_TRY(status_code(hs));
         sweeps = hs[kStSweeps];
-        prof_set_last_flops(h, TSVD_K_SVD, jacobi_flops(rb, k > b ? k : b, sweeps));
+        prof_set_last_flops(h, TSVD_K_SVD, jacobi_flops(d, nv, sweeps));
         double rmax = 0.0;
         for (int j = 0; j < k; ++j) rmax = std::fmax(rmax, hrho[j]);
         rho_last = hsig[0] > 0.0 ? rmax / hsig[0] : NAN;
         const bool done = rho_last <= o->tol;
         if (done || restarts >= o->max_restarts) {
             // S8/S9 (and the FP64 Rayleigh-Ritz step in the mixed form)
-            TSVD_TRY(final_triplets<T>(h, op, k, Pbar, rb, Ub, rb, P, rb, Vb, rb, rb, sig, f, dU, dV, dsig, ctx, ar,
+            TSVD_TRY(final_triplets<T>(h, op, k, Pbar, rb, Ub, d, P, rb, Vb, d, d, sig, f, dU, dV, dsig, ctx, ar,
                                        status, st, nullptr));
             TSVD_TRY(explicit_residual<T>(h, op, k, dU, dV, dsig, f, status, st, &resid));
             if ((done && resid <= o->tol) || restarts >= o->max_restarts) {
@@ -672,10 +686,23 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
             }
         }
         ++restarts;
-        // S7: Qbar_1 = Pbar Ubar_1, re-orthonormalised by CholeskyQR2
-        TSVD_TRY_CUDA((gemm_nn<T, double, T>(h, m, rb, b, 1.0, Pbar, rb, Ub, rb, 0.0, Qnext, b, false, st)));
-        TSVD_TRY_CUDA(copy_block<T>(Qnext, b, Pbar, rb, m, b, st));
-        TSVD_TRY(cgs_cqr2<T>(h, m, 0, b, nullptr, 0, Pbar, rb, nullptr, Rr, b, false, ctx, ar, status, st));
+        if (keep > 0) {
+            // thick restart: P~ = P Vbar_s, Pbar~ = Pbar Ubar_s, B = diag(S_s) on them, and the
+            // residual block Qbar_{r+1} continues the recurrence as the next left block
+            TSVD_TRY_CUDA((gemm_nn<T, double, T>(h, n, d, keep, 1.0, P, rb, Vb, d, 0.0, Pk, keep, false, st)));
+            TSVD_TRY_CUDA((gemm_nn<T, double, T>(h, m, d, keep, 1.0, Pbar, rb, Ub, d, 0.0, Pbk, keep, false, st)));
+            TSVD_TRY_CUDA(copy_block<T>(Pk, keep, P, rb, n, keep, st));
+            TSVD_TRY_CUDA(copy_block<T>(Pbk, keep, Pbar, rb, m, keep, st));
+            TSVD_TRY_CUDA(copy_block<T>(Qnext, b, Pbar + keep, rb, m, b, st));
+            TSVD_TRY_CUDA(cudaMemsetAsync(B, 0, sizeof(double) * (size_t)rb * rb, st));
+            TSVD_TRY_CUDA(put_diagonal(h, keep, sig, B, rb, st));
+            s0 = keep;
+        } else {
+            // S7: Qbar_1 = Pbar Ubar_1, re-orthonormalised by CholeskyQR2
+            TSVD_TRY_CUDA((gemm_nn<T, double, T>(h, m, rb, b, 1.0, Pbar, rb, Ub, rb, 0.0, Qnext, b, false, st)));
+            TSVD_TRY_CUDA(copy_block<T>(Qnext, b, Pbar, rb, m, b, st));
+            TSVD_TRY(cgs_cqr2<T>(h, m, 0, b, nullptr, 0, Pbar, rb, nullptr, Rr, b, false, ctx, ar, status, st));
+        }
     }
     TSVD_TRY(read_status(st, status, hs));
     TSVD_TRY(status_code(hs));

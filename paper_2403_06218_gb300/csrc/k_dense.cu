@@ -460,6 +460,19 @@ __global__ void apply_sign_kernel(int64_t rows, int k, double* __restrict__ A, i
     if (sgn[j] < 0.0) A[i * lda + j] = -A[i * lda + j];
 }
 
+__global__ void put_transposed_kernel(int rows, int cols, const double* __restrict__ H, int64_t ldh,
+                                      double* __restrict__ D, int64_t ldd) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)rows * cols) return;
+    const int i = (int)(idx / cols), j = (int)(idx % cols);
+    D[(int64_t)j * ldd + i] = H[(int64_t)i * ldh + j];
+}
+
+__global__ void put_diagonal_kernel(int s, const double* __restrict__ sig, double* __restrict__ B, int64_t ldb) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < s) B[(int64_t)i * ldb + i] = sig[i];
+}
+
 int colres_groups(int64_t q) {
     int64_t g = (q + 255) / 256;
     if (g > 512) g = 512;
@@ -609,6 +622,22 @@ cudaError_t col_residual_sq(tsvd_handle* h, int64_t q, int k, const double* Y, i
     h->launches += 2;
     colres_partial_kernel<<<g, 128, 0, st>>>(q, k, Y, ldy, U, ldu, sigma, partial, rows_per);
     colres_reduce_kernel<<<1, 128, 0, st>>>(k, g, partial, out);
+    return cudaGetLastError();
+}
+
+cudaError_t put_transposed(tsvd_handle* h, int rows, int cols, const double* H, int64_t ldh, double* D, int64_t ldd,
+                           cudaStream_t st) {
+    if (rows == 0 || cols == 0) return cudaSuccess;
+    const int64_t tot = (int64_t)rows * cols;
+    h->launches++;
+    put_transposed_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(rows, cols, H, ldh, D, ldd);
+    return cudaGetLastError();
+}
+
+cudaError_t put_diagonal(tsvd_handle* h, int s, const double* sig, double* B, int64_t ldb, cudaStream_t st) {
+    if (s == 0) return cudaSuccess;
+    h->launches++;
+    put_diagonal_kernel<<<(unsigned)((s + 255) / 256), 256, 0, st>>>(s, sig, B, ldb);
     return cudaGetLastError();
 }
 

@@ -248,6 +248,11 @@ cudaError_t col_residual_sq(tsvd_handle* h, int64_t q, int k, const double* Y, i
                             double* partial, cudaStream_t st);
 
 // rho[j] = || Rr * Vlast[:, j] ||_2, Rr b x b upper (ld b), Vlast b rows of Vbar (ld ldv), j < k.
+// D (cols x rows, ld ldd) = H^T for H rows x cols (ld ldh).
+cudaError_t put_transposed(tsvd_handle* h, int rows, int cols, const double* H, int64_t ldh, double* D, int64_t ldd,
+                           cudaStream_t st);
+// B[i][i] = sig[i], i < s.
+cudaError_t put_diagonal(tsvd_handle* h, int s, const double* sig, double* B, int64_t ldb, cudaStream_t st);
 cudaError_t lanczos_rho(tsvd_handle* h, int b, int k, const double* Rr, const double* Vlast,
                         int64_t ldv, double* rho, cudaStream_t st);
 

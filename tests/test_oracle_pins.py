@@ -360,3 +360,52 @@ def test_householder_workload_has_its_spectrum_and_vectors():
     assert np.abs(A @ HV[:, :5] - HU[:, :5] * s[:5]).max() < 1e-14
     At, _ = workloads.dense_householder_spectrum_torch(m, n, seed=2, L=16, device="cpu")
     assert np.abs(At.numpy() - A).max() < 1e-14
+
+
+# ------------------------------------------------------------------ thick restart (keep > 0)
+def test_blanczos_thick_restart_relations_and_coupling_block():
+    """After a thick restart the cycle still satisfies A P = Pbar B + Qbar R E^T and
+    A^T Pbar = P B^T with orthonormal bases; B is diag(S_s) on the kept pairs, the
+    coupling block below them equals G = R_r E^T Vbar_s of the previous cycle, and
+    everything else outside the block lower bidiagonal part is zero."""
+    A = workloads.csr_uniform(700, 400, 9, seed=11).toarray()
+    k, b, r, keep = 6, 6, 5, 12
+    # cycle 1 alone, then cycles 1-2 from the same start
+    _, _, _, _, st1 = O.blanczos(A, k, b, r, seed=4, tol=0.0, max_restarts=0, keep=keep, return_state=True)
+    _, _, _, info2, st2 = O.blanczos(A, k, b, r, seed=4, tol=0.0, max_restarts=1, keep=keep, return_state=True)
+    assert info2.iterations == 2
+    P1, Pb1, B1, R1, Q1 = st1
+    P, Pb, B, R, Q = st2
+    d = P.shape[1]
+    assert d == keep + ((r * b - keep) // b) * b
+    E = np.zeros((d, b))
+    E[d - b:, :] = np.eye(b)
+    assert np.abs(A @ P - Pb @ B - Q @ R @ E.T).max() < 1e-12 * np.abs(A).max() * d
+    assert np.abs(A.T @ Pb - P @ B.T).max() < 1e-12 * np.abs(A).max() * d
+    assert np.abs(P.T @ P - np.eye(d)).max() < 1e-13 and np.abs(Pb.T @ Pb - np.eye(d)).max() < 1e-13
+    Ub1, s1, Vb1 = np.linalg.svd(B1)
+    np.testing.assert_allclose(np.diag(B[:keep, :keep]), s1[:keep], rtol=1e-13)
+    assert np.abs(B[:keep, :keep] - np.diag(np.diag(B[:keep, :keep]))).max() == 0.0
+    G = R1 @ Vb1.T[B1.shape[0] - b:, :keep]          # R_r E^T Vbar_s (signs of the SVD vectors...)
+    # singular vectors are unique up to sign: compare |G| column by column
+    np.testing.assert_allclose(np.abs(B[keep:keep + b, :keep]), np.abs(G), atol=1e-12 * s1[0])
+    assert np.abs(B[:keep, keep:]).max() == 0.0 and np.abs(B[keep + b:, :keep]).max() == 0.0
+    for i in range(keep, d, b):  # nothing above the block diagonal in the bidiagonal part
+        assert np.abs(B[i:i + b, i + b:]).max(initial=0.0) == 0.0
+    # the kept right Ritz vectors span P Vbar_s of cycle 1
+    assert subspace_sin(P[:, :keep], P1 @ Vb1.T[:, :keep]) < 1e-12
+
+
+def test_blanczos_thick_restart_converges_to_known_spectrum_with_fewer_products():
+    A, s_true, U0, V0 = workloads.dense_known_spectrum(512, 256, seed=0)
+    tol = 1e-8
+    s, U, V, info = O.blanczos(A, 10, 16, 4, seed=0, tol=tol, max_restarts=200, keep=32)
+    assert info.converged and info.resid_max <= tol
+    assert np.max(np.abs(s - s_true[:10])) <= 2 * tol * s_true[0]
+    relgap = (s_true[9] - s_true[10]) / s_true[0]
+    assert subspace_sin(U, U0[:, :10]) < 10 * tol / relgap and subspace_sin(V, V0[:, :10]) < 10 * tol / relgap
+    assert np.abs(A.T @ U - V * s).max() < 1e-13  # exact by construction, as for basic restart
+    # A-products: cycle 1 has r blocks, later cycles (r b - keep) / b; fewer in total than basic restart
+    _, _, _, ib = O.blanczos(A, 10, 16, 4, seed=0, tol=tol, max_restarts=200)
+    thick_blocks = 4 + (info.iterations - 1) * ((64 - 32) // 16)
+    assert thick_blocks < 4 * ib.iterations, (thick_blocks, 4 * ib.iterations)
