@@ -27,3 +27,4 @@ from .tsvd_oracle import (  # noqa: F401
     as_operator,
     OracleInfo,
 )
+from .tsvd_backward import svd_backward  # noqa: F401
