@@ -276,6 +276,36 @@ def run_case(case):
         P = tsvd.cgs_qr(torch.randn(100_000, 960, dtype=torch.float64, device="cuda", generator=g), 128)[0]
         Y = torch.randn(100_000, 64, dtype=torch.float64, device="cuda", generator=g)
         call = lambda: tsvd.cgs_cqr2(Y, P)  # noqa: E731
+    elif case == "backward":
+        # gradient of sum(sigma) + ||U^T X||^2 for the 200,000 x 200,000 (5M nnz) sparse
+        # workload, k = b = 32, r = 16, thick restart keeping 128
+        import numpy as np
+        import workloads
+        A = workloads.csr_uniform(200_000, 200_000, 25, seed=4)
+        Ad = tsvd.CsrMatrix.from_scipy(A)
+        X = torch.from_numpy(np.random.default_rng(4).standard_normal((200_000, 32))).cuda()
+        res = tsvd.blanczos(Ad, 32, 32, 16, seed=0, tol=1e-10, max_restarts=200, restart_keep=128)
+        sb = torch.ones(32, dtype=torch.float64, device="cuda")
+        Ub = 2 * X @ (X.T @ res.U)
+        info = {}
+
+        def call():
+            g, inf = tsvd.svd_backward(Ad, res.sigma, res.U, res.V, sb, Ub)
+            info.update(inf)
+            return g
+        out = None
+        times = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            out = call()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        print(json.dumps({"case": case, "ms": times, "forward_ms": res.info["ms_total"],
+                          "forward_cycles": res.info["iterations"], "cg_iters": [info["cg_iters_u"], info["cg_iters_v"]],
+                          "cg_resid": info["cg_resid_u"]}))
+        return 0
     elif case in ("tc", "f32", "f64"):
         # dense A Q of the 20,000 x 20,000 workload with a 128-column block: split-BF16 tensor
         # cores (tc), FP32 CUDA cores (f32) or FP64 (f64)
@@ -322,7 +352,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--workload", default="sparse100k-lanczos-thick", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default=None, choices=("orth", "svd", "tc", "f32", "f64"),
+    ap.add_argument("--case", default=None, choices=("orth", "svd", "tc", "f32", "f64", "backward"),
                     help="run one building block at its benchmark shape (for profiler captures) and exit")
     args = ap.parse_args(argv)
     cfg = WORKLOADS[args.workload]

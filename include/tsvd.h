@@ -240,6 +240,48 @@ int tsvd_dense_mm_f32(tsvd_handle* h, int trans, int64_t m, int64_t n, const flo
                       int w, const float* X, int64_t ldx, float* Y, int64_t ldy,
                       void* ws, size_t ws_bytes, void* stream);
 
+/* ---- gradient of a loss on the k leading triplets (differentiation; the paper
+ * has no backward pass) ----------------------------------------------------
+ * Given the k leading triplets (sigma, U, V) of A, as tsvd_blanczos / tsvd_rsvd
+ * return them, and the adjoints of a scalar loss L, sigma_bar = dL/dsigma (k),
+ * U_bar = dL/dU (m x k), V_bar = dL/dV (n x k) (each may be NULL = 0), computes
+ * dL/dA for the truncated SVD exactly (the other singular values of A need not
+ * be zero):
+ *   dL/dA = U C V^T + Y S V^T + U (A^T Y)^T + U S Z^T + (A Z) V^T,
+ *   C = (F o (J - J^T)) S + diag(sigma_bar) + S (F o (K - K^T)),
+ *   J = U^T U_bar, K = V^T V_bar, F_ij = 1/(s_j^2 - s_i^2) (i != j), S = diag(sigma),
+ * with y_j, z_j the solutions of (s_j^2 I - A A^T) y_j = (I - UU^T) u_bar_j and
+ * (s_j^2 I - A^T A) z_j = (I - VV^T) v_bar_j on the complements of span(U), span(V)
+ * (conjugate gradients, one shift per column; positive definite there when
+ * sigma_k > sigma_{k+1}).  Requires distinct sigma_1..sigma_k.
+ *   grad: CSR A: nnz values on A's pattern, in CSR order (an SDDMM of the rank-2k
+ *         factors); dense A: m x n row-major (ld n).  Device memory.
+ *   All inputs are device FP64 row-major (U ld k, V ld k); A as for the solvers
+ *   (FP64 or FP32 values, device or host).
+ * Returns TSVD_NOT_CONVERGED (with the gradient of the last CG iterate) if a
+ * solve did not reach cg_tol within cg_max_iter iterations. */
+typedef struct tsvd_backward_opts {
+    double cg_tol;           /* relative residual of every complement solve (default 1e-12) */
+    int32_t cg_max_iter;     /* per side (default 20000) */
+    int32_t check_every;     /* CG iterations between convergence reads (default 10) */
+    void* stream;            /* cudaStream_t */
+} tsvd_backward_opts;
+
+typedef struct tsvd_backward_info {
+    int32_t cg_iters_u;      /* CG iterations of the U-side (A A^T) solves */
+    int32_t cg_iters_v;      /* CG iterations of the V-side (A^T A) solves */
+    double cg_resid_u;       /* largest final relative residual, U side */
+    double cg_resid_v;       /* same, V side */
+    double ms_total;         /* device time of the call (CUDA events) */
+} tsvd_backward_info;
+
+void tsvd_default_backward_opts(tsvd_backward_opts* opts);
+int tsvd_svd_backward_workspace(const tsvd_matrix* A, int k, const tsvd_backward_opts* opts, size_t* bytes);
+int tsvd_svd_backward(tsvd_handle* h, const tsvd_matrix* A, int k, const double* sigma, const double* U,
+                      const double* V, const double* sigma_bar, const double* U_bar, const double* V_bar,
+                      double* grad, const tsvd_backward_opts* opts, void* ws, size_t ws_bytes,
+                      tsvd_backward_info* info);
+
 /* Tensor-core products of the mixed form for dense A.  A (or A^T) is stored
  * once as three BF16 pieces, A = A0 + A1 + A2 to 24 significant bits, and the
  * block X as three pieces too; Y = sum of the six terms A_i X_j with i + j <= 2

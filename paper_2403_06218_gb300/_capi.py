@@ -70,6 +70,19 @@ class TsvdInfo(C.Structure):
         return out
 
 
+class TsvdBackwardOpts(C.Structure):
+    _fields_ = [("cg_tol", C.c_double), ("cg_max_iter", C.c_int32), ("check_every", C.c_int32),
+                ("stream", C.c_void_p)]
+
+
+class TsvdBackwardInfo(C.Structure):
+    _fields_ = [("cg_iters_u", C.c_int32), ("cg_iters_v", C.c_int32), ("cg_resid_u", C.c_double),
+                ("cg_resid_v", C.c_double), ("ms_total", C.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 # (name, restype, argtypes); every symbol listed here is declared in include/tsvd.h.
 _P = C.c_void_p
 _I = C.c_int
@@ -95,6 +108,9 @@ SIGNATURES = [
     ("tsvd_dense_mm_workspace", _I, [_I, _I64, _I64, _I, _PSZ]),
     ("tsvd_dense_mm", _I, [_P, _I, _I64, _I64, _P, _I64, _I, _P, _I64, _P, _I64, _P, _SZ, _P]),
     ("tsvd_dense_mm_f32", _I, [_P, _I, _I64, _I64, _P, _I64, _I, _P, _I64, _P, _I64, _P, _SZ, _P]),
+    ("tsvd_default_backward_opts", None, [_P]),
+    ("tsvd_svd_backward_workspace", _I, [_P, _I, _P, _PSZ]),
+    ("tsvd_svd_backward", _I, [_P, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     ("tsvd_bf16x3_bytes", _I, [_I64, _I64, _PSZ]),
     ("tsvd_bf16x3_split", _I, [_P, _I, _I64, _I64, _P, _I64, _P, _P]),
     ("tsvd_mm_bf16x6_workspace", _I, [_I64, _I64, _I, _PSZ]),

@@ -317,6 +317,91 @@ def dense_mm(A: torch.Tensor, X: torch.Tensor, trans: bool = False) -> torch.Ten
     return Y
 
 
+# ---------------------------------------------------------------------------
+# Gradient with respect to A, and a differentiable truncated SVD.
+# ---------------------------------------------------------------------------
+def svd_backward(A, sigma: torch.Tensor, U: torch.Tensor, V: torch.Tensor, sigma_bar=None, U_bar=None, V_bar=None,
+                 cg_tol: float = 1e-12, cg_max_iter: int = 20000):
+    """dL/dA of a loss on the k leading triplets (sigma, U, V) of A, given the
+    adjoints dL/dsigma, dL/dU, dL/dV (None = 0): the values on A's pattern for a
+    CsrMatrix (CSR order), the dense m x n gradient for a dense A.  Returns
+    (grad, info)."""
+    lib = capi.load()
+    desc, keep, dev = _desc(A)
+    if dev is None:
+        raise TypeError("A must be on the GPU")
+    k = int(sigma.numel())
+    m, n = int(desc.m), int(desc.n)
+
+    def f64(t, shape, name):
+        if t is None:
+            return None
+        t = t.detach().to(device=dev, dtype=torch.float64).contiguous()
+        if tuple(t.shape) != shape:
+            raise ValueError(f"{name} must have shape {shape}")
+        return t
+
+    s_, U_, V_ = f64(sigma, (k,), "sigma"), f64(U, (m, k), "U"), f64(V, (n, k), "V")
+    sb, Ub, Vb = f64(sigma_bar, (k,), "sigma_bar"), f64(U_bar, (m, k), "U_bar"), f64(V_bar, (n, k), "V_bar")
+    opts = capi.TsvdBackwardOpts()
+    lib.tsvd_default_backward_opts(C.byref(opts))
+    opts.cg_tol = float(cg_tol)
+    opts.cg_max_iter = int(cg_max_iter)
+    sparse = isinstance(A, CsrMatrix)
+    grad = torch.empty((A.nnz,) if sparse else (m, n), dtype=torch.float64, device=dev)
+    info = capi.TsvdBackwardInfo()
+    with torch.cuda.device(dev):
+        opts.stream = _stream_ptr(dev)
+        nb = C.c_size_t()
+        capi.check(lib.tsvd_svd_backward_workspace(C.byref(desc), k, C.byref(opts), C.byref(nb)),
+                   "tsvd_svd_backward_workspace")
+        ws = _ws(nb.value, dev)
+        rc = lib.tsvd_svd_backward(handle(dev), C.byref(desc), k, _ptr(s_), _ptr(U_), _ptr(V_),
+                                   _ptr(sb) if sb is not None else None, _ptr(Ub) if Ub is not None else None,
+                                   _ptr(Vb) if Vb is not None else None, grad.data_ptr(), C.byref(opts),
+                                   ws.data_ptr(), ws.numel(), C.byref(info))
+        capi.check(rc, "tsvd_svd_backward", allow_not_converged=True)
+    del keep
+    return grad, info.as_dict()
+
+
+class _TruncatedSVD(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, data, structure, k, solve, bwd):
+        A = data if structure is None else CsrMatrix(structure[0], structure[1], data, structure[2])
+        res = blanczos(A, k, **solve)
+        if res.status != 0:
+            raise capi.TsvdError(res.status, "truncated_svd (LancSVD did not converge)")
+        ctx.structure = structure
+        ctx.bwd = bwd
+        ctx.save_for_backward(data, res.sigma, res.U, res.V)
+        return res.sigma, res.U, res.V
+
+    @staticmethod
+    def backward(ctx, gs, gU, gV):
+        data, sigma, U, V = ctx.saved_tensors
+        st = ctx.structure
+        A = data if st is None else CsrMatrix(st[0], st[1], data, st[2])
+        grad, _ = svd_backward(A, sigma, U, V, gs, gU, gV, **ctx.bwd)
+        return grad.to(data.dtype), None, None, None, None
+
+
+def truncated_svd(A, k: int, b: int, r: int, seed: int = 0, tol: float = 1e-10, max_restarts: int = 200,
+                  restart_keep: int = 0, cg_tol: float = 1e-12):
+    """Differentiable k leading singular triplets (sigma, U, V) by LancSVD (FP64).
+
+    A: a dense CUDA tensor, or a CsrMatrix whose ``val`` may require grad.
+    Gradients with respect to A (dense) or to the CSR values flow through
+    tsvd_svd_backward (exact for the truncated SVD; complement terms by CG).
+    The loss should not depend on the signs of the singular vectors (the sign
+    convention makes them locally constant)."""
+    solve = dict(b=b, r=r, seed=seed, tol=tol, max_restarts=max_restarts, restart_keep=restart_keep)
+    bwd = dict(cg_tol=cg_tol)
+    if isinstance(A, CsrMatrix):
+        return _TruncatedSVD.apply(A.val, (A.row_ptr, A.col_idx, A.shape), k, solve, bwd)
+    return _TruncatedSVD.apply(A, None, k, solve, bwd)
+
+
 @dataclasses.dataclass
 class Bf16x3:
     """Three BF16 pieces of a rows x cols matrix (A = A0 + A1 + A2), as stored by

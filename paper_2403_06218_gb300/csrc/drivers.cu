@@ -726,6 +726,175 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
     return converged ? TSVD_OK : TSVD_NOT_CONVERGED;
 }
 
+// ---------------------------------------------------------------------------
+// Gradient of a loss on the k leading triplets (see backward.cu for the formula).
+namespace {
+
+// One side's complement solves by CG: columns x_j of X (rows x k) with
+// (s_j^2 I - G) x_j = (I - Q Q^T) rhs_j on the complement of span(Q), where
+// G = op2(op1(.)) is A A^T (op1 = A^T, op2 = A) or A^T A.  Every operator
+// application is projected back onto the complement.
+struct CgBufs {
+    double *R, *P, *AP, *T, *H, *rr, *rr_new, *pap, *bb, *alpha, *beta, *part, *cpart;
+};
+
+template <typename F1, typename F2>
+int cg_side(tsvd_handle* h, int64_t rows, int k, const double* Q, const double* rhs, const double* s, F1 op1, F2 op2,
+            double* X, const tsvd_backward_opts* o, CgBufs& b, cudaStream_t st, int* iters, double* resid) {
+    const size_t bytes = sizeof(double) * (size_t)rows * k;
+    auto project = [&](double* Z) -> int {
+        TSVD_TRY_CUDA((gemm_tn<double, double>(h, rows, k, k, Q, k, Z, k, b.H, k, false, b.part, st)));
+        TSVD_TRY_CUDA((gemm_nn<double, double, double>(h, rows, k, k, -1.0, Q, k, b.H, k, 1.0, Z, k, false, st)));
+        return TSVD_OK;
+    };
+    TSVD_TRY_CUDA(cudaMemcpyAsync(b.R, rhs, bytes, cudaMemcpyDeviceToDevice, st));
+    TSVD_TRY(project(b.R));
+    TSVD_TRY_CUDA(cudaMemsetAsync(X, 0, bytes, st));
+    TSVD_TRY_CUDA(cudaMemcpyAsync(b.P, b.R, bytes, cudaMemcpyDeviceToDevice, st));
+    TSVD_TRY_CUDA(coldot(h, rows, k, b.R, k, b.R, k, b.bb, b.cpart, st));
+    TSVD_TRY_CUDA(cudaMemcpyAsync(b.rr, b.bb, sizeof(double) * k, cudaMemcpyDeviceToDevice, st));
+    const double tol2 = o->cg_tol * o->cg_tol;
+    std::vector<double> hrr(k), hbb(k);
+    int it = 0;
+    double worst = 0.0;
+    for (;;) {
+        const bool check = (it % std::max(1, o->check_every) == 0) || it >= o->cg_max_iter;
+        if (check) {
+            TSVD_TRY_CUDA(cudaMemcpyAsync(hrr.data(), b.rr, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+            TSVD_TRY_CUDA(cudaMemcpyAsync(hbb.data(), b.bb, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+            TSVD_TRY_CUDA(cudaStreamSynchronize(st));
+            bool done = true;
+            worst = 0.0;
+            for (int j = 0; j < k; ++j) {
+                if (!std::isfinite(hrr[j])) return TSVD_ERR_NONFINITE;
+                if (hbb[j] > 0.0) {
+                    worst = std::fmax(worst, std::sqrt(hrr[j] / hbb[j]));
+                    if (hrr[j] > tol2 * hbb[j]) done = false;
+                }
+            }
+            if (done || it >= o->cg_max_iter) break;
+        }
+        TSVD_TRY(op1(b.P, b.T));                                                  // T = op1(P)
+        TSVD_TRY(op2(b.T, b.AP));                                                 // AP = op2(T)
+        TSVD_TRY_CUDA(shifted(h, rows, k, s, b.P, b.AP, b.AP, st));               // AP = s^2 P - G P
+        TSVD_TRY(project(b.AP));
+        TSVD_TRY_CUDA(coldot(h, rows, k, b.P, k, b.AP, k, b.pap, b.cpart, st));
+        TSVD_TRY_CUDA(cg_alpha(h, k, b.rr, b.pap, b.bb, tol2, b.alpha, st));
+        TSVD_TRY_CUDA(cg_xr(h, rows, k, b.alpha, b.P, b.AP, X, b.R, st));
+        TSVD_TRY_CUDA(coldot(h, rows, k, b.R, k, b.R, k, b.rr_new, b.cpart, st));
+        TSVD_TRY_CUDA(cg_beta(h, k, b.rr, b.rr_new, b.alpha, b.beta, st));
+        TSVD_TRY_CUDA(cg_p(h, rows, k, b.alpha, b.beta, b.R, b.P, st));
+        ++it;
+    }
+    TSVD_TRY(project(X));
+    *iters = it;
+    *resid = worst;
+    return worst <= o->cg_tol ? TSVD_OK : TSVD_NOT_CONVERGED;
+}
+
+}  // namespace
+
+int svd_backward_run(tsvd_handle* h, const tsvd_matrix* A, int k, const double* sigma, const double* U,
+                     const double* V, const double* sb, const double* Ub, const double* Vb, double* grad,
+                     const tsvd_backward_opts* o, char* ws, size_t ws_bytes, size_t* sizing,
+                     tsvd_backward_info* info) {
+    const bool run = sizing == nullptr;
+    cudaStream_t st = static_cast<cudaStream_t>(o->stream);
+    Arena ar{run ? ws : nullptr, ws_bytes, 0};
+    int* status = ar.take<int>(kStCount);
+    if (run) {
+        if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+        TSVD_TRY_CUDA(cudaMemsetAsync(status, 0, sizeof(int) * kStCount, st));
+    }
+    Timer* total = run ? new Timer(st) : nullptr;
+    struct Del {
+        Timer* t;
+        ~Del() { delete t; }
+    } del{total};
+    Op<double> op;
+    TSVD_TRY(setup_op<double>(h, A, k, ar, op, status, st, run, nullptr));
+    const int64_t m = A->m, n = A->n, mx = std::max(m, n);
+    const int kk = 2 * k;
+    double* J = ar.take<double>((size_t)k * k);
+    double* K = ar.take<double>((size_t)k * k);
+    double* C = ar.take<double>((size_t)k * k);
+    double* Y = ar.take<double>((size_t)m * k);
+    double* Z = ar.take<double>((size_t)n * k);
+    double* Lf = ar.take<double>((size_t)m * kk);
+    double* Rf = ar.take<double>((size_t)n * kk);
+    double* RfT = A->format == TSVD_CSR ? nullptr : ar.take<double>((size_t)n * kk);
+    CgBufs b{};
+    b.R = ar.take<double>((size_t)mx * k);
+    b.P = ar.take<double>((size_t)mx * k);
+    b.AP = ar.take<double>((size_t)mx * k);
+    b.T = ar.take<double>((size_t)mx * k);
+    b.H = ar.take<double>((size_t)k * k);
+    for (double** v : {&b.rr, &b.rr_new, &b.pap, &b.bb, &b.alpha, &b.beta}) *v = ar.take<double>(k);
+    b.part = ar.take<double>(tn_partial_max(h, mx, k, k) / sizeof(double) + 1);
+    b.cpart = ar.take<double>(coldot_ws(mx, k) / sizeof(double) + 1);
+    if (!run) {
+        *sizing = ar.off + 256;
+        return TSVD_OK;
+    }
+    if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+    // products with A and A^T in the caller's orientation (op(A) may be A^T)
+    auto amul = [&](const double* X, double* Yo, int64_t ldy) {
+        return op.transposed ? op_tmul64(h, op, k, X, k, Yo, ldy, status, st) : op_mul64(h, op, k, X, k, Yo, ldy, status, st);
+    };
+    auto atmul = [&](const double* X, double* Yo, int64_t ldy) {
+        return op.transposed ? op_mul64(h, op, k, X, k, Yo, ldy, status, st) : op_tmul64(h, op, k, X, k, Yo, ldy, status, st);
+    };
+    // inside span(U), span(V): C
+    if (Ub) TSVD_TRY_CUDA((gemm_tn<double, double>(h, m, k, k, U, k, Ub, k, J, k, false, b.part, st)));
+    if (Vb) TSVD_TRY_CUDA((gemm_tn<double, double>(h, n, k, k, V, k, Vb, k, K, k, false, b.part, st)));
+    TSVD_TRY_CUDA(coupling(h, k, sigma, sb, Ub ? J : nullptr, Vb ? K : nullptr, C, st));
+    // outside: complement solves
+    int it_u = 0, it_v = 0;
+    double res_u = 0.0, res_v = 0.0;
+    int rc_u = TSVD_OK, rc_v = TSVD_OK;
+    if (Ub) {
+        rc_u = cg_side(h, m, k, U, Ub, sigma, [&](const double* X, double* T) { return atmul(X, T, k); },
+                       [&](const double* X, double* T) { return amul(X, T, k); }, Y, o, b, st, &it_u, &res_u);
+        TSVD_TRY(rc_u);
+    } else {
+        TSVD_TRY_CUDA(cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)m * k, st));
+    }
+    if (Vb) {
+        rc_v = cg_side(h, n, k, V, Vb, sigma, [&](const double* X, double* T) { return amul(X, T, k); },
+                       [&](const double* X, double* T) { return atmul(X, T, k); }, Z, o, b, st, &it_v, &res_v);
+        TSVD_TRY(rc_v);
+    } else {
+        TSVD_TRY_CUDA(cudaMemsetAsync(Z, 0, sizeof(double) * (size_t)n * k, st));
+    }
+    // Lf = [A Z + U C + Y S, U],  Rf = [V, A^T Y + Z S]
+    TSVD_TRY(amul(Z, Lf, kk));
+    TSVD_TRY_CUDA((gemm_nn<double, double, double>(h, m, k, k, 1.0, U, k, C, k, 1.0, Lf, kk, false, st)));
+    TSVD_TRY_CUDA(add_scaled_cols(h, m, k, Y, sigma, Lf, kk, st));
+    TSVD_TRY_CUDA(copy_block<double>(U, k, Lf + k, kk, m, k, st));
+    TSVD_TRY_CUDA(copy_block<double>(V, k, Rf, kk, n, k, st));
+    TSVD_TRY(atmul(Y, Rf + k, kk));
+    TSVD_TRY_CUDA(add_scaled_cols(h, n, k, Z, sigma, Rf + k, kk, st));
+    if (A->format == TSVD_CSR) {
+        TSVD_TRY_CUDA(sddmm(h, m, A->nnz, op.rp, op.ci, kk, Lf, kk, Rf, kk, grad, st));
+    } else {
+        TSVD_TRY_CUDA(put_transposed(h, (int)n, kk, Rf, kk, RfT, n, st));
+        ProfClass pc(h, TSVD_K_APROD);
+        TSVD_TRY_CUDA((gemm_nn<double, double, double>(h, m, kk, n, 1.0, Lf, kk, RfT, n, 0.0, grad, n, false, st)));
+    }
+    int hs[kStCount];
+    TSVD_TRY(read_status(st, status, hs));
+    TSVD_TRY(status_code(hs));
+    const double ms = total->stop();
+    if (info) {
+        info->cg_iters_u = it_u;
+        info->cg_iters_v = it_v;
+        info->cg_resid_u = res_u;
+        info->cg_resid_v = res_v;
+        info->ms_total = ms;
+    }
+    return (rc_u == TSVD_OK && rc_v == TSVD_OK) ? TSVD_OK : TSVD_NOT_CONVERGED;
+}
+
 template int rsvd_run<double>(tsvd_handle*, const tsvd_matrix*, int, int, int, int, uint64_t, const tsvd_opts*,
                               char*, size_t, size_t*, double*, double*, double*, tsvd_info*);
 template int rsvd_run<float>(tsvd_handle*, const tsvd_matrix*, int, int, int, int, uint64_t, const tsvd_opts*,

@@ -239,6 +239,56 @@ int tsvd_blanczos(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uin
 }
 
 // ---------------------------------------------------------------------------
+// Gradient with respect to A.
+// ---------------------------------------------------------------------------
+void tsvd_default_backward_opts(tsvd_backward_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->cg_tol = 1e-12;
+    o->cg_max_iter = 20000;
+    o->check_every = 10;
+    o->stream = nullptr;
+}
+
+static int check_backward_args(const tsvd_matrix* A, int k, const tsvd_backward_opts* o) {
+    TSVD_TRY(validate_matrix(A));
+    const int64_t mn = A->m < A->n ? A->m : A->n;
+    if (k < 1 || k > mn) return TSVD_ERR_INVALID_ARG;
+    if (k > TSVD_MAX_BLOCK) return TSVD_ERR_UNSUPPORTED;  // 2k factor columns per SDDMM row
+    if (!(o->cg_tol > 0.0) || o->cg_max_iter < 0) return TSVD_ERR_INVALID_ARG;
+    return TSVD_OK;
+}
+
+int tsvd_svd_backward_workspace(const tsvd_matrix* A, int k, const tsvd_backward_opts* opts, size_t* bytes) {
+    if (!A || !bytes) return TSVD_ERR_INVALID_ARG;
+    tsvd_backward_opts o;
+    tsvd_default_backward_opts(&o);
+    if (opts) o = *opts;
+    TSVD_TRY(check_backward_args(A, k, &o));
+    tsvd_handle hh = sizing_handle();
+    return svd_backward_run(&hh, A, k, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, &o, nullptr, 0,
+                            bytes, nullptr);
+}
+
+int tsvd_svd_backward(tsvd_handle* h, const tsvd_matrix* A, int k, const double* sigma, const double* U,
+                      const double* V, const double* sigma_bar, const double* U_bar, const double* V_bar,
+                      double* grad, const tsvd_backward_opts* opts, void* ws, size_t ws_bytes,
+                      tsvd_backward_info* info) {
+    if (!h || !A || !sigma || !U || !V || !grad) return TSVD_ERR_INVALID_ARG;
+    tsvd_backward_opts o;
+    tsvd_default_backward_opts(&o);
+    if (opts) o = *opts;
+    TSVD_TRY(check_backward_args(A, k, &o));
+    size_t need = 0;
+    TSVD_TRY(tsvd_svd_backward_workspace(A, k, &o, &need));
+    TSVD_TRY(check_ws(ws, ws_bytes, need));
+    TSVD_TRY_CUDA(cudaSetDevice(h->device));
+    if (info) std::memset(info, 0, sizeof(*info));
+    return svd_backward_run(h, A, k, sigma, U, V, sigma_bar, U_bar, V_bar, grad, &o, static_cast<char*>(ws), ws_bytes,
+                            nullptr, info);
+}
+
+// ---------------------------------------------------------------------------
 // Building blocks.
 // ---------------------------------------------------------------------------
 int tsvd_gaussian_block(int64_t rows, int64_t cols, uint64_t seed, uint32_t stream_id, double* out, int64_t ld,

@@ -248,6 +248,32 @@ cudaError_t col_residual_sq(tsvd_handle* h, int64_t q, int k, const double* Y, i
                             double* partial, cudaStream_t st);
 
 // rho[j] = || Rr * Vlast[:, j] ||_2, Rr b x b upper (ld b), Vlast b rows of Vbar (ld ldv), j < k.
+// ---- backward kernels (backward.cu) -----------------------------------------
+int svd_backward_run(tsvd_handle* h, const tsvd_matrix* A, int k, const double* sigma, const double* U,
+                     const double* V, const double* sb, const double* Ub, const double* Vb, double* grad,
+                     const tsvd_backward_opts* o, char* ws, size_t ws_bytes, size_t* sizing,
+                     tsvd_backward_info* info);
+size_t coldot_ws(int64_t rows, int k);
+// out[j] = sum_i X[i][j] Y[i][j] (fixed order); partial: coldot_ws bytes.
+cudaError_t coldot(tsvd_handle* h, int64_t rows, int k, const double* X, int64_t ldx, const double* Y, int64_t ldy,
+                   double* out, double* partial, cudaStream_t st);
+cudaError_t cg_alpha(tsvd_handle* h, int k, const double* rr, const double* pap, const double* bb, double tol2,
+                     double* alpha, cudaStream_t st);
+cudaError_t cg_beta(tsvd_handle* h, int k, double* rr, const double* rr_new, const double* alpha, double* beta,
+                    cudaStream_t st);
+cudaError_t cg_xr(tsvd_handle* h, int64_t rows, int k, const double* alpha, const double* p, const double* Ap,
+                  double* x, double* r, cudaStream_t st);
+cudaError_t cg_p(tsvd_handle* h, int64_t rows, int k, const double* alpha, const double* beta, const double* r,
+                 double* p, cudaStream_t st);
+cudaError_t shifted(tsvd_handle* h, int64_t rows, int k, const double* s, const double* p, const double* q,
+                    double* out, cudaStream_t st);
+cudaError_t add_scaled_cols(tsvd_handle* h, int64_t rows, int k, const double* Y, const double* s, double* out,
+                            int64_t ldo, cudaStream_t st);
+cudaError_t coupling(tsvd_handle* h, int k, const double* s, const double* sb, const double* J, const double* K,
+                     double* C, cudaStream_t st);
+cudaError_t sddmm(tsvd_handle* h, int64_t m, int64_t nnz, const int32_t* rp, const int32_t* ci, int kk,
+                  const double* Lf, int64_t ldl, const double* Rf, int64_t ldr, double* grad, cudaStream_t st);
+
 // D (cols x rows, ld ldd) = H^T for H rows x cols (ld ldh).
 cudaError_t put_transposed(tsvd_handle* h, int rows, int cols, const double* H, int64_t ldh, double* D, int64_t ldd,
                            cudaStream_t st);
