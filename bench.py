@@ -64,6 +64,27 @@ FP64_FLOPS_PER_CLK_PER_SM = 4  # 2 DFMA lanes per SM (measured 2.06 DFMA/clk/SM)
 FP32_FLOPS_PER_CLK_PER_SM = 256  # 128 FFMA lanes per SM, 2 flops each
 
 
+def replica_env():
+    """(world, rank, local_rank) of this process under torchrun (1, 0, 0 alone)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def replica_seed(cfg, rank):
+    """Each replica solves its own matrix: the workload seed plus the rank."""
+    return cfg["seed"] + rank
+
+
+def max_over_ranks(value, dist, device):
+    """The job's time is the slowest replica's (identity without a process group)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _roofline(cfg, dom, ms_cls, fl_cls, by_cls, ln_cls):
     """Bound, achieved and peak of kernel class ``dom`` from its algorithmic flops or
     bytes and its event-timed duration."""
@@ -108,14 +129,14 @@ def _measured_peaks():
 def _make_matrix(cfg, rank):
     import workloads
     if cfg["kind"] == "csr":
-        return workloads.csr_uniform(cfg["m"], cfg["n"], cfg["d"], seed=cfg["seed"] + rank)
+        return workloads.csr_uniform(cfg["m"], cfg["n"], cfg["d"], seed=replica_seed(cfg, rank))
     if cfg["kind"] == "csr-powerlaw":
-        return workloads.csr_power_law(cfg["m"], cfg["n"], cfg["nnz"], seed=cfg["seed"] + rank)
+        return workloads.csr_power_law(cfg["m"], cfg["n"], cfg["nnz"], seed=replica_seed(cfg, rank))
     if cfg["kind"] == "dense-hh":
-        A, _ = workloads.dense_householder_spectrum_torch(cfg["m"], cfg["n"], seed=cfg["seed"] + rank,
+        A, _ = workloads.dense_householder_spectrum_torch(cfg["m"], cfg["n"], seed=replica_seed(cfg, rank),
                                                           device="cuda")
         return A
-    A, _, _, _ = workloads.dense_known_spectrum(cfg["m"], cfg["n"], seed=cfg["seed"] + rank)
+    A, _, _, _ = workloads.dense_known_spectrum(cfg["m"], cfg["n"], seed=replica_seed(cfg, rank))
     return A
 
 
@@ -365,9 +386,7 @@ def main(argv=None):
     import torch
     import paper_2403_06218_gb300 as tsvd
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = replica_env()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -378,6 +397,7 @@ def main(argv=None):
         if dist is not None:
             dist.barrier()
 
+    seed = replica_seed(cfg, rank)
     A_host = _make_matrix(cfg, rank)
     if cfg["kind"] in ("csr", "csr-powerlaw"):
         A_dev = tsvd.CsrMatrix.from_scipy(A_host)
@@ -396,7 +416,6 @@ def main(argv=None):
         h2d = 8 * A_host.size
     m, n = cfg["m"], cfg["n"]
     d2h = 8 * (m + n) * cfg["k"] + 8 * cfg["k"]
-    seed = cfg["seed"] + rank
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
     with ClockSampler(local) as clk:
@@ -420,11 +439,7 @@ def main(argv=None):
         torch.cuda.synchronize()
         clk.mark_end()
         barrier()
-    ms_total = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     ms_step = ms_total / args.steps
     clocks = clk.summary()
 
@@ -446,11 +461,7 @@ def main(argv=None):
     for _ in range(e2e_steps):
         r_host = _solve(tsvd, cfg, A_pinned, seed, output="host")
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist is not None:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, "cuda")
 
     # ---- roofline of the dominant kernel class (CUDA events on the launching stream) ----
     from paper_2403_06218_gb300._capi import KERNEL_CLASSES
