@@ -399,11 +399,12 @@ def test_invalid_arguments_raise(tsvd, torch_cuda):
 
 
 # ------------------------------------------------------------------ full-size bench configuration
-@pytest.mark.parametrize("r,restarts", [(16, 0), (8, 1)])
+@pytest.mark.parametrize("r,restarts", [(16, 0), (9, 0), (8, 1)])
 def test_blanczos_full_size_sparse(tsvd, torch_cuda, r, restarts):
     """100,000 x 100,000 CSR, 10 nnz/row, k = b = 64 from the same start block: one
-    cycle with r = 16 (the benchmark's launch configuration) and two cycles with
-    r = 8.  Two cycles are not compared at r = 16: its first restart keeps 64 of
+    cycle with r = 16 and with r = 9 (the benchmark's basic-restart and
+    thick-restart launch configurations; a thick restart's first cycle is the
+    basic one) and two cycles with r = 8.  Two cycles are not compared at r = 16: its first restart keeps 64 of
     1024 Ritz vectors across a small Ritz gap, which turns rounding-level
     differences into subspace differences of ~1e-6 (sigma still agree to 1e-10)."""
     A = workloads.csr_uniform(100_000, 100_000, 10, seed=1)

@@ -222,3 +222,11 @@ def dense_householder_spectrum_torch(m: int, n: int, seed: int = 2, sigma=None, 
     del S
     reflect_left_torch(At, torch.as_tensor(Vv, device=device))
     return At.T.contiguous(), sigma
+
+
+def spectrum_paper_dense(n: int) -> np.ndarray:
+    """Singular values of the paper's dense experiment (Sec. 4.2), read as decreasing:
+    sigma_i = 10^(1 - 15 i / (n/2)) for i < n/2 (10 down to ~1e-14), then 1e-14."""
+    h = n // 2
+    i = np.arange(n)
+    return np.where(i < h, 10.0 ** (1.0 - 15.0 * i / h), 1e-14)
