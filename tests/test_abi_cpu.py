@@ -68,6 +68,51 @@ def test_host_side_validation_without_gpu(tsvd):
     assert lib.tsvd_small_svd_workspace(4096, C.byref(nb)) == _capi.TSVD_ERR_UNSUPPORTED
 
 
+def test_validation_of_the_newer_entry_points_without_gpu(tsvd):
+    """Thick restart, the gradient, the tensor-core product and the SpMM plan reject
+    bad arguments (or size their workspace) before any device work."""
+    from paper_2403_06218_gb300 import _capi
+    lib = tsvd.load()
+    d = _capi.TsvdMatrix()
+    d.m, d.n, d.format, d.location, d.ld = 1000, 500, _capi.TSVD_DENSE, _capi.TSVD_DEVICE, 500
+    d.val = 1
+    nb = C.c_size_t()
+    opts = _capi.TsvdOpts()
+    lib.tsvd_default_opts(C.byref(opts))
+    assert opts.restart_keep == 0
+    for keep, code in ((4, _capi.TSVD_ERR_INVALID_ARG),    # keep < k
+                       (28, _capi.TSVD_ERR_INVALID_ARG),   # keep + b > r b
+                       (-1, _capi.TSVD_ERR_INVALID_ARG),
+                       (16, _capi.TSVD_OK)):
+        opts.restart_keep = keep
+        assert lib.tsvd_workspace_size(C.byref(d), 1, 8, 8, 4, C.byref(opts), C.byref(nb)) == code, keep
+    base = nb.value
+    opts.restart_keep = 0
+    assert lib.tsvd_workspace_size(C.byref(d), 1, 8, 8, 4, C.byref(opts), C.byref(nb)) == _capi.TSVD_OK
+    assert base > nb.value  # the kept Ritz vectors need room
+    opts.restart_keep, opts.precision = 16, _capi.TSVD_PREC_MIXED
+    assert lib.tsvd_workspace_size(C.byref(d), 1, 8, 8, 4, C.byref(opts), C.byref(nb)) == \
+        _capi.TSVD_ERR_UNSUPPORTED
+    # gradient: k in [1, min(m, n)], k <= TSVD_MAX_BLOCK, positive tolerance
+    bo = _capi.TsvdBackwardOpts()
+    lib.tsvd_default_backward_opts(C.byref(bo))
+    assert bo.cg_tol == 1e-12 and bo.cg_max_iter > 0
+    assert lib.tsvd_svd_backward_workspace(C.byref(d), 0, C.byref(bo), C.byref(nb)) == _capi.TSVD_ERR_INVALID_ARG
+    assert lib.tsvd_svd_backward_workspace(C.byref(d), 129, C.byref(bo), C.byref(nb)) == \
+        _capi.TSVD_ERR_UNSUPPORTED
+    assert lib.tsvd_svd_backward_workspace(C.byref(d), 8, C.byref(bo), C.byref(nb)) == _capi.TSVD_OK and nb.value > 0
+    bo.cg_tol = 0.0
+    assert lib.tsvd_svd_backward_workspace(C.byref(d), 8, C.byref(bo), C.byref(nb)) == _capi.TSVD_ERR_INVALID_ARG
+    # split-BF16 product and SpMM workspaces
+    assert lib.tsvd_mm_bf16x6_workspace(-1, 10, 4, C.byref(nb)) == _capi.TSVD_ERR_INVALID_ARG
+    assert lib.tsvd_mm_bf16x6_workspace(1000, 500, 64, C.byref(nb)) == _capi.TSVD_OK and nb.value > 0
+    assert lib.tsvd_bf16x3_bytes(1000, 501, C.byref(nb)) == _capi.TSVD_OK
+    assert nb.value >= 3 * 1000 * 504 * 2 and nb.value % 256 == 0  # rows padded to a multiple of 8
+    small = C.c_size_t()
+    assert lib.tsvd_spmm_workspace(100, 1000, 64, C.byref(small)) == _capi.TSVD_OK
+    assert lib.tsvd_spmm_workspace(100, 10 ** 7, 64, C.byref(nb)) == _capi.TSVD_OK and nb.value > small.value
+
+
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     from paper_2403_06218_gb300 import _capi
     monkeypatch.setattr(_capi, "LIB_PATH", tmp_path / "libtsvd.so")
