@@ -409,3 +409,32 @@ def test_blanczos_thick_restart_converges_to_known_spectrum_with_fewer_products(
     _, _, _, ib = O.blanczos(A, 10, 16, 4, seed=0, tol=tol, max_restarts=200)
     thick_blocks = 4 + (info.iterations - 1) * ((64 - 32) // 16)
     assert thick_blocks < 4 * ib.iterations, (thick_blocks, 4 * ib.iterations)
+
+
+def test_power_law_generator_statistics():
+    """The power-law workload's structure: row degrees follow Zipf(2.1) (the slope of
+    their complementary distribution over degrees 60..2000 gives the exponent within
+    0.1), every row has exactly its target degree of distinct sorted columns, the
+    degree cap holds, and column popularity is heavy-tailed: the top column is in more
+    rows than Zipf(1.5)'s first-rank probability 1/zeta(1.5) = 0.383 alone gives (it is
+    drawn ~2d times per row), and the rank-frequency slope over ranks 2..2000 is between
+    -1.6 and -1.1 (flatter than -1.5 because a column appears at most once per row)."""
+    A = workloads.csr_power_law(200_000, 100_000, 5_000_000, seed=3)
+    assert abs(A.nnz - 5_000_000) <= 0.005 * 5_000_000
+    deg = np.diff(A.indptr)
+    assert deg.max() <= 20_000 and deg.min() >= 1
+    for i in range(0, 200_000, 9973):
+        c = A.indices[A.indptr[i]:A.indptr[i + 1]]
+        assert np.all(np.diff(c) > 0)
+    d = np.sort(deg)[::-1]
+    ranks = np.arange(1, d.size + 1)
+    sel = (d >= 60) & (d <= 2000)
+    exponent = 1.0 - np.polyfit(np.log(d[sel]), np.log(ranks[sel]), 1)[0]
+    assert abs(exponent - 2.1) < 0.1, exponent
+    col = np.sort(np.bincount(A.indices, minlength=100_000))[::-1]
+    assert col[0] / 200_000 > 0.383
+    r = np.arange(1, col.size + 1)
+    sel = (r >= 2) & (r <= 2000)
+    slope = np.polyfit(np.log(r[sel]), np.log(col[sel]), 1)[0]
+    assert -1.6 < slope < -1.1, slope
+    assert A.dtype == np.float32 and 0.0 <= A.data.min() and A.data.max() < 1.0
