@@ -437,4 +437,4 @@ def test_power_law_generator_statistics():
     sel = (r >= 2) & (r <= 2000)
     slope = np.polyfit(np.log(r[sel]), np.log(col[sel]), 1)[0]
     assert -1.6 < slope < -1.1, slope
-    assert A.dtype == np.float32 and 0.0 <= A.data.min() and A.data.max() < 1.0
+    assert A.dtype == np.float32 and 0.0 <= A.data.min() and A.data.max() <= 1.0  # U(0,1) rounded to FP32
