@@ -61,24 +61,27 @@ extern "C" {
 
 /* tsvd_opts.precision */
 #define TSVD_PREC_FP64   0   /* every step in FP64 (the paper's method)                      */
-#define TSVD_PREC_MIXED  1   /* FP32 A, blocks, bases and products; FP64 Gram reductions,
-                                Cholesky, R, B, small SVD, and a final FP64 Rayleigh-Ritz
-                                step on the Ritz vectors with the FP64 A (k <= TSVD_MAX_BLOCK) */
+#define TSVD_PREC_MIXED  1   /* FP32 blocks, bases and products (sparse A: FP32 values;
+                                dense A: split-BF16 tensor-core products of FP32 accuracy);
+                                FP64 Gram reductions, Cholesky, R, B, small SVD, and a final
+                                FP64 Rayleigh-Ritz step on the Ritz vectors with the FP64 A
+                                (k <= TSVD_MAX_BLOCK; basic restart only) */
 
 /* Largest block width of one Cholesky factorisation (CholeskyQR2 / CGS-CQR2);
  * CGS-QR splits wider blocks (Alg. 3).  Largest small-SVD order. */
 #define TSVD_MAX_BLOCK      128
 #define TSVD_MAX_SMALL_SVD  2048
 
-/* The matrix A (m x n).  Dense: `val` points to m*ld doubles, row-major.
+/* The matrix A (m x n).  Dense: `val` points to m*ld values (dtype), row-major.
  * CSR: row_ptr[m+1] (row_ptr[0] = 0, non-decreasing, row_ptr[m] = nnz),
- * col_idx[nnz] in [0, n), val[nnz]; columns within a row in any order. */
+ * col_idx[nnz] in [0, n), val[nnz] (dtype); columns within a row in any order. */
 typedef struct tsvd_matrix {
     int64_t m, n;
     int32_t format;          /* TSVD_DENSE or TSVD_CSR                     */
-    int32_t dtype;           /* TSVD_F64                                   */
+    int32_t dtype;           /* TSVD_F64 or TSVD_F32 (values widened exactly
+                                wherever FP64 is needed)                   */
     int32_t location;        /* TSVD_DEVICE or TSVD_HOST (copied in)       */
-    int32_t reserved;
+    int32_t reserved;        /* set to 0                                   */
     const void* val;
     int64_t ld;              /* dense only                                 */
     const int32_t* row_ptr;  /* CSR only                                   */
