@@ -299,6 +299,41 @@ def run_case(case):
         P = tsvd.cgs_qr(torch.randn(100_000, 960, dtype=torch.float64, device="cuda", generator=g), 128)[0]
         Y = torch.randn(100_000, 64, dtype=torch.float64, device="cuda", generator=g)
         call = lambda: tsvd.cgs_cqr2(Y, P)  # noqa: E731
+    elif case == "spmm":
+        # the SpMM alone: compulsory HBM bytes vs the gathered X rows (nnz w e bytes through L2)
+        import numpy as np
+        import workloads
+        peaks = _measured_peaks()
+        hbm = float(peaks.get("hbm_gbs", 6790.3))
+        rows = []
+        A1 = workloads.csr_uniform(100_000, 100_000, 10, seed=1)
+        P = workloads.csr_power_law(2_000_000, 1_000_000, 50_000_000, seed=3)
+        cases = [("uniform 100k, FP64", A1, np.float64, 64), ("uniform 100k, FP32", A1, np.float32, 64),
+                 ("uniform 100k, FP32", A1, np.float32, 128), ("power-law 2M x 1M, FP32, A", P, np.float32, 128),
+                 ("power-law 2M x 1M, FP32, A^T", P.T.tocsr(), np.float32, 128)]
+        for name, M, dt, w in cases:
+            Md = tsvd.CsrMatrix.from_scipy(M.astype(dt))
+            X = torch.randn(M.shape[1], w, dtype=torch.float64, device="cuda", generator=g).to(
+                torch.float32 if dt == np.float32 else torch.float64)
+            ts = []
+            for _ in range(4):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                tsvd.spmm(Md, X)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            t = min(ts[1:]) * 1e-3
+            es = np.dtype(dt).itemsize
+            comp = (4 + es) * M.nnz + 4 * (M.shape[0] + 1) + es * (M.shape[0] + M.shape[1]) * w
+            gath = es * M.nnz * w
+            rows.append({"case": name, "w": w, "ms": t * 1e3, "compulsory_gbs": comp / t / 1e9,
+                         "hbm_frac": comp / t / 1e9 / hbm, "gathered_gbs": gath / t / 1e9,
+                         "tflops": 2.0 * M.nnz * w / t / 1e12})
+            del Md, X
+        for r in rows:
+            print(json.dumps({k: (round(v, 3) if isinstance(v, float) else v) for k, v in r.items()}))
+        return 0
     elif case == "backward":
         # gradient of sum(sigma) + ||U^T X||^2 for the 200,000 x 200,000 (5M nnz) sparse
         # workload, k = b = 32, r = 16, thick restart keeping 128
@@ -375,7 +410,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--workload", default="sparse100k-lanczos-thick", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default=None, choices=("orth", "svd", "tc", "f32", "f64", "backward"),
+    ap.add_argument("--case", default=None, choices=("orth", "svd", "tc", "f32", "f64", "backward", "spmm"),
                     help="run one building block at its benchmark shape (for profiler captures) and exit")
     args = ap.parse_args(argv)
     cfg = WORKLOADS[args.workload]

@@ -226,6 +226,12 @@ int tsvd_spmm(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz,
               const int32_t* row_ptr, const int32_t* col_idx, const double* val,
               int w, const double* X, int64_t ldx, double* Y, int64_t ldy,
               void* ws, size_t ws_bytes, void* stream);
+/* The same product in FP32 (values, X and Y float32; the mixed form's SpMM), with
+ * the workspace tsvd_spmm_workspace reports. */
+int tsvd_spmm_f32(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz,
+                  const int32_t* row_ptr, const int32_t* col_idx, const float* val,
+                  int w, const float* X, int64_t ldx, float* Y, int64_t ldy,
+                  void* ws, size_t ws_bytes, void* stream);
 
 /* Y = op(A) X for dense row-major A (m x n, lda): trans = 0 gives A X
  * (X n x w, Y m x w); trans = 1 gives A^T X (X m x w, Y n x w).

@@ -104,6 +104,7 @@ SIGNATURES = [
     ("tsvd_csr_transpose_workspace", _I, [_I64, _I64, _I64, _PSZ]),
     ("tsvd_csr_transpose", _I, [_P, _I64, _I64, _I64, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     ("tsvd_spmm_workspace", _I, [_I64, _I64, _I, _PSZ]),
+    ("tsvd_spmm_f32", _I, [_P, _I64, _I64, _I64, _P, _P, _P, _I, _P, _I64, _P, _I64, _P, _SZ, _P]),
     ("tsvd_spmm", _I, [_P, _I64, _I64, _I64, _P, _P, _P, _I, _P, _I64, _P, _I64, _P, _SZ, _P]),
     ("tsvd_dense_mm_workspace", _I, [_I, _I64, _I64, _I, _PSZ]),
     ("tsvd_dense_mm", _I, [_P, _I, _I64, _I64, _P, _I64, _I, _P, _I64, _P, _I64, _P, _SZ, _P]),

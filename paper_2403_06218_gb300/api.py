@@ -272,22 +272,29 @@ def csr_transpose(A: CsrMatrix) -> CsrMatrix:
 
 
 def spmm(A: CsrMatrix, X: torch.Tensor) -> torch.Tensor:
-    """Y = A X for CSR A (FP64 values) on the GPU."""
+    """Y = A X for CSR A on the GPU: FP64 values and block (tsvd_spmm), or FP32 values
+    and block (tsvd_spmm_f32, the mixed form's SpMM)."""
     lib = capi.load()
-    _cuda_f64(X, "X")
-    if A.val.dtype != torch.float64:
-        raise TypeError("spmm takes FP64 CSR values")
+    f32 = A.val.dtype == torch.float32
+    if f32:
+        if not (X.is_cuda and X.dtype == torch.float32 and X.dim() == 2 and X.stride(1) == 1):
+            raise TypeError("X must be a 2-D float32 CUDA tensor with unit column stride")
+    else:
+        _cuda_f64(X, "X")
+        if A.val.dtype != torch.float64:
+            raise TypeError("spmm takes FP64 or FP32 CSR values")
     dev = X.device
     m, n = A.shape
     w = X.shape[1]
-    Y = torch.empty((m, w), dtype=torch.float64, device=dev)
+    Y = torch.empty((m, w), dtype=A.val.dtype, device=dev)
+    fn = lib.tsvd_spmm_f32 if f32 else lib.tsvd_spmm
     with torch.cuda.device(dev):
         nb = C.c_size_t()
         capi.check(lib.tsvd_spmm_workspace(m, A.nnz, w, C.byref(nb)), "tsvd_spmm_workspace")
         ws = _ws(nb.value, dev)
-        capi.check(lib.tsvd_spmm(handle(dev), m, n, A.nnz, A.row_ptr.data_ptr(), A.col_idx.data_ptr(),
-                                 A.val.data_ptr(), w, X.data_ptr(), X.stride(0), Y.data_ptr(), max(w, 1),
-                                 ws.data_ptr(), ws.numel(), _stream_ptr(dev)), "tsvd_spmm")
+        capi.check(fn(handle(dev), m, n, A.nnz, A.row_ptr.data_ptr(), A.col_idx.data_ptr(), A.val.data_ptr(), w,
+                      X.data_ptr(), X.stride(0), Y.data_ptr(), max(w, 1), ws.data_ptr(), ws.numel(),
+                      _stream_ptr(dev)), "tsvd_spmm_f32" if f32 else "tsvd_spmm")
     return Y
 
 

@@ -333,9 +333,10 @@ int tsvd_spmm_workspace(int64_t m, int64_t nnz, int w, size_t* bytes) {
     return TSVD_OK;
 }
 
-int tsvd_spmm(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
-              const double* val, int w, const double* X, int64_t ldx, double* Y, int64_t ldy, void* ws,
-              size_t ws_bytes, void* stream) {
+extern "C++" template <typename T>
+int spmm_entry(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr,
+                      const int32_t* col_idx, const T* val, int w, const T* X, int64_t ldx, T* Y, int64_t ldy,
+                      void* ws, size_t ws_bytes, void* stream) {
     if (!h || m < 0 || n < 0 || nnz < 0 || w < 0 || ldx < w || ldy < w || !row_ptr) return TSVD_ERR_INVALID_ARG;
     if (m * (int64_t)w > 0 && (!X || !Y)) return TSVD_ERR_INVALID_ARG;
     size_t need = 0;
@@ -347,10 +348,22 @@ int tsvd_spmm(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz, const int32_t* 
     Arena ar{static_cast<char*>(ws), ws_bytes, align256(sizeof(int) * kStCount)};
     SpmmPlan plan;
     TSVD_TRY(spmm_plan(h, m, nnz, row_ptr, w, sizeof(double), ar, &plan, st));
-    TSVD_TRY_CUDA(launch_spmm<double>(h, m, n, nnz, row_ptr, col_idx, val, w, X, ldx, Y, ldy, status, st, &plan));
+    TSVD_TRY_CUDA(launch_spmm<T>(h, m, n, nnz, row_ptr, col_idx, val, w, X, ldx, Y, ldy, status, st, &plan));
     int hs[kStCount];
     TSVD_TRY(read_status(st, status, hs));
     return hs[kStBadCsr] ? TSVD_ERR_INVALID_ARG : TSVD_OK;
+}
+
+int tsvd_spmm_f32(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+                  const float* val, int w, const float* X, int64_t ldx, float* Y, int64_t ldy, void* ws,
+                  size_t ws_bytes, void* stream) {
+    return spmm_entry<float>(h, m, n, nnz, row_ptr, col_idx, val, w, X, ldx, Y, ldy, ws, ws_bytes, stream);
+}
+
+int tsvd_spmm(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx,
+              const double* val, int w, const double* X, int64_t ldx, double* Y, int64_t ldy, void* ws,
+              size_t ws_bytes, void* stream) {
+    return spmm_entry<double>(h, m, n, nnz, row_ptr, col_idx, val, w, X, ldx, Y, ldy, ws, ws_bytes, stream);
 }
 
 int tsvd_dense_mm_workspace(int trans, int64_t m, int64_t n, int w, size_t* bytes) {

@@ -93,6 +93,24 @@ def test_spmm_long_rows_split_in_chunks(tsvd, torch_cuda, w):
         assert np.array_equal(Y, Y2)  # fixed summation order
 
 
+@pytest.mark.parametrize("w", [64, 128, 33])
+def test_spmm_f32_within_fp32_bound(tsvd, torch_cuda, w):
+    """The mixed form's FP32 SpMM (tsvd_spmm_f32) against the exact product of the same
+    FP32 values: |Y - A X| <= (len + 2) u (|A| |X|), u = 2^-24, for uniform rows and
+    for power-law rows long enough to be split into chunks; bitwise repeatable."""
+    torch = torch_cuda
+    for A in (workloads.csr_uniform(5000, 4000, 10, seed=2, dtype=np.float32),
+              workloads.csr_power_law(20_000, 10_000, 400_000, seed=5, deg_max=5_000)):
+        X = np.random.default_rng(w).standard_normal((A.shape[1], w)).astype(np.float32)
+        Ad = tsvd.CsrMatrix.from_scipy(A)
+        Xd = torch.from_numpy(X).cuda()
+        Y = _np(tsvd.spmm(Ad, Xd)).astype(np.float64)
+        A64, X64 = A.astype(np.float64), X.astype(np.float64)
+        lens = np.diff(A.indptr)[:, None]
+        assert np.all(np.abs(Y - A64 @ X64) <= (lens + 2) * 2.0 ** -24 * (abs(A64) @ np.abs(X64)) + 1e-30)
+        assert np.array_equal(Y, _np(tsvd.spmm(Ad, Xd)).astype(np.float64))
+
+
 def test_csr_transpose_is_exact(tsvd, torch_cuda):
     # column degrees span the warp (<=32), CTA (<=4096) and global-memory sort paths
     rng = np.random.default_rng(7)
