@@ -43,6 +43,11 @@ WORKLOADS = {
     "sparse100k-lanczos-thick": dict(kind="csr", m=100_000, n=100_000, d=10, seed=1, method="blanczos",
                                      k=64, b=64, r=9, tol=1e-6, max_restarts=50, oracle_cycles=7,
                                      restart_keep=128),
+    # the thick-restart solve in the mixed form (FP32 products and bases, FP64 masters of the
+    # kept Ritz vectors, FP64 small algebra and final Rayleigh-Ritz step)
+    "sparse100k-lanczos-thick-mixed": dict(kind="csr", m=100_000, n=100_000, d=10, seed=1, method="blanczos",
+                                           k=64, b=64, r=9, tol=1e-6, max_restarts=50, oracle_cycles=7,
+                                           restart_keep=128, precision="mixed"),
     "sparse100k-rsvd": dict(kind="csr", m=100_000, n=100_000, d=10, seed=1, method="rsvd",
                             k=64, p=64, q=3),
     "dense512-lanczos": dict(kind="dense", m=512, n=256, seed=0, method="blanczos",

@@ -65,7 +65,7 @@ extern "C" {
                                 dense A: split-BF16 tensor-core products of FP32 accuracy);
                                 FP64 Gram reductions, Cholesky, R, B, small SVD, and a final
                                 FP64 Rayleigh-Ritz step on the Ritz vectors with the FP64 A
-                                (k <= TSVD_MAX_BLOCK; basic restart only) */
+                                (k <= TSVD_MAX_BLOCK) */
 
 /* Largest block width of one Cholesky factorisation (CholeskyQR2 / CGS-CQR2);
  * CGS-QR splits wider blocks (Alg. 3).  Largest small-SVD order. */
@@ -120,7 +120,8 @@ typedef struct tsvd_opts {
                                 b leading left Ritz vectors; s > 0 = thick restart keeping the s
                                 leading Ritz pairs (k <= s, s + b <= r b) and continuing from
                                 the residual block, with (r b - s) / b new blocks per cycle;
-                                FP64 method only (TSVD_ERR_UNSUPPORTED with TSVD_PREC_MIXED) */
+                                in the mixed form the kept vectors have FP64 master copies (the
+                                bases hold their FP32 rounding) */
 } tsvd_opts;
 
 /* Per-call report.  Phase times are CUDA-event milliseconds on `stream`. */

@@ -368,11 +368,15 @@ size_t final_tail_ws(tsvd_handle* h, int64_t m, int64_t n, int k, bool mixed) {
 // The returned triplets from the last small SVD: sigma, U = Bm Wm[:, :k],
 // V = Bn Wn[:, :k] (FP64 path), or the same followed by the FP64 Rayleigh-Ritz
 // step (mixed path).  Writes dev.{U,V,sigma} in op orientation.
+// In the mixed form the first s0 basis columns may have FP64 master copies (Mm, Mn:
+// the kept Ritz vectors of a thick restart); their share of U and V is then formed
+// from the masters in FP64.
 template <typename T>
 int final_triplets(tsvd_handle* h, Op<T>& op, int k, const T* Bm, int64_t ldbm, const double* Wm, int64_t ldwm,
                    const T* Bn, int64_t ldbn, const double* Wn, int64_t ldwn, int wdim, const double* sig,
                    Final& f, double* dU, double* dV, double* dsig, OrthCtx& ctx, Arena tail, int* status,
-                   cudaStream_t st, int* sweeps) {
+                   cudaStream_t st, int* sweeps, const double* Mm = nullptr, int64_t ldmm = 0,
+                   const double* Mn = nullptr, int64_t ldmn = 0, int s0 = 0) {
     constexpr bool kF64 = sizeof(T) == sizeof(double);
     const int64_t m = op.m, n = op.n;
     if (kF64) {
@@ -382,8 +386,20 @@ int final_triplets(tsvd_handle* h, Op<T>& op, int k, const T* Bm, int64_t ldbm, 
         return TSVD_OK;
     }
     // FP64 Rayleigh-Ritz on span(U), span(V)
-    TSVD_TRY_CUDA((gemm_nn<T, double, double>(h, m, wdim, k, 1.0, Bm, ldbm, Wm, ldwm, 0.0, f.U64, k, false, st)));
-    TSVD_TRY_CUDA((gemm_nn<T, double, double>(h, n, wdim, k, 1.0, Bn, ldbn, Wn, ldwn, 0.0, f.V64, k, false, st)));
+    if (s0 > 0 && Mm && Mn) {
+        // the FP32 columns first, then the FP64 masters added by the FP64 kernel
+        TSVD_TRY_CUDA((gemm_nn<T, double, double>(h, m, wdim - s0, k, 1.0, Bm + s0, ldbm, Wm + (int64_t)s0 * ldwm,
+                                                  ldwm, 0.0, f.U64, k, false, st)));
+        TSVD_TRY_CUDA((gemm_nn<double, double, double>(h, m, s0, k, 1.0, Mm, ldmm, Wm, ldwm, 1.0, f.U64, k, false,
+                                                       st)));
+        TSVD_TRY_CUDA((gemm_nn<T, double, double>(h, n, wdim - s0, k, 1.0, Bn + s0, ldbn, Wn + (int64_t)s0 * ldwn,
+                                                  ldwn, 0.0, f.V64, k, false, st)));
+        TSVD_TRY_CUDA((gemm_nn<double, double, double>(h, n, s0, k, 1.0, Mn, ldmn, Wn, ldwn, 1.0, f.V64, k, false,
+                                                       st)));
+    } else {
+        TSVD_TRY_CUDA((gemm_nn<T, double, double>(h, m, wdim, k, 1.0, Bm, ldbm, Wm, ldwm, 0.0, f.U64, k, false, st)));
+        TSVD_TRY_CUDA((gemm_nn<T, double, double>(h, n, wdim, k, 1.0, Bn, ldbn, Wn, ldwn, 0.0, f.V64, k, false, st)));
+    }
     TSVD_TRY(cgs_cqr2<double>(h, m, 0, k, nullptr, 0, f.U64, k, nullptr, f.Mkk, k, false, ctx, tail, status, st));
     TSVD_TRY(cgs_cqr2<double>(h, n, 0, k, nullptr, 0, f.V64, k, nullptr, f.Mkk, k, false, ctx, tail, status, st));
     TSVD_TRY(op_mul64(h, op, k, f.V64, k, f.AV, k, status, st));
@@ -592,6 +608,17 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
     T* Qnext = ar.take<T>((size_t)m * b);
     T* Pk = keep ? ar.take<T>((size_t)n * keep) : nullptr;    // P Vbar_s, Pbar Ubar_s
     T* Pbk = keep ? ar.take<T>((size_t)m * keep) : nullptr;
+    // mixed form: FP64 master copies of the kept Ritz vectors (two generations each); the
+    // bases hold their FP32 rounding for the orthogonalisations
+    const bool masters = kMixed && keep > 0;
+    double* Pk64[2] = {nullptr, nullptr};
+    double* Pbk64[2] = {nullptr, nullptr};
+    if (masters)
+        for (int g = 0; g < 2; ++g) {
+            Pk64[g] = ar.take<double>((size_t)n * keep);
+            Pbk64[g] = ar.take<double>((size_t)m * keep);
+        }
+    int cur = 0;
     double* Hk = keep ? ar.take<double>((size_t)keep * b) : nullptr;  // coefficients of A^T Qbar on P Vbar_s
     double* B = ar.take<double>((size_t)rb * rb);
     double* Ub = ar.take<double>((size_t)rb * rb);
@@ -677,8 +704,10 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
         const bool done = rho_last <= o->tol;
         if (done || restarts >= o->max_restarts) {
             // S8/S9 (and the FP64 Rayleigh-Ritz step in the mixed form)
+            const bool with_masters = masters && s0 > 0;
             TSVD_TRY(final_triplets<T>(h, op, k, Pbar, rb, Ub, d, P, rb, Vb, d, d, sig, f, dU, dV, dsig, ctx, ar,
-                                       status, st, nullptr));
+                                       status, st, nullptr, with_masters ? Pbk64[cur] : nullptr, keep,
+                                       with_masters ? Pk64[cur] : nullptr, keep, with_masters ? s0 : 0));
             TSVD_TRY(explicit_residual<T>(h, op, k, dU, dV, dsig, f, status, st, &resid));
             if ((done && resid <= o->tol) || restarts >= o->max_restarts) {
                 converged = resid <= o->tol ? 1 : 0;
@@ -689,10 +718,30 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
         if (keep > 0) {
             // thick restart: P~ = P Vbar_s, Pbar~ = Pbar Ubar_s, B = diag(S_s) on them, and the
             // residual block Qbar_{r+1} continues the recurrence as the next left block
-            TSVD_TRY_CUDA((gemm_nn<T, double, T>(h, n, d, keep, 1.0, P, rb, Vb, d, 0.0, Pk, keep, false, st)));
-            TSVD_TRY_CUDA((gemm_nn<T, double, T>(h, m, d, keep, 1.0, Pbar, rb, Ub, d, 0.0, Pbk, keep, false, st)));
-            TSVD_TRY_CUDA(copy_block<T>(Pk, keep, P, rb, n, keep, st));
-            TSVD_TRY_CUDA(copy_block<T>(Pbk, keep, Pbar, rb, m, keep, st));
+            if (masters) {
+                // new FP64 masters from the FP32 columns and the old masters, then their
+                // FP32 rounding into the bases
+                double* nPk = Pk64[1 - cur];
+                double* nPbk = Pbk64[1 - cur];
+                TSVD_TRY_CUDA((gemm_nn<T, double, double>(h, n, d - s0, keep, 1.0, P + s0, rb, Vb + (int64_t)s0 * d,
+                                                          d, 0.0, nPk, keep, false, st)));
+                TSVD_TRY_CUDA((gemm_nn<T, double, double>(h, m, d - s0, keep, 1.0, Pbar + s0, rb,
+                                                          Ub + (int64_t)s0 * d, d, 0.0, nPbk, keep, false, st)));
+                if (s0 > 0) {
+                    TSVD_TRY_CUDA((gemm_nn<double, double, double>(h, n, s0, keep, 1.0, Pk64[cur], keep, Vb, d, 1.0,
+                                                                   nPk, keep, false, st)));
+                    TSVD_TRY_CUDA((gemm_nn<double, double, double>(h, m, s0, keep, 1.0, Pbk64[cur], keep, Ub, d, 1.0,
+                                                                   nPbk, keep, false, st)));
+                }
+                cur = 1 - cur;
+                TSVD_TRY_CUDA((convert2d<double, T>(h, n, keep, Pk64[cur], keep, P, rb, st)));
+                TSVD_TRY_CUDA((convert2d<double, T>(h, m, keep, Pbk64[cur], keep, Pbar, rb, st)));
+            } else {
+                TSVD_TRY_CUDA((gemm_nn<T, double, T>(h, n, d, keep, 1.0, P, rb, Vb, d, 0.0, Pk, keep, false, st)));
+                TSVD_TRY_CUDA((gemm_nn<T, double, T>(h, m, d, keep, 1.0, Pbar, rb, Ub, d, 0.0, Pbk, keep, false, st)));
+                TSVD_TRY_CUDA(copy_block<T>(Pk, keep, P, rb, n, keep, st));
+                TSVD_TRY_CUDA(copy_block<T>(Pbk, keep, Pbar, rb, m, keep, st));
+            }
             TSVD_TRY_CUDA(copy_block<T>(Qnext, b, Pbar + keep, rb, m, b, st));
             TSVD_TRY_CUDA(cudaMemsetAsync(B, 0, sizeof(double) * (size_t)rb * rb, st));
             TSVD_TRY_CUDA(put_diagonal(h, keep, sig, B, rb, st));

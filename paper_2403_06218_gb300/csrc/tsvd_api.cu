@@ -99,10 +99,6 @@ int check_lanc_args(const tsvd_matrix* A, int k, int b, int r, const tsvd_opts* 
     if (o->precision == TSVD_PREC_MIXED && k > TSVD_MAX_BLOCK) return TSVD_ERR_UNSUPPORTED;
     if (o->restart_keep < 0) return TSVD_ERR_INVALID_ARG;
     if (o->restart_keep > 0 && (o->restart_keep < k || o->restart_keep + b > r * b)) return TSVD_ERR_INVALID_ARG;
-    // thick restart carries the kept Ritz vectors in the working precision from cycle to
-    // cycle; in FP32 their rounding is not represented in B, and the FP64 residual
-    // stalls near 1e-6 while the Lanczos estimate keeps falling
-    if (o->restart_keep > 0 && o->precision == TSVD_PREC_MIXED) return TSVD_ERR_UNSUPPORTED;
     return TSVD_OK;
 }
 

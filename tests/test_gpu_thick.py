@@ -47,8 +47,11 @@ def test_thick_restart_converges_dense_known_spectrum(tsvd, torch_cuda):
     assert np.max(np.abs(s - s_true[:10])) <= 2e-6
     relgap = (s_true[9] - s_true[10]) / s_true[0]
     assert subspace_sin(U, U0[:, :10]) < 10e-6 / relgap and subspace_sin(V, V0[:, :10]) < 10e-6 / relgap
-    with pytest.raises(tsvd.TsvdError):  # thick restart is an FP64-method option
-        tsvd.blanczos(torch.from_numpy(A).cuda(), 10, 16, 4, restart_keep=32, precision="mixed")
+    # mixed form (tensor-core products, FP32 bases with FP64 masters of the kept vectors)
+    rm = tsvd.blanczos(torch.from_numpy(A).cuda(), 10, 16, 4, seed=0, tol=1e-6, max_restarts=100,
+                       restart_keep=32, precision="mixed")
+    assert rm.status == 0 and rm.info["converged"] == 1
+    assert np.max(np.abs(_np(rm.sigma) - s_true[:10])) <= 2e-6
     so, _, _, info = oracle.blanczos(A, 10, 16, 4, seed=0, tol=1e-6, max_restarts=100, keep=32)
     np.testing.assert_allclose(_np(res.sigma), so, rtol=2e-6)
 
@@ -81,3 +84,22 @@ def test_thick_restart_full_size_sparse(tsvd, torch_cuda):
           f"({blocks_thick} blocks), basic {rb_.info['ms_total'] / 1e3:.3f} s, {rb_.info['iterations']} cycles "
           f"({blocks_basic} blocks), resid {rt.info['resid_max']:.2e}")
     assert blocks_thick < blocks_basic
+
+
+def test_thick_restart_mixed_form_converges_where_fp32_kept_vectors_stall(tsvd, torch_cuda):
+    """The mixed form with thick restart keeps FP64 master copies of the kept Ritz
+    vectors (their FP32 rounding alone stalls the FP64 residual just above 1e-6 on
+    the 100,000^2 matrix): it must reach tol against the FP64 A and agree with the
+    FP64 method, at the benchmark's thick-restart configuration."""
+    A = workloads.csr_uniform(100_000, 100_000, 10, seed=1)
+    Ad = tsvd.CsrMatrix.from_scipy(A)
+    rm = tsvd.blanczos(Ad, 64, 64, 9, seed=1, tol=1e-6, restart_keep=128, precision="mixed")
+    rd = tsvd.blanczos(Ad, 64, 64, 9, seed=1, tol=1e-6, restart_keep=128)
+    assert rm.status == 0 and rm.info["converged"] == 1 and rm.info["resid_max"] <= 1e-6
+    s32, s64 = _np(rm.sigma), _np(rd.sigma)
+    assert np.max(np.abs(s32 - s64)) / s64[0] <= 2e-6
+    U, V = _np(rm.U), _np(rm.V)
+    resid = max(np.linalg.norm(A @ V - U * s32, axis=0).max(), np.linalg.norm(A.T @ U - V * s32, axis=0).max())
+    assert resid / s32[0] <= 1e-6 * 1.0001
+    print(f"mixed thick: {rm.info['ms_total'] / 1e3:.3f} s ({rm.info['iterations']} cycles), "
+          f"FP64 thick {rd.info['ms_total'] / 1e3:.3f} s ({rd.info['iterations']} cycles), resid {resid / s32[0]:.2e}")
