@@ -9,6 +9,14 @@
 //               projection U^T A V is formed with the FP64 A and its SVD rotates
 //               them; the residual test uses the FP64 A.
 //
+// LancSVD restarts either as the paper does (from the b leading left Ritz
+// vectors) or thick: the s leading Ritz pairs are kept, B starts with diag(S_s)
+// and the coupling block of the residual block, and the recurrence continues
+// from that block (the improved restart the paper leaves to future work, Sec. 5).
+// In the mixed form the kept vectors have FP64 master copies and the bases hold
+// their FP32 rounding.  The gradient of a loss on the triplets (svd_backward_run)
+// also lives here, next to the operator it applies.
+//
 // The host only sequences kernels and reads back a few status words (Cholesky
 // breakdown flags after each orthogonalisation, the Lanczos estimate once per
 // cycle, the explicit residual).  When m < n both methods run on A^T and swap U
