@@ -170,15 +170,17 @@ def _oracle_solve(cfg, A, seed, cycles=None):
 class ClockSampler:
     """nvidia-smi clock and throttle-reason samples during the timed region.
 
-    The sampler starts before the warm-up steps (nvidia-smi's own start-up takes
-    driver time that would otherwise land in the first timed step) and only the
-    samples stamped inside [mark_start, mark_end] are summarised."""
+    The sampler starts before the warm-up steps, and the steps wait for its first
+    sample (nvidia-smi's own start-up takes driver time that would otherwise land
+    in the timed steps); only the samples stamped inside [mark_start, mark_end]
+    are summarised."""
     FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, interval_ms=200):
         self.gpu = gpu_index
+        self.interval_ms = int(interval_ms)
         self.proc = None
         self.path = None
         self.t0 = self.t1 = None
@@ -195,9 +197,16 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", str(self.interval_ms)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+        # wait (at most 20 s) for the first sample: on a GPU no process has touched yet,
+        # nvidia-smi's start-up holds the driver for seconds and would slow the steps
+        deadline = time.time() + 20.0
+        while self.proc is not None and self.proc.poll() is None and time.time() < deadline:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.05)
         return self
 
     def __exit__(self, *exc):
@@ -415,6 +424,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--workload", default="sparse100k-lanczos-thick", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clock-ms", type=int, default=200, help="nvidia-smi sampling interval in the timed region")
     ap.add_argument("--case", default=None, choices=("orth", "svd", "tc", "f32", "f64", "backward", "spmm"),
                     help="run one building block at its benchmark shape (for profiler captures) and exit")
     args = ap.parse_args(argv)
@@ -460,7 +470,7 @@ def main(argv=None):
     d2h = 8 * (m + n) * cfg["k"] + 8 * cfg["k"]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, args.clock_ms) as clk:
         for i in range(args.warmup):  # the last one profiled, so the library's CUDA event pool is warm
             res = _solve(tsvd, cfg, A_dev, seed, profile=(i == args.warmup - 1))
         torch.cuda.synchronize()
