@@ -221,7 +221,10 @@ int tsvd_csr_transpose(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz,
  * is summed in chunks of 1024 whose partial sums are added in chunk order
  * (deterministic).  ws (tsvd_spmm_workspace bytes) holds the status words and
  * the chunk plan; an entry whose column lies outside [0, n) is skipped and
- * reported as TSVD_ERR_INVALID_ARG. */
+ * reported as TSVD_ERR_INVALID_ARG.  row_ptr must be a valid CSR row pointer
+ * (row_ptr[0] = 0, non-decreasing, row_ptr[m] = nnz): the product reads each
+ * row's extent from it unchecked, as sparse BLAS libraries do (tsvd_csr_transpose
+ * and both methods validate the structure before their first product). */
 int tsvd_spmm_workspace(int64_t m, int64_t nnz, int w, size_t* bytes);
 int tsvd_spmm(tsvd_handle* h, int64_t m, int64_t n, int64_t nnz,
               const int32_t* row_ptr, const int32_t* col_idx, const double* val,

@@ -96,6 +96,35 @@ def _ptr(t) -> int:
     return t.data_ptr()
 
 
+def _check_csr(A: "CsrMatrix"):
+    """The structure checks a pointer-based entry point cannot make: contiguous int32
+    index arrays of lengths m + 1 and nnz, float values of length nnz, one device."""
+    m, n = A.shape
+    for t, dt, name in ((A.row_ptr, torch.int32, "row_ptr"), (A.col_idx, torch.int32, "col_idx")):
+        if t.dtype != dt or not t.is_contiguous():
+            raise TypeError(f"CsrMatrix needs a contiguous int32 {name}")
+    if A.val.dtype not in (torch.float64, torch.float32) or not A.val.is_contiguous():
+        raise TypeError("CsrMatrix needs contiguous float64 or float32 values")
+    if A.row_ptr.dim() != 1 or A.row_ptr.numel() != m + 1:
+        raise ValueError(f"row_ptr must have m + 1 = {m + 1} entries")
+    if A.col_idx.dim() != 1 or A.val.dim() != 1 or A.val.numel() != A.col_idx.numel():
+        raise ValueError("col_idx and val must be 1-D with nnz entries each")
+    if not (A.row_ptr.device == A.col_idx.device == A.val.device):
+        raise ValueError("row_ptr, col_idx and val must be on one device")
+
+
+def _check_rows(t, rows: int, name: str):
+    if not isinstance(t, torch.Tensor) or t.dim() != 2 or t.shape[0] != rows:
+        shape = tuple(t.shape) if isinstance(t, torch.Tensor) else type(t).__name__
+        raise ValueError(f"{name} must be a 2-D tensor with {rows} rows (got {shape})")
+
+
+def _same_device(dev, *named):
+    for t, name in named:
+        if t.device != dev:
+            raise ValueError(f"{name} is on {t.device}, expected {dev}")
+
+
 def _desc(A):
     """(TsvdMatrix, keep-alive list, torch.device or None for host)."""
     import scipy.sparse as sp
@@ -117,11 +146,7 @@ def _desc(A):
         d.val, d.row_ptr, d.col_idx, d.nnz = va.ctypes.data, rp.ctypes.data, ci.ctypes.data, ci.size
         return d, keep, None
     if isinstance(A, CsrMatrix):
-        for t, dt in ((A.row_ptr, torch.int32), (A.col_idx, torch.int32)):
-            if t.dtype != dt or not t.is_contiguous():
-                raise TypeError("CsrMatrix needs contiguous int32 indices")
-        if A.val.dtype not in (torch.float64, torch.float32) or not A.val.is_contiguous():
-            raise TypeError("CsrMatrix needs contiguous float64 or float32 values")
+        _check_csr(A)
         keep += [A.row_ptr, A.col_idx, A.val]
         d.m, d.n = A.shape
         d.format = capi.TSVD_CSR
@@ -185,9 +210,15 @@ def _run_driver(fn_name, method, A, k, a, c, seed, tol, max_restarts, qr_block, 
     opts.precision = _PRECISIONS[precision]
     opts.restart_keep = int(restart_keep)
     if start_block is not None:
-        if not (isinstance(start_block, torch.Tensor) and start_block.is_cuda and start_block.dtype == torch.float64
-                and start_block.is_contiguous()):
+        # LancSVD: max(m, n) x b; RandSVD: min(m, n) x (k + p) (the dimensions after the m < n transpose)
+        m_, n_ = int(desc.m), int(desc.n)
+        rows = max(m_, n_) if method == capi.TSVD_METHOD_BLANCZOS else min(m_, n_)
+        cols = a if method == capi.TSVD_METHOD_BLANCZOS else k + a
+        if not isinstance(start_block, torch.Tensor) or tuple(start_block.shape) != (rows, cols):
+            raise ValueError(f"start_block must have shape ({rows}, {cols})")
+        if not (start_block.is_cuda and start_block.dtype == torch.float64 and start_block.is_contiguous()):
             raise TypeError("start_block must be a contiguous float64 CUDA tensor")
+        _same_device(dev, (start_block, "start_block"))
         keep.append(start_block)
         opts.start_block = start_block.data_ptr()
     with torch.cuda.device(dev):
@@ -255,6 +286,9 @@ def gaussian_block(rows: int, cols: int, seed: int, stream_id: int, device=None)
 def csr_transpose(A: CsrMatrix) -> CsrMatrix:
     """CSR of A^T (rows of A^T list original rows in increasing order)."""
     lib = capi.load()
+    _check_csr(A)
+    if A.val.dtype != torch.float64 or not A.val.is_cuda:
+        raise TypeError("csr_transpose takes a CsrMatrix with float64 values on the GPU")
     dev = A.val.device
     m, n = A.shape
     nnz = A.nnz
@@ -275,15 +309,18 @@ def spmm(A: CsrMatrix, X: torch.Tensor) -> torch.Tensor:
     """Y = A X for CSR A on the GPU: FP64 values and block (tsvd_spmm), or FP32 values
     and block (tsvd_spmm_f32, the mixed form's SpMM)."""
     lib = capi.load()
+    if not isinstance(A, CsrMatrix):
+        raise TypeError("A must be a CsrMatrix")
+    _check_csr(A)
+    _check_rows(X, A.shape[1], "X")
     f32 = A.val.dtype == torch.float32
     if f32:
         if not (X.is_cuda and X.dtype == torch.float32 and X.dim() == 2 and X.stride(1) == 1):
             raise TypeError("X must be a 2-D float32 CUDA tensor with unit column stride")
     else:
         _cuda_f64(X, "X")
-        if A.val.dtype != torch.float64:
-            raise TypeError("spmm takes FP64 or FP32 CSR values")
     dev = X.device
+    _same_device(dev, (A.val, "A"))
     m, n = A.shape
     w = X.shape[1]
     Y = torch.empty((m, w), dtype=A.val.dtype, device=dev)
@@ -302,6 +339,9 @@ def dense_mm(A: torch.Tensor, X: torch.Tensor, trans: bool = False) -> torch.Ten
     """op(A) X for dense row-major A on the GPU: FP64 operands (tsvd_dense_mm), or
     FP32 operands (tsvd_dense_mm_f32, the mixed-precision form's kernels)."""
     lib = capi.load()
+    if not (isinstance(A, torch.Tensor) and A.dim() == 2):
+        raise TypeError("A must be a 2-D tensor")
+    _check_rows(X, A.shape[0] if trans else A.shape[1], "X")
     f32 = A.dtype == torch.float32
     if f32:
         for t, name in ((A, "A"), (X, "X")):
@@ -311,6 +351,7 @@ def dense_mm(A: torch.Tensor, X: torch.Tensor, trans: bool = False) -> torch.Ten
         _cuda_f64(A, "A")
         _cuda_f64(X, "X")
     dev = A.device
+    _same_device(dev, (X, "X"))
     m, n = A.shape
     w = X.shape[1]
     Y = torch.empty(((n if trans else m), w), dtype=A.dtype, device=dev)
@@ -452,6 +493,7 @@ def mm_bf16x6(P: Bf16x3, X: torch.Tensor) -> torch.Tensor:
     if X.shape[0] != P.cols:
         raise ValueError("X must have P.cols rows")
     dev = X.device
+    _same_device(dev, (P.data, "P"))
     w = X.shape[1]
     Y = torch.empty((P.rows, w), dtype=torch.float32, device=dev)
     nb = C.c_size_t()
@@ -490,9 +532,13 @@ def cholqr2(Y: torch.Tensor, seed: int = 0):
 def cgs_cqr2(Y: torch.Tensor, P: torch.Tensor, seed: int = 0):
     """CGS-CQR2 (Alg. 5) of a copy of Y against P: returns (Q, H, R, breakdowns)."""
     lib = capi.load()
+    if not (isinstance(Y, torch.Tensor) and Y.dim() == 2):
+        raise TypeError("Y must be a 2-D tensor")
+    _check_rows(P, Y.shape[0], "P")
     _cuda_f64(Y, "Y")
     _cuda_f64(P, "P")
     dev = Y.device
+    _same_device(dev, (P, "P"))
     Q = Y.clone()
     q, b = Q.shape
     s = P.shape[1]
