@@ -5,16 +5,22 @@
  * Matrices on Graphics Processors"):
  *   - RandSVD, randomized subspace iteration (Sec. 2.1, Alg. 1);
  *   - LancSVD, block Golub-Kahan-Lanczos bidiagonalisation with full two-sided
- *     block re-orthogonalisation and basic restart (Sec. 2.2, Alg. 2);
- * and their building blocks: CGS-QR (Alg. 3), CholeskyQR2 (Alg. 4),
+ *     block re-orthogonalisation and basic restart (Sec. 2.2, Alg. 2), or a
+ *     thick restart that keeps Ritz pairs (tsvd_opts.restart_keep);
+ * their building blocks: CGS-QR (Alg. 3), CholeskyQR2 (Alg. 4),
  * CGS-CQR2 (Alg. 5), the sparse/dense block products with A and A^T (Table 1),
  * the small SVD of the projected matrix (Alg. 1 S5, Alg. 2 S6) and the
- * Gaussian start block (Sec. 4).
+ * Gaussian start block (Sec. 4); a mixed-precision form of both methods
+ * (TSVD_PREC_MIXED); and the gradient of a loss on the k leading triplets
+ * with respect to A (tsvd_svd_backward).
  *
  * Conventions shared by every entry point
  *   - Dense blocks are ROW-MAJOR: element (i, j) of a block with leading
  *     dimension ld is at p[i * ld + j].  ld >= number of columns.
- *   - All arithmetic and all floating-point outputs are FP64.
+ *   - Arithmetic and floating-point outputs are FP64, except where an entry
+ *     point says otherwise: the *_f32 and BF16-piece products, and the FP32
+ *     blocks and products of the mixed form (TSVD_PREC_MIXED), whose returned
+ *     triplets are still FP64.
  *   - Pointers are CUDA device pointers unless a descriptor field says
  *     TSVD_HOST.  The caller owns every buffer; the library keeps no pointer
  *     after a call returns and never allocates device memory: scratch comes
