@@ -63,6 +63,25 @@ def test_spmm_matches_oracle(tsvd, torch_cuda, w):
     assert np.all(Y[5] == 0) and np.all(Y[1002] == 0)
 
 
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_spmm_empty_inputs(tsvd, torch_cuda, dtype):
+    """Degenerate shapes: no columns in the block (w = 0), no stored entries (nnz = 0,
+    Y = 0 exactly) and no rows (m = 0)."""
+    import scipy.sparse as sp
+    torch = torch_cuda
+    tdt = torch.float64 if dtype == np.float64 else torch.float32
+    A = workloads.csr_uniform(300, 200, 5, seed=11).astype(dtype)
+    Y = tsvd.spmm(tsvd.CsrMatrix.from_scipy(A), torch.zeros((200, 0), dtype=tdt, device="cuda"))
+    assert tuple(Y.shape) == (300, 0)
+    Z = sp.csr_matrix((300, 200), dtype=dtype)
+    X = torch.ones((200, 7), dtype=tdt, device="cuda")
+    Y = _np(tsvd.spmm(tsvd.CsrMatrix.from_scipy(Z), X))
+    assert Y.shape == (300, 7) and np.all(Y == 0)
+    E = sp.csr_matrix((0, 200), dtype=dtype)
+    Y = tsvd.spmm(tsvd.CsrMatrix.from_scipy(E), X)
+    assert tuple(Y.shape) == (0, 7)
+
+
 def test_spmm_strided_blocks(tsvd, torch_cuda):
     torch = torch_cuda
     A = workloads.csr_uniform(300, 200, 7, seed=3)
