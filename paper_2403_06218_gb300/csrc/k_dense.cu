@@ -132,8 +132,10 @@ struct TnPlan {
 };
 
 // One full wave of the kernel on a 152-SM GB300: 7 resident CTAs per SM for the
-// FP64 kernel (its 72 registers x 128 threads and 16 KB of shared memory allow 7),
-// 16 for the 64-thread FP32 kernel.  Splitting K so that regions x slabs fills
+// FP64 kernel (its 72 registers x 128 threads and 16 KB of shared memory allow 7).
+// The FP32 target assumes 16 CTAs of the 64-thread FP32 kernel; at its 72
+// registers only 14 are resident, so the last eighth of that split runs as a
+// short second wave.  Splitting K so that regions x slabs fills
 // exactly one wave keeps every SM equally busy; a fixed target (rather than the
 // device's SM count) keeps the split, the workspace size and the summation order
 // independent of the device.
