@@ -9,7 +9,7 @@ Each step follows the algorithm listing of the paper in its own order; a library
 primitive (numpy matrix product, scipy CSR product, LAPACK SVD as in the paper's
 Table 1, triangular solve as the paper's TRSM) stands for a single step.  Where
 the paper is silent, garbled or inconsistent, the reading taken is named at the
-point of use (labels G1..G23, listed with reasons in the design notes):
+point of use (labels G1..G25, listed with reasons in the design notes):
 
 * G7  CholeskyQR2 returns R = Lbar^T L^T (the product order that satisfies
       Q_out R = Q_in; the listing prints the factors swapped).
@@ -28,6 +28,10 @@ point of use (labels G1..G23, listed with reasons in the design notes):
 * G1  residual: max over j of the two one-sided residuals ||A v_j - sigma_j u_j||_2
       and ||A^T u_j - sigma_j v_j||_2, divided by sigma_1 (the second is ~0 by
       construction for both methods, so this equals the first in exact arithmetic).
+* G25 thick restart (the improved restart left to future work in Sec. 5), when
+      ``keep`` > 0: the leading Ritz pairs are kept, B starts with their singular
+      values and the coupling block of the residual block, and the recurrence
+      continues from that block.
 """
 
 from __future__ import annotations
