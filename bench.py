@@ -2,11 +2,14 @@
 
 One step = one full LancSVD solve (Alg. 2: start block, CSR(A^T) build, every
 restart cycle of SpMM / SpMM^T / CGS-CQR2 / Jacobi SVD, the residual checks and
-the Ritz vectors) on a synthetic 100,000 x 100,000 CSR matrix with exactly 10
-uniformly drawn distinct columns per row and N(0,1) values (seed 1), k = b = 64,
-r = 16 blocks, FP64 with the paper's basic restart (``--workload
-sparse100k-lanczos``).  The default workload restarts thick instead: r = 9
-blocks, 128 Ritz pairs kept.  A is resident in HBM before the timed region.
+the Ritz vectors), with A resident in HBM before the timed region.
+
+Default workload (``sparse100k-lanczos-thick``): a synthetic 100,000 x 100,000
+CSR matrix with exactly 10 uniformly drawn distinct columns per row and N(0,1)
+values (seed 1), k = b = 64, FP64, thick restart with r = 9 blocks per cycle and
+128 Ritz pairs kept.  ``--workload sparse100k-lanczos`` runs the paper's basic
+restart (r = 16); the other entries of WORKLOADS are the mixed-precision forms,
+RandSVD, and the dense and power-law matrices.
 
 Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead
 (host cores, bounded sample).  Multi-GPU (torchrun): independent replicas, one
