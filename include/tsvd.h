@@ -112,7 +112,9 @@ typedef struct tsvd_matrix {
 
 /* Options; fill with tsvd_default_opts() and override fields. */
 typedef struct tsvd_opts {
-    double tol;              /* LancSVD stops when max_j ||A v_j - s_j u_j|| <= tol * s_1 (default 1e-6) */
+    double tol;              /* LancSVD stops when the residual of every returned triplet,
+                                max(||A v_j - s_j u_j||, ||A^T u_j - s_j v_j||), is <= tol * s_1
+                                (default 1e-6) */
     int32_t max_restarts;    /* LancSVD restarts allowed after the first cycle (default 50) */
     int32_t qr_block;        /* RandSVD CGS-QR block width; 0 = min(k+p, TSVD_MAX_BLOCK) */
     int32_t output_location; /* TSVD_DEVICE or TSVD_HOST for sigma/U/V (default device) */
@@ -138,7 +140,8 @@ typedef struct tsvd_info {
     int32_t converged;       /* 1 if resid_max <= tol (LancSVD)                      */
     int32_t transposed;      /* 1 if m < n and the method ran on A^T                 */
     int32_t svd_sweeps;      /* Jacobi sweeps of the last small SVD                   */
-    double resid_max;        /* max_j ||A v_j - s_j u_j||_2 / s_1 of the returned triplets */
+    double resid_max;        /* max over j of ||A v_j - s_j u_j||_2 and ||A^T u_j - s_j v_j||_2,
+                                divided by s_1, for the returned triplets */
     double rho_last;         /* last Lanczos residual estimate / s_1                  */
     double ms_total;         /* whole call, including the CSR transpose build         */
     double ms_transpose;     /* CSR(A^T) build                                         */
@@ -190,8 +193,11 @@ int tsvd_rsvd(tsvd_handle* h, const tsvd_matrix* A, int k, int p, int q, uint64_
 
 /* LancSVD, Alg. 2 (Sec. 2.2): blocks of width b, r blocks per cycle (Krylov
  * dimension r*b), full block re-orthogonalisation on both sides (Alg. 5),
- * basic restart with the b leading Ritz vectors, repeated until
- * max_j ||A v_j - s_j u_j||_2 <= opts->tol * s_1 or opts->max_restarts.
+ * basic restart with the b leading Ritz vectors (or the thick restart of
+ * opts->restart_keep), repeated until the residual of every returned triplet
+ * (tsvd_opts.tol) is <= opts->tol * s_1, or opts->max_restarts.  A cycle ends
+ * early only when the Lanczos estimate rho_j = ||R_r vbar_j[last b rows]|| has
+ * passed; the explicit residual then confirms it.
  * The start block is N(0,1) Philox4x32-10 (key = seed, stream 2),
  * orthonormalised by CholeskyQR2 (S1), unless opts->start_block is given.
  * Outputs as tsvd_rsvd.  Requires 1 <= b <= TSVD_MAX_BLOCK, r >= 1,
