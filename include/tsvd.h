@@ -195,9 +195,9 @@ int tsvd_rsvd(tsvd_handle* h, const tsvd_matrix* A, int k, int p, int q, uint64_
  * dimension r*b), full block re-orthogonalisation on both sides (Alg. 5),
  * basic restart with the b leading Ritz vectors (or the thick restart of
  * opts->restart_keep), repeated until the residual of every returned triplet
- * (tsvd_opts.tol) is <= opts->tol * s_1, or opts->max_restarts.  A cycle ends
- * early only when the Lanczos estimate rho_j = ||R_r vbar_j[last b rows]|| has
- * passed; the explicit residual then confirms it.
+ * (tsvd_opts.tol) is <= opts->tol * s_1, or opts->max_restarts.  The explicit
+ * residual is computed only at the end of a cycle whose Lanczos estimate
+ * rho_j = ||R_r vbar_j[last b rows]|| has passed; it confirms the stop.
  * The start block is N(0,1) Philox4x32-10 (key = seed, stream 2),
  * orthonormalised by CholeskyQR2 (S1), unless opts->start_block is given.
  * Outputs as tsvd_rsvd.  Requires 1 <= b <= TSVD_MAX_BLOCK, r >= 1,
