@@ -395,14 +395,15 @@ int tsvd_small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, int nv,
  *     memory owned by the caller.
  *   - Shapes whose partial sums would exceed TSVD_NOALLOC_SCRATCH_BYTES return
  *     TSVD_ERR_UNSUPPORTED before any device work.
- *   - The first call on a device looks up the array's device address with the
- *     handle's device made current (cudaGetSymbolAddress); make that first call
- *     before any stream capture.
+ *   - Every call looks up the array's device address (cudaGetSymbolAddress)
+ *     with the handle's device made current, and restores the caller's
+ *     current device before returning.
  *   - Every call on a device shares the one array: calls whose work overlaps on
  *     the GPU (other streams, other threads) race on it and must be serialised
  *     by the caller.  Nothing in it needs to start at zero.
  *   - Each GPU that loads the library keeps the array until the process exits.
- *   - Synchronises `stream` before returning. */
+ *   - Synchronises `stream` before returning, so the call blocks the host
+ *     until the product is done. */
 #define TSVD_NOALLOC_SCRATCH_BYTES (4 * 1024 * 1024)
 int tsvd_dense_mm_t_noalloc(tsvd_handle* h, int64_t m, int64_t n, const double* A, int64_t lda,
                             int w, const double* X, int64_t ldx, double* Y, int64_t ldy,

@@ -11,8 +11,6 @@
 //
 // Cost of the design: every GPU that loads the library reserves the array
 // (kNoAllocScratchBytes) until the process exits, and all calls share it.
-#include <mutex>
-
 #include "tsvd_internal.cuh"
 
 namespace {
@@ -23,21 +21,14 @@ constexpr size_t kNoAllocScratchBytes = TSVD_NOALLOC_SCRATCH_BYTES;  // split-K 
 // object: its device address must be fetched with cudaGetSymbolAddress.
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchBytes / sizeof(double)];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch on the current device, fetched once per device.
-int scratch_address(int device, void** out) {
-    if (device < 0 || device >= kMaxDevices) return TSVD_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (g_scratch_addr[device] == nullptr) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || p == nullptr) return TSVD_ERR_CUDA;
-        g_scratch_addr[device] = p;
-    }
-    *out = g_scratch_addr[device];
+// Device address of the scratch on the current device.  It is looked up on every
+// call rather than cached: a cached address would go stale if the application
+// reset the device or rebuilt its context between calls.
+int scratch_address(void** out) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) return TSVD_ERR_CUDA;
+    *out = p;
     return TSVD_OK;
 }
 
@@ -49,9 +40,10 @@ extern "C" int tsvd_dense_mm_t_noalloc(tsvd_handle* h, int64_t m, int64_t n, con
         return TSVD_ERR_INVALID_ARG;
     const size_t need = tsvd::gemm_tn_ws(h, m, n, w, false);
     if (need > kNoAllocScratchBytes) return TSVD_ERR_UNSUPPORTED;
-    TSVD_TRY_CUDA(cudaSetDevice(h->device));
+    tsvd::DeviceGuard dg(h->device);
+    if (!dg.ok()) return TSVD_ERR_CUDA;
     void* scratch = nullptr;
-    TSVD_TRY(scratch_address(h->device, &scratch));
+    TSVD_TRY(scratch_address(&scratch));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // Every partial-sum slot the reduction reads is written first by the same
     // call, so nothing in the scratch has to start at zero.

@@ -207,7 +207,8 @@ int tsvd_rsvd(tsvd_handle* h, const tsvd_matrix* A, int k, int p, int q, uint64_
     size_t need = 0;
     TSVD_TRY(tsvd_workspace_size(A, TSVD_METHOD_RSVD, k, p, q, &o, &need));
     TSVD_TRY(check_ws(ws, ws_bytes, need));
-    TSVD_TRY_CUDA(cudaSetDevice(h->device));
+    DeviceGuard dg(h->device);
+    if (!dg.ok()) return TSVD_ERR_CUDA;
     ProfileGuard pg(h, (o.flags & TSVD_FLAG_PROFILE) != 0);
     const int bq = qr_block_of(&o, k + p);
     char* w = static_cast<char*>(ws);
@@ -226,7 +227,8 @@ int tsvd_blanczos(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uin
     size_t need = 0;
     TSVD_TRY(tsvd_workspace_size(A, TSVD_METHOD_BLANCZOS, k, b, r, &o, &need));
     TSVD_TRY(check_ws(ws, ws_bytes, need));
-    TSVD_TRY_CUDA(cudaSetDevice(h->device));
+    DeviceGuard dg(h->device);
+    if (!dg.ok()) return TSVD_ERR_CUDA;
     ProfileGuard pg(h, (o.flags & TSVD_FLAG_PROFILE) != 0);
     char* w = static_cast<char*>(ws);
     if (o.precision == TSVD_PREC_MIXED)
@@ -278,7 +280,8 @@ int tsvd_svd_backward(tsvd_handle* h, const tsvd_matrix* A, int k, const double*
     size_t need = 0;
     TSVD_TRY(tsvd_svd_backward_workspace(A, k, &o, &need));
     TSVD_TRY(check_ws(ws, ws_bytes, need));
-    TSVD_TRY_CUDA(cudaSetDevice(h->device));
+    DeviceGuard dg(h->device);
+    if (!dg.ok()) return TSVD_ERR_CUDA;
     if (info) std::memset(info, 0, sizeof(*info));
     return svd_backward_run(h, A, k, sigma, U, V, sigma_bar, U_bar, V_bar, grad, &o, static_cast<char*>(ws), ws_bytes,
                             nullptr, info);

@@ -55,6 +55,26 @@ enum StatusWord : int {
         if (tsvd_s_ < 0) return tsvd_s_;                      \
     } while (0)
 
+// Makes the handle's device current for the lifetime of the guard and restores
+// the caller's current device afterwards (on every return path).
+class DeviceGuard {
+  public:
+    explicit DeviceGuard(int device) {
+        ok_ = cudaGetDevice(&prev_) == cudaSuccess;
+        if (ok_ && prev_ != device) ok_ = cudaSetDevice(device) == cudaSuccess;
+        switched_ = ok_;
+        if (!ok_) prev_ = -1;
+    }
+    ~DeviceGuard() {
+        if (switched_ && prev_ >= 0) cudaSetDevice(prev_);
+    }
+    bool ok() const { return ok_; }
+
+  private:
+    int prev_ = -1;
+    bool ok_ = false, switched_ = false;
+};
+
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Brackets the launches of one kernel class with events on the launching stream.
