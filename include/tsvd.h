@@ -257,6 +257,34 @@ int tsvd_dense_mm(tsvd_handle* h, int trans, int64_t m, int64_t n, const double*
                   int w, const double* X, int64_t ldx, double* Y, int64_t ldy,
                   void* ws, size_t ws_bytes, void* stream);
 
+/* The same products, FP64-accurate, on the tensor cores (what the FP64 methods
+ * run for their Gram, projection, update and Ritz products when the shape is
+ * large enough; the dense GEMM rows of Table 1).  Each row of the left operand
+ * and each column of the right operand is scaled by its own power of two and
+ * split into 7 signed 8-bit digits held exactly in BF16 (exponent-aligned
+ * slicing: Ozaki, Ogita, Oishi, Rump 2012; Ootomo, Ozaki, Yokota 2024); the 28
+ * digit products of weight >= 2^-48 are summed as exact integers (BF16 MMAs with
+ * FP32 accumulation over 128 terms, then 64-bit integers) and scaled back in
+ * FP64.  With 2^ea_i, 2^eb_j the powers of two just above max_k |a_ik| and
+ * max_k |x_kj| (K = the inner dimension):
+ *   |Y - op(A) X|_ij <= 2^-56 (2^ea_i sum_k |x_kj| + sum_k |a_ik| 2^eb_j)
+ *                       + 6.2 K 2^(ea_i + eb_j - 56) + 2^-52 P sum_k |a_ik x_kj|
+ * (normwise FP64 accuracy; the middle term, the dropped digit products, is a
+ * sum of mean-zero terms and in practice near sqrt(K) of that; P is the number
+ * of FP64 partial sums the K range is cut into: one per CTA share of it and per
+ * 8,192 k within a share, 1 when K <= 8,192 and the output has at least 152
+ * tiles of 128 x 64).  Inf or NaN in
+ * a row of op(A) or a column of X gives
+ * NaN in the corresponding row (column) of Y.  Deterministic (fixed split and
+ * summation order).  Workspace from tsvd_dense_mm_f64tc_workspace (planes of
+ * both operands and split-K partial sums, 256-byte aligned).  Synchronises
+ * `stream` before returning; a device wait that gives up returns
+ * TSVD_ERR_TIMEOUT. */
+int tsvd_dense_mm_f64tc_workspace(int trans, int64_t m, int64_t n, int w, size_t* bytes);
+int tsvd_dense_mm_f64tc(tsvd_handle* h, int trans, int64_t m, int64_t n, const double* A, int64_t lda,
+                        int w, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                        void* ws, size_t ws_bytes, void* stream);
+
 /* The same products in FP32 (the mixed-precision form's kernels): A, X and Y
  * float32, products accumulated in FP32 within a row slab, and for trans = 1
  * the slabs' partial sums added in FP64 in a fixed order.  The workspace is

@@ -109,6 +109,8 @@ SIGNATURES = [
     ("tsvd_dense_mm_workspace", _I, [_I, _I64, _I64, _I, _PSZ]),
     ("tsvd_dense_mm", _I, [_P, _I, _I64, _I64, _P, _I64, _I, _P, _I64, _P, _I64, _P, _SZ, _P]),
     ("tsvd_dense_mm_f32", _I, [_P, _I, _I64, _I64, _P, _I64, _I, _P, _I64, _P, _I64, _P, _SZ, _P]),
+    ("tsvd_dense_mm_f64tc_workspace", _I, [_I, _I64, _I64, _I, _PSZ]),
+    ("tsvd_dense_mm_f64tc", _I, [_P, _I, _I64, _I64, _P, _I64, _I, _P, _I64, _P, _I64, _P, _SZ, _P]),
     ("tsvd_default_backward_opts", None, [_P]),
     ("tsvd_svd_backward_workspace", _I, [_P, _I, _P, _PSZ]),
     ("tsvd_svd_backward", _I, [_P, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),

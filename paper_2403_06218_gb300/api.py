@@ -335,9 +335,11 @@ def spmm(A: CsrMatrix, X: torch.Tensor) -> torch.Tensor:
     return Y
 
 
-def dense_mm(A: torch.Tensor, X: torch.Tensor, trans: bool = False) -> torch.Tensor:
-    """op(A) X for dense row-major A on the GPU: FP64 operands (tsvd_dense_mm), or
-    FP32 operands (tsvd_dense_mm_f32, the mixed-precision form's kernels)."""
+def dense_mm(A: torch.Tensor, X: torch.Tensor, trans: bool = False, tensor_cores: bool = False) -> torch.Tensor:
+    """op(A) X for dense row-major A on the GPU: FP64 operands (tsvd_dense_mm, or
+    with ``tensor_cores=True`` the FP64-accurate sliced product on the tensor cores,
+    tsvd_dense_mm_f64tc), or FP32 operands (tsvd_dense_mm_f32, the mixed-precision
+    form's kernels)."""
     lib = capi.load()
     if not (isinstance(A, torch.Tensor) and A.dim() == 2):
         raise TypeError("A must be a 2-D tensor")
@@ -355,10 +357,17 @@ def dense_mm(A: torch.Tensor, X: torch.Tensor, trans: bool = False) -> torch.Ten
     m, n = A.shape
     w = X.shape[1]
     Y = torch.empty(((n if trans else m), w), dtype=A.dtype, device=dev)
-    fn, name = (lib.tsvd_dense_mm_f32, "tsvd_dense_mm_f32") if f32 else (lib.tsvd_dense_mm, "tsvd_dense_mm")
+    if tensor_cores and f32:
+        raise TypeError("the tensor-core product takes float64 operands")
+    if tensor_cores:
+        fn, name, wsfn = lib.tsvd_dense_mm_f64tc, "tsvd_dense_mm_f64tc", lib.tsvd_dense_mm_f64tc_workspace
+    elif f32:
+        fn, name, wsfn = lib.tsvd_dense_mm_f32, "tsvd_dense_mm_f32", lib.tsvd_dense_mm_workspace
+    else:
+        fn, name, wsfn = lib.tsvd_dense_mm, "tsvd_dense_mm", lib.tsvd_dense_mm_workspace
     with torch.cuda.device(dev):
         nb = C.c_size_t()
-        capi.check(lib.tsvd_dense_mm_workspace(int(trans), m, n, w, C.byref(nb)), "tsvd_dense_mm_workspace")
+        capi.check(wsfn(int(trans), m, n, w, C.byref(nb)), name + "_workspace")
         ws = _ws(nb.value, dev)
         capi.check(fn(handle(dev), int(trans), m, n, A.data_ptr(), A.stride(0), w, X.data_ptr(), X.stride(0),
                       Y.data_ptr(), max(w, 1), ws.data_ptr(), ws.numel(), _stream_ptr(dev)), name)

@@ -504,6 +504,9 @@ int rsvd_run(tsvd_handle* h, const tsvd_matrix* A, int k, int p, int q, int bq, 
     T* Qsave = ar.take<T>((size_t)n * ell);
     Final f;
     carve_final(ar, o, m, n, k, kMixed, f);
+    // FP64 method: scratch of the FP64-accurate tensor-core products
+    const size_t ozb = kMixed ? 0 : oz_ws_bound(std::max(m, n), ell, ell);
+    void* ozws = kMixed ? nullptr : ar.take<char>(ozb);
     if (!run) {
         const int64_t qmax = m > n ? m : n;
         size_t t1 = orth_ws(h, qmax, ell > bq ? ell - bq : 0, bq) + align256(sizeof(double) * (size_t)ell * bq);
@@ -514,6 +517,7 @@ int rsvd_run(tsvd_handle* h, const tsvd_matrix* A, int k, int p, int q, int bq, 
         return TSVD_OK;
     }
     if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+    OzScope oz(h, ozws, ozb, status);
     OrthCtx ctx;
     ctx.seed = seed;
     // Q_0 (n x l): raw Gaussian block (Alg. 1)
@@ -637,6 +641,9 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
     double* g64 = kMixed ? ar.take<double>((size_t)m * b) : nullptr;
     Final f;
     carve_final(ar, o, m, n, k, kMixed, f);
+    // FP64 method: scratch of the FP64-accurate tensor-core products
+    const size_t ozb = kMixed ? 0 : oz_ws_bound(std::max(m, n), rb, std::max(std::max(b, k), keep));
+    void* ozws = kMixed ? nullptr : ar.take<char>(ozb);
     if (!run) {
         size_t t1 = orth_ws(h, m, rb, b);
         const size_t t2 = orth_ws(h, n, rb, b), t3 = small_svd_ws(rb), t4 = final_tail_ws(h, m, n, k, kMixed);
@@ -647,6 +654,7 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
         return TSVD_OK;
     }
     if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+    OzScope oz(h, ozws, ozb, status);
     OrthCtx ctx;
     ctx.seed = seed;
     double* dU = f.oU ? f.oU : (op.transposed ? V : U);

@@ -1,0 +1,694 @@
+// FP64-accurate products on the tensor cores for the FP64 method: the Gram and
+// projection products of CholeskyQR2 and CGS-CQR2 (Alg. 4 S1/S4, Alg. 5 S1/S6:
+// C = X^T Z), the updates and triangular solves (Alg. 5 S2/S7, Alg. 4 S3/S6:
+// Y = beta Y + alpha X M), and the Ritz / restart products (Alg. 2 S7-S9).
+// GB300's FP64 pipe issues 2 DFMA/clk/SM; its BF16 tensor cores are about 1500x
+// faster, so these products are run as exact integer arithmetic on BF16 digits
+// (the exponent-aligned slicing of Ozaki, Ogita, Oishi and Rump, 2012, with the
+// fixed-point digits of Ootomo, Ozaki and Yokota, 2024):
+//
+//  * every row of the left operand A and every column of the right operand B
+//    gets one exponent e (the smallest e with |x| < 2^e over that row or
+//    column); each entry becomes the 56-bit integer F = round(x 2^(55 - e)),
+//    split into 7 balanced base-256 digits d_0..d_6 (F = sum d_p 2^(8(6-p)),
+//    |d_p| <= 128).  Digit p is stored as the BF16 value d_p 2^(-8p) (exact);
+//  * the 28 digit products with p + q <= 6 are issued as tcgen05 MMAs (M = 128,
+//    N <= 64, K = 16, FP32 accumulators in tensor memory), one accumulator per
+//    value of p + q (7 accumulators, 448 TMEM columns).  Over 128 consecutive k
+//    each product is an integer times 2^(-8(p+q)) of magnitude <= 2^14 and each
+//    group sum T_{p+q} is an integer below 2^24, so every accumulation is exact
+//    whatever the tensor core's internal rounding;
+//  * every 128 k the epilogue converts the accumulators to integers and adds
+//    T_0..T_4 into a 64-bit integer (units of 2^-32 of the leading digit
+//    product), T_5 and T_6 (rounded to 2^-40) into a 32-bit one, and at the end
+//    of its K range writes C = 2^(ea + eb - 46) (hi + lo 2^-8) in FP64.
+// Each operand entry is represented to 2^-56 of its row (column) scale 2^e, the
+// dropped digit products are below 6.1 K 2^(ea + eb - 56), and the result is
+// rounded once to FP64: normwise FP64 accuracy (checked against exact products
+// in the CPU tests of the scheme and on the GPU).
+//
+// Layout: every operand is sliced into 7 BF16 planes stored K-major,
+// [7][rows][ld] (ld = K rounded up to 8), by one of two slicing kernels:
+//   rows  the source rows are the stored rows (A = X of X M: one exponent per
+//         source row, computed by the warp that slices the row);
+//   cols  the source columns are the stored rows (A = X^T and B = Z of X^T Z,
+//         B = M of X M: one exponent per source column, from a column-max pass
+//         with atomicMax, then a tiled transpose).
+// The product kernel (one CTA per SM, 320 threads) is the TMA / tcgen05
+// pipeline of the split-BF16 product: warp 0 loads 3-D boxes (32 K x rows x 7
+// planes, 64-byte swizzle) of both operands into a 2-stage ring, warp 1 owns 512
+// TMEM columns and issues the 56 MMAs of each stage from one thread, warps 2-9
+// drain the accumulators (two warps per 32 TMEM lanes, 32 columns each).  Work units (output tile, 32-wide K block) are split
+// over one wave of CTAs: whole tiles per CTA when there are more tiles than
+// CTAs (the epilogue writes the output itself), an even split of the K blocks
+// otherwise (partial tiles, added by a fix-up kernel in CTA order, so the
+// result is deterministic).  Every mbarrier wait is bounded.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "tc_ptx.cuh"
+#include "tsvd_internal.cuh"
+
+namespace tsvd {
+namespace {
+
+using namespace tcx;
+
+constexpr int kOzDig = 7;                                   // digits per operand entry
+constexpr int kOzM = 128;                                   // output rows per tile (TMEM lanes)
+constexpr int kOzN = 64;                                    // output columns per tile
+constexpr int kOzBK = 32;                                   // K per stage (one 64-byte row)
+constexpr int kOzRowB = 2 * kOzBK;
+constexpr int kOzStages = 2;
+constexpr int kOzPlaneA = kOzM * kOzRowB;                   // 8 KB
+constexpr int kOzPlaneB = kOzN * kOzRowB;                   // 4 KB
+constexpr int kOzStageBytes = kOzDig * (kOzPlaneA + kOzPlaneB);  // 84 KB
+constexpr int kOzSmem = kOzStages * kOzStageBytes + 1024;
+constexpr int kOzChunk = 4;          // K blocks per exact accumulation (128 k)
+constexpr int kOzFlushChunks = 64;   // chunks between FP64 flushes of the integer sums (8192 k)
+constexpr int kOzSlots = 7;          // accumulators: p+q = 6, 5, 4, 3, 2, 1, 0
+constexpr int kOzEpiWarps = 8;   // two per TMEM lane quarter, 32 columns each
+constexpr int kOzThreads = 64 + 32 * kOzEpiWarps;
+constexpr int kOzWave = 152;
+constexpr int kOzTmemCols = 512;
+constexpr int kOzNanExp = 1 << 20;      // exponent of a row holding Inf or NaN
+constexpr int kOzZeroExp = -(1 << 20);  // exponent of a zero entry
+
+// Digit pairs (p, q) in issue order, grouped by accumulator slot: slot s holds
+// the pairs with p + q = 6 - s.
+__constant__ int8_t c_pair_p[28] = {0, 1, 2, 3, 4, 5, 6, 0, 1, 2, 3, 4, 5, 0, 1, 2, 3, 4, 0, 1, 2, 3, 0, 1, 2, 0, 1, 0};
+__constant__ int8_t c_pair_q[28] = {6, 5, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0, 4, 3, 2, 1, 0, 3, 2, 1, 0, 2, 1, 0, 1, 0, 0};
+__constant__ int8_t c_slot_end[kOzSlots] = {7, 13, 18, 22, 25, 27, 28};
+
+// ---- digits ------------------------------------------------------------------
+__device__ inline int oz_exp(double x) {
+    const uint64_t u = (uint64_t)__double_as_longlong(x);
+    const int be = (int)((u >> 52) & 0x7FF);
+    const uint64_t mant = u & ((1ull << 52) - 1);
+    if (be == 0x7FF) return kOzNanExp;
+    if (be == 0) return mant == 0 ? kOzZeroExp : (63 - __clzll((long long)mant)) - 1073;
+    return be - 1022;
+}
+
+__device__ inline int oz_norm_exp(int e) { return e <= kOzZeroExp ? 0 : e; }
+
+// round(x 2^(55 - e)) (ties away from zero) as balanced base-256 digits.
+__device__ inline void oz_digits(double x, int e, int d[kOzDig]) {
+    const uint64_t u = (uint64_t)__double_as_longlong(x);
+    const int be = (int)((u >> 52) & 0x7FF);
+    uint64_t m = u & ((1ull << 52) - 1);
+    int q = -1074;
+    if (be != 0) {
+        m |= 1ull << 52;
+        q = be - 1075;
+    }
+    int64_t F = 0;
+    if (be != 0x7FF && e < kOzNanExp && m != 0) {
+        const int sh = q + 55 - e;  // <= 2 when |x| < 2^e
+        if (sh >= 0) {
+            F = (int64_t)(m << sh);
+        } else if (sh > -54) {
+            F = (int64_t)((m + (1ull << (-sh - 1))) >> (-sh));
+        }
+        if (u >> 63) F = -F;
+    }
+    int64_t r = F;
+#pragma unroll
+    for (int p = kOzDig - 1; p >= 1; --p) {
+        const int lo = (int)((r + 128) & 255) - 128;
+        d[p] = lo;
+        r = (r - lo) >> 8;
+    }
+    d[0] = (int)r;
+}
+
+__device__ inline float oz_digit_scale(int p) { return __int_as_float((127 - 8 * p) << 23); }  // 2^(-8p)
+
+__device__ inline __nv_bfloat162 oz_pack(int d0, int d1, int p) {
+    const float s = oz_digit_scale(p);
+    return __floats2bfloat162_rn((float)d0 * s, (float)d1 * s);  // exact: |d| <= 128
+}
+
+// Rows slicer: row i of S (R x K, lds) -> stored row i; one warp per row.
+__global__ void __launch_bounds__(256) oz_slice_rows_kernel(int64_t R, int64_t K, const double* __restrict__ S,
+                                                            int64_t lds, __nv_bfloat16* __restrict__ planes,
+                                                            int64_t ldk, int64_t pstride, int* __restrict__ eexp) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < R; i += nw) {
+        const double* src = S + i * lds;
+        int e = kOzZeroExp;
+        for (int64_t k = lane; k < K; k += 32) e = max(e, oz_exp(src[k]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+        e = oz_norm_exp(e);
+        if (lane == 0) eexp[i] = e;
+        for (int64_t k = 2 * lane; k < K; k += 64) {
+            int da[kOzDig], db[kOzDig];
+            oz_digits(src[k], e, da);
+            oz_digits(k + 1 < K ? src[k + 1] : 0.0, e, db);
+            __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(planes + i * ldk + k);
+#pragma unroll
+            for (int p = 0; p < kOzDig; ++p) dst[p * (pstride / 2)] = oz_pack(da[p], db[p], p);
+        }
+    }
+}
+
+// Column maxima of the exponents of S (K x R, lds); upper: entries with k > j are zero.
+__global__ void __launch_bounds__(256) oz_colmax_kernel(int64_t K, int64_t R, const double* __restrict__ S,
+                                                        int64_t lds, int upper, int64_t rows_per,
+                                                        int* __restrict__ eexp) {
+    __shared__ int red[8][33];
+    const int64_t j = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    const int64_t k0 = (int64_t)blockIdx.y * rows_per, k1 = min(K, k0 + rows_per);
+    int e = kOzZeroExp;
+    if (j < R)
+        for (int64_t k = k0 + threadIdx.y; k < k1; k += 8)
+            if (!(upper && k > j)) e = max(e, oz_exp(S[k * lds + j]));
+    red[threadIdx.y][threadIdx.x] = e;
+    __syncthreads();
+    if (threadIdx.y == 0 && j < R) {
+#pragma unroll
+        for (int y = 1; y < 8; ++y) e = max(e, red[y][threadIdx.x]);
+        atomicMax(&eexp[j], e);
+    }
+}
+
+// Cols slicer: column j of S (K x R, lds) -> stored row j, tiles of 64 k x 32 j.
+__global__ void __launch_bounds__(256) oz_slice_cols_kernel(int64_t K, int64_t R, const double* __restrict__ S,
+                                                            int64_t lds, int upper, const int* __restrict__ eexp,
+                                                            __nv_bfloat16* __restrict__ planes, int64_t ldk,
+                                                            int64_t pstride) {
+    __shared__ double tile[64][33];
+    const int64_t k0 = (int64_t)blockIdx.x * 64, j0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int r = ty; r < 64; r += 8) {
+        const int64_t k = k0 + r, j = j0 + tx;
+        double v = 0.0;
+        if (k < K && j < R && !(upper && k > j)) v = S[k * lds + j];
+        tile[r][tx] = v;
+    }
+    __syncthreads();
+    const int kp = tx;  // k pair within the tile
+    const int64_t k = k0 + 2 * kp;
+    if (k >= ldk) return;
+    for (int jj = ty; jj < 32; jj += 8) {
+        const int64_t j = j0 + jj;
+        if (j >= R) break;
+        const int e = oz_norm_exp(eexp[j]);
+        int da[kOzDig], db[kOzDig];
+        oz_digits(tile[2 * kp][jj], e, da);
+        oz_digits(tile[2 * kp + 1][jj], e, db);
+        __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(planes + j * ldk + k);
+#pragma unroll
+        for (int p = 0; p < kOzDig; ++p) dst[p * (pstride / 2)] = oz_pack(da[p], db[p], p);
+    }
+}
+
+__global__ void oz_fill_kernel(int64_t n, int v, int* __restrict__ x) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = v;
+}
+
+// ---- the product kernel ------------------------------------------------------
+struct OzArgs {
+    int64_t M, N, KB, tiles, total;
+    int NT, Npad, G, aligned, maxseg;
+    const int* ea;
+    const int* eb;
+    double* out;  // C (direct tiles)
+    int64_t ldo;
+    double alpha, beta;
+    int symmetric;
+    double* partial;  // [G][maxseg][128][64]
+    int* status;
+};
+
+__host__ __device__ inline int64_t oz_lo(int c, const OzArgs& a) {
+    return a.aligned ? ((int64_t)c * a.tiles / a.G) * a.KB : (int64_t)c * a.total / a.G;
+}
+
+// C = 2^(ea + eb - 14) (hi 2^-32 + lo 2^-40) in FP64.
+__device__ inline double oz_value(long long hi, int lo, int ea, int eb) {
+    if (ea >= kOzNanExp || eb >= kOzNanExp) return __longlong_as_double(0x7ff8000000000000LL);
+    const double x = fma((double)lo, 0.00390625, (double)hi);  // hi + lo 2^-8
+    const int E = ea + eb - 46;
+    if (E >= -1022 && E <= 1023) return x * __longlong_as_double((long long)(E + 1023) << 52);  // exact scaling
+    return ldexp(x, E);
+}
+
+// The output rule: out = alpha v + beta out (beta == 0: no read); a symmetric
+// product writes each pair (i, j), (j, i) once, from the entry with i <= j.
+__device__ inline void oz_store(const OzArgs& a, int64_t i, int64_t j, double v) {
+    if (a.symmetric) {
+        if (i > j) return;
+        a.out[i * a.ldo + j] = v;
+        a.out[j * a.ldo + i] = v;
+        return;
+    }
+    double* o = a.out + i * a.ldo + j;
+    *o = (a.beta != 0.0) ? fma(a.beta, *o, a.alpha * v) : a.alpha * v;
+}
+
+__global__ void __launch_bounds__(kOzThreads, 1)
+    oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzArgs a) {
+    extern __shared__ uint8_t dsm[];
+    __shared__ __align__(8) uint64_t bars[2 * kOzStages + 2 * kOzSlots + 1];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    const uint32_t base = (smem_u32(dsm) + 1023u) & ~1023u;
+    const uint32_t bar0 = smem_u32(bars);
+    auto full = [&](int s) { return bar0 + 8u * (uint32_t)s; };
+    auto empty = [&](int s) { return bar0 + 8u * (uint32_t)(kOzStages + s); };
+    auto accf = [&](int g) { return bar0 + 8u * (uint32_t)(2 * kOzStages + g); };
+    auto acce = [&](int g) { return bar0 + 8u * (uint32_t)(2 * kOzStages + kOzSlots + g); };
+    const uint32_t drain = bar0 + 8u * (uint32_t)(2 * kOzStages + 2 * kOzSlots);
+    volatile int* abort_flag = &s_abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = blockIdx.x;
+    const int64_t lo = oz_lo(c, a), hi = oz_lo(c + 1, a);
+    const int64_t KB = a.KB;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kOzStages; ++s) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), 1);
+        }
+        for (int g = 0; g < kOzSlots; ++g) {
+            mbar_init(accf(g), 1);
+            mbar_init(acce(g), 32 * kOzEpiWarps);
+        }
+        mbar_init(drain, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(smem_u32(&s_tmem), kOzTmemCols);
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = s_tmem;
+    const uint32_t stage_tx = (uint32_t)(kOzDig * (kOzPlaneA + a.Npad * kOzRowB));
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer: both operands' 7 planes of one 32-wide K block per stage
+            int64_t it = 0;
+            bool ok = true;
+            for (int64_t i = lo; i < hi && ok; ++i, ++it) {
+                const int st = (int)(it % kOzStages);
+                if (it >= kOzStages) ok = mbar_wait(empty(st), (uint32_t)(((it / kOzStages) - 1) & 1), abort_flag);
+                if (!ok) break;
+                const int64_t t = i / KB;
+                const int kx = (int)((i - t * KB) * kOzBK);
+                const int mt = (int)(t / a.NT), nt = (int)(t % a.NT);
+                const uint32_t sA = base + (uint32_t)st * kOzStageBytes;
+                mbar_arrive_expect_tx(full(st), stage_tx);
+                tma_load_3d(sA, &tmA, kx, mt * kOzM, 0, full(st));
+                tma_load_3d(sA + kOzDig * kOzPlaneA, &tmB, kx, nt * kOzN, 0, full(st));
+            }
+            if (!ok) {
+                atomicOr(&a.status[kStTimeout], 1);
+                s_abort = 1;
+            }
+            const int64_t first = it > kOzStages ? it - kOzStages : 0;
+            for (int64_t j = first; j < it; ++j) mbar_drain(full((int)(j % kOzStages)), (uint32_t)((j / kOzStages) & 1));
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer
+            const uint32_t idesc = idesc_bf16(kOzM, a.Npad);
+            const uint32_t planeB = (uint32_t)(a.Npad * kOzRowB);
+            int64_t it = 0, ch = 0;  // K blocks and chunks issued by this CTA
+            bool ok = true;
+            for (int64_t i = lo; i < hi && ok;) {
+                const int64_t t = i / KB;
+                const int64_t e = min(hi, (t + 1) * KB);
+                for (; i < e && ok; ++ch) {
+                    const int64_t ce = min(e, i + kOzChunk);
+                    for (int64_t i0 = i; i < ce; ++i, ++it) {
+                        const int st = (int)(it % kOzStages);
+                        ok = mbar_wait(full(st), (uint32_t)((it / kOzStages) & 1), abort_flag);
+                        if (!ok) break;
+                        fence_after();
+                        const bool first_kb = (i == i0), last_kb = (i + 1 == ce);
+                        const uint32_t sA = base + (uint32_t)st * kOzStageBytes;
+                        const uint32_t sB = sA + kOzDig * kOzPlaneA;
+                        int pr = 0;
+                        for (int g = 0; g < kOzSlots && ok; ++g) {
+                            if (first_kb && ch > 0) {
+                                // the epilogue has drained this accumulator of the previous chunk
+                                ok = mbar_wait(acce(g), (uint32_t)((ch - 1) & 1), abort_flag);
+                                if (!ok) break;
+                                fence_after();
+                            }
+                            const uint32_t d = tmem + (uint32_t)(g * kOzN);
+                            const int pe = c_slot_end[g];
+                            for (; pr < pe; ++pr) {
+                                const uint32_t pA = sA + (uint32_t)c_pair_p[pr] * kOzPlaneA;
+                                const uint32_t pB = sB + (uint32_t)c_pair_q[pr] * planeB;
+                                const bool fresh = first_kb && (pr == (g == 0 ? 0 : c_slot_end[g - 1]));
+                                mma_bf16(d, sdesc_sw64(pA), sdesc_sw64(pB), idesc, fresh ? 0u : 1u);
+                                mma_bf16(d, sdesc_sw64(pA + 32), sdesc_sw64(pB + 32), idesc, 1u);
+                            }
+                            if (last_kb) commit(accf(g));
+                        }
+                        if (!ok) break;
+                        commit(empty(st));
+                    }
+                }
+            }
+            if (!ok) {
+                atomicOr(&a.status[kStTimeout], 1);
+                s_abort = 1;
+            }
+            commit(drain);
+            mbar_drain(drain, 0);
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 and 32 of the columns
+        const int quarter = warp & 3;
+        const int cg = (warp - 2) >> 2;        // column half: columns 32 cg .. 32 cg + 31
+        const int ncol = a.Npad >> 1;          // 16 or 32 valid columns in this half
+        const int r = quarter * 32 + lane;
+        const uint32_t tlane = (uint32_t)(quarter * 32) << 16;
+        int64_t ch = 0;
+        int seg = 0;
+        bool ok = true;
+        for (int64_t i = lo; i < hi && ok; ++seg) {
+            const int64_t t = i / KB;
+            const int64_t e = min(hi, (t + 1) * KB);
+            const int mt = (int)(t / a.NT), nt = (int)(t % a.NT);
+            const int64_t row = (int64_t)mt * kOzM + r;
+            const int64_t col0 = (int64_t)nt * kOzN + cg * ncol;
+            const bool direct = (i == t * KB) && (e == (t + 1) * KB) && KB <= (int64_t)kOzChunk * kOzFlushChunks;
+            const int ea = row < a.M ? a.ea[row] : 0;
+            double* slot = a.partial + (((int64_t)c * a.maxseg + seg) * kOzM + r) * kOzN + cg * ncol;
+            // integer sums of the digit products: hi in units of 2^-32 (p + q <= 4, exact),
+            // lo in units of 2^-40 (p + q = 5 exact, p + q = 6 rounded to 2^-40)
+            long long hi[32];
+            int lo[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0;
+            int nchunks = 0;
+            bool stored = false;
+            for (; i < e && ok; ++ch) {
+                const int64_t ce = min(e, i + kOzChunk);
+                for (int g = 0; g < kOzSlots; ++g) {
+                    int w_ok = 1;
+                    if (lane == 0) w_ok = mbar_wait(accf(g), (uint32_t)(ch & 1), abort_flag) ? 1 : 0;
+                    w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
+                    if (!w_ok) {
+                        if (lane == 0) {
+                            atomicOr(&a.status[kStTimeout], 1);
+                            s_abort = 1;
+                        }
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    // slot g holds T_d 2^(-8d), d = 6 - g, with T_d an integer below 2^24
+                    const int d = 6 - g;
+                    const float mul = oz_digit_scale(-d);
+                    const uint32_t taddr = tmem + tlane + (uint32_t)(g * kOzN + cg * ncol);
+#pragma unroll
+                    for (int c0 = 0; c0 < 32; c0 += 16) {
+                        if (c0 < ncol) {
+                            float v[16];
+                            tmem_ld16(taddr + (uint32_t)c0, v);
+                            if (d <= 4) {
+#pragma unroll
+                                for (int q = 0; q < 16; ++q)
+                                    hi[c0 + q] += (long long)__float2int_rn(v[q] * mul) << (8 * (4 - d));
+                            } else if (d == 5) {
+#pragma unroll
+                                for (int q = 0; q < 16; ++q) lo[c0 + q] += __float2int_rn(v[q] * mul);
+                            } else {
+#pragma unroll
+                                for (int q = 0; q < 16; ++q) lo[c0 + q] += (__float2int_rn(v[q] * mul) + 128) >> 8;
+                            }
+                        }
+                    }
+                    fence_before();
+                    mbar_arrive(acce(g));
+                }
+                if (!ok) break;
+                i = ce;
+                ++nchunks;
+                const bool seg_end = (i == e);
+                if (!(seg_end || nchunks % kOzFlushChunks == 0)) continue;
+                if (direct) {
+                    // the whole tile's K range in this CTA: the final output
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int64_t col = col0 + j;
+                        if (j < ncol && row < a.M && col < a.N)
+                            oz_store(a, row, col, oz_value(hi[j], lo[j], ea, a.eb[col]));
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int64_t col = col0 + j;
+                        if (j < ncol) {
+                            const double v = (row < a.M && col < a.N) ? oz_value(hi[j], lo[j], ea, a.eb[col]) : 0.0;
+                            slot[j] = stored ? slot[j] + v : v;
+                        }
+                        hi[j] = lo[j] = 0;
+                    }
+                    stored = true;
+                }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        tmem_dealloc(tmem, kOzTmemCols);
+    }
+}
+
+// Tiles whose K range is split over CTAs (or longer than one 64-bit
+// accumulation): the parts are added in CTA order and the output rule applied.
+__global__ void oz_fixup_kernel(OzArgs a) {
+    __shared__ int s_c0, s_c1;
+    const int64_t t = blockIdx.y;
+    const int64_t KB = a.KB;
+    if (threadIdx.x == 0) {
+        auto cta_of = [&](int64_t u) {
+            int cc = (int)(u * a.G / a.total);
+            while (cc + 1 < a.G && oz_lo(cc + 1, a) <= u) ++cc;
+            while (cc > 0 && oz_lo(cc, a) > u) --cc;
+            return cc;
+        };
+        s_c0 = cta_of(t * KB);
+        s_c1 = cta_of((t + 1) * KB - 1);
+    }
+    __syncthreads();
+    if (s_c0 == s_c1 && KB <= (int64_t)kOzChunk * kOzFlushChunks) return;  // written by its CTA
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= kOzM * kOzN) return;
+    const int r = idx / kOzN, cl = idx % kOzN;
+    const int mt = (int)(t / a.NT), nt = (int)(t % a.NT);
+    const int64_t row = (int64_t)mt * kOzM + r, col = (int64_t)nt * kOzN + cl;
+    if (row >= a.M || col >= a.N) return;
+    double acc = 0.0;
+    for (int cc = s_c0; cc <= s_c1; ++cc) {
+        const int seg = (int)(t - oz_lo(cc, a) / KB);
+        acc += a.partial[(((int64_t)cc * a.maxseg + seg) * kOzM + r) * kOzN + cl];
+    }
+    oz_store(a, row, col, acc);
+}
+
+// ---- host side -------------------------------------------------------------------
+struct OzPlan {
+    int64_t M, N, K, KB, tiles, total;
+    int MT, NT, Npad, G, maxseg;
+    bool aligned;
+};
+
+OzPlan oz_plan(int64_t M, int64_t N, int64_t K) {
+    OzPlan p{};
+    p.M = M;
+    p.N = N;
+    p.K = K;
+    p.MT = (int)((M + kOzM - 1) / kOzM);
+    p.NT = (int)((N + kOzN - 1) / kOzN);
+    p.Npad = N <= 32 ? 32 : kOzN;
+    p.KB = std::max<int64_t>(1, (K + kOzBK - 1) / kOzBK);
+    p.tiles = (int64_t)p.MT * p.NT;
+    p.total = p.tiles * p.KB;
+    p.aligned = p.tiles >= kOzWave;
+    p.G = (int)std::min<int64_t>(kOzWave, p.aligned ? p.tiles : p.total);
+    p.maxseg = 1;
+    OzArgs a{};
+    a.KB = p.KB;
+    a.tiles = p.tiles;
+    a.total = p.total;
+    a.G = p.G;
+    a.aligned = p.aligned ? 1 : 0;
+    for (int c = 0; c < p.G; ++c) {
+        const int64_t lo = oz_lo(c, a), hi = oz_lo(c + 1, a);
+        if (hi > lo) p.maxseg = std::max<int>(p.maxseg, (int)((hi - 1) / p.KB - lo / p.KB + 1));
+    }
+    return p;
+}
+
+inline int64_t oz_ld(int64_t K) { return (K + 7) / 8 * 8; }
+inline size_t oz_planes_bytes(int64_t rows, int64_t K) {
+    return align256((size_t)kOzDig * (size_t)rows * (size_t)oz_ld(K) * 2);
+}
+inline size_t oz_partial_bytes(const OzPlan& p) {
+    const bool needs = !p.aligned || p.KB > (int64_t)kOzChunk * kOzFlushChunks;
+    return needs ? align256(sizeof(double) * (size_t)p.G * p.maxseg * kOzM * kOzN) : 0;
+}
+
+struct OzBufs {
+    __nv_bfloat16 *pa, *pb;
+    int *ea, *eb;
+    double* partial;
+};
+
+OzBufs oz_carve(Arena& ar, const OzPlan& p, bool shared_ab) {
+    OzBufs b{};
+    b.pa = reinterpret_cast<__nv_bfloat16*>(ar.take<char>(oz_planes_bytes(p.M, p.K)));
+    b.pb = shared_ab ? b.pa : reinterpret_cast<__nv_bfloat16*>(ar.take<char>(oz_planes_bytes(p.N, p.K)));
+    b.ea = ar.take<int>((size_t)p.M);
+    b.eb = shared_ab ? b.ea : ar.take<int>((size_t)p.N);
+    const size_t pb = oz_partial_bytes(p);
+    b.partial = pb ? reinterpret_cast<double*>(ar.take<char>(pb)) : nullptr;
+    return b;
+}
+
+int oz_slice_rows(tsvd_handle* h, int64_t R, int64_t K, const double* S, int64_t lds, __nv_bfloat16* planes,
+                  int* eexp, cudaStream_t st) {
+    if (R == 0) return TSVD_OK;
+    const int64_t ldk = oz_ld(K);
+    const int64_t blocks = std::min<int64_t>((R + 7) / 8, (int64_t)h->sm_count * 16);
+    h->launches++;
+    oz_slice_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(R, K, S, lds, planes, ldk, R * ldk, eexp);
+    TSVD_TRY_CUDA(cudaGetLastError());
+    return TSVD_OK;
+}
+
+int oz_slice_cols(tsvd_handle* h, int64_t K, int64_t R, const double* S, int64_t lds, bool upper,
+                  __nv_bfloat16* planes, int* eexp, cudaStream_t st) {
+    if (R == 0) return TSVD_OK;
+    const int64_t ldk = oz_ld(K);
+    const unsigned gx = (unsigned)((R + 31) / 32);
+    int64_t gy = std::min<int64_t>((K + 255) / 256, std::max<int64_t>(1, (int64_t)h->sm_count * 8 / gx));
+    const int64_t rows_per = (K + gy - 1) / gy;
+    gy = (K + rows_per - 1) / rows_per;
+    h->launches += 3;
+    oz_fill_kernel<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(R, kOzZeroExp - 1, eexp);
+    oz_colmax_kernel<<<dim3(gx, (unsigned)std::max<int64_t>(1, gy)), dim3(32, 8), 0, st>>>(K, R, S, lds,
+                                                                                           upper ? 1 : 0, rows_per,
+                                                                                           eexp);
+    const dim3 sg((unsigned)((oz_ld(K) + 63) / 64), gx);
+    oz_slice_cols_kernel<<<sg, 256, 0, st>>>(K, R, S, lds, upper ? 1 : 0, eexp, planes, ldk, R * ldk);
+    TSVD_TRY_CUDA(cudaGetLastError());
+    return TSVD_OK;
+}
+
+int oz_run(tsvd_handle* h, const OzPlan& p, const OzBufs& b, double* out, int64_t ldo, double alpha, double beta,
+           bool symmetric, int* status, cudaStream_t st) {
+    if (p.tiles > 65535) return TSVD_ERR_UNSUPPORTED;  // one fix-up grid row per tile
+    static thread_local int configured = -1;
+    if (configured != h->device) {
+        TSVD_TRY_CUDA(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem));
+        configured = h->device;
+    }
+    CUtensorMap mA, mB;
+    if (!make_plane_map(&mA, b.pa, p.K, p.M, oz_ld(p.K), kOzM, kOzDig)) return TSVD_ERR_CUDA;
+    if (!make_plane_map(&mB, b.pb, p.K, p.N, oz_ld(p.K), p.Npad, kOzDig)) return TSVD_ERR_CUDA;
+    OzArgs a{};
+    a.M = p.M;
+    a.N = p.N;
+    a.KB = p.KB;
+    a.tiles = p.tiles;
+    a.total = p.total;
+    a.NT = p.NT;
+    a.Npad = p.Npad;
+    a.G = p.G;
+    a.aligned = p.aligned ? 1 : 0;
+    a.maxseg = p.maxseg;
+    a.ea = b.ea;
+    a.eb = b.eb;
+    a.out = out;
+    a.ldo = ldo;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.symmetric = symmetric ? 1 : 0;
+    a.partial = b.partial;
+    a.status = status;
+    h->launches++;
+    oz_gemm_kernel<<<p.G, kOzThreads, kOzSmem, st>>>(mA, mB, a);
+    TSVD_TRY_CUDA(cudaGetLastError());
+    if (b.partial) {
+        h->launches++;
+        oz_fixup_kernel<<<dim3((kOzM * kOzN + 255) / 256, (unsigned)p.tiles), 256, 0, st>>>(a);
+        TSVD_TRY_CUDA(cudaGetLastError());
+    }
+    return TSVD_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+bool oz_worth(int64_t M, int64_t N, int64_t K) {
+    // below ~30 MFLOP the FP64 pipe finishes before the slicing passes would
+    const int64_t tiles = ((M + kOzM - 1) / kOzM) * ((N + kOzN - 1) / kOzN);
+    return M > 0 && N > 0 && K >= 32 && tiles <= 65535 && N <= 65535 * 32 && 2.0 * (double)M * N * K >= 3.0e7;
+}
+
+size_t oz_tn_ws(int64_t q, int64_t s, int64_t b, bool symmetric) {
+    Arena ar;
+    oz_carve(ar, oz_plan(s, b, q), symmetric);
+    return ar.off;
+}
+
+size_t oz_nn_ws(int64_t q, int64_t s, int64_t b) {
+    Arena ar;
+    oz_carve(ar, oz_plan(q, b, s), false);
+    return ar.off;
+}
+
+size_t oz_ws_bound(int64_t qmax, int64_t smax, int64_t bmax) {
+    size_t w = 0;
+    for (int64_t s : {smax, bmax})
+        for (int64_t b : {bmax, smax}) {
+            w = std::max(w, oz_tn_ws(qmax, s, b, false));
+            w = std::max(w, oz_nn_ws(qmax, s, b));
+        }
+    return w + 4096;
+}
+
+int oz_gemm_tn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, const double* X, int64_t ldx, const double* Z,
+               int64_t ldz, double* C, int64_t ldc, bool symmetric, void* ws, size_t ws_bytes, int* status,
+               cudaStream_t st) {
+    const OzPlan p = oz_plan(s, b, q);
+    Arena ar{static_cast<char*>(ws), ws_bytes, 0};
+    const OzBufs bf = oz_carve(ar, p, symmetric);
+    if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+    TSVD_TRY(oz_slice_cols(h, q, s, X, ldx, false, bf.pa, bf.ea, st));
+    if (!symmetric) TSVD_TRY(oz_slice_cols(h, q, b, Z, ldz, false, bf.pb, bf.eb, st));
+    return oz_run(h, p, bf, C, ldc, 1.0, 0.0, symmetric, status, st);
+}
+
+int oz_gemm_nn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, double alpha, const double* X, int64_t ldx,
+               const double* Mm, int64_t ldm, double beta, double* Y, int64_t ldy, bool upper, void* ws,
+               size_t ws_bytes, int* status, cudaStream_t st) {
+    const OzPlan p = oz_plan(q, b, s);
+    Arena ar{static_cast<char*>(ws), ws_bytes, 0};
+    const OzBufs bf = oz_carve(ar, p, false);
+    if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+    TSVD_TRY(oz_slice_rows(h, q, s, X, ldx, bf.pa, bf.ea, st));
+    TSVD_TRY(oz_slice_cols(h, s, b, Mm, ldm, upper, bf.pb, bf.eb, st));
+    return oz_run(h, p, bf, Y, ldy, alpha, beta, false, status, st);
+}
+
+}  // namespace tsvd

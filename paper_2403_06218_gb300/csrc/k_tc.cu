@@ -40,6 +40,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "tc_ptx.cuh"
 #include "tsvd_internal.cuh"
 
 namespace tsvd {
@@ -58,94 +59,9 @@ constexpr int kTcEpiWarps = 8;                      // two per TMEM lane quarter
 constexpr int kTcThreads = 64 + 32 * kTcEpiWarps;
 constexpr int kTcWave = 152;
 constexpr int kTcTmemCols = 256;
-constexpr long long kTcMaxWait = 2000000000LL;     // clock64 cycles (about 1 s)
+constexpr long long kTcMaxWait = tcx::kMaxWait;
 
-// ---- PTX wrappers ----------------------------------------------------------
-__device__ inline uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ inline void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ inline void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ inline void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ inline bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Waits for the completion of the phase with the given parity; false if the
-// wait gave up (deadline or another role's abort).
-__device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (*abort_flag) return false;
-        if (clock64() - t0 > kTcMaxWait) return false;
-    }
-    return true;
-}
-
-__device__ inline void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
-        : "memory");
-}
-
-__device__ inline void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ inline void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, rows of
-// 64 bytes, 8-row groups 512 bytes apart (tile base 512-byte aligned).
-__device__ inline uint64_t sdesc_sw64(uint32_t addr) {
-    return (uint64_t)((addr >> 4) & 0x3FFFu)  // start address / 16
-           | ((uint64_t)1 << 16)              // leading byte offset (unused for swizzled K-major)
-           | ((uint64_t)(512 >> 4) << 32)     // stride byte offset: 8 rows x 64 B
-           | ((uint64_t)1 << 46)              // descriptor version of tcgen05
-           | ((uint64_t)4 << 61);             // swizzle mode: 64 B
-}
-
-// Instruction descriptor of kind::f16: FP32 D, BF16 A and B, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ inline void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-__device__ inline void tc_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-__device__ inline void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
+using namespace tcx;
 
 struct TcPlan {
     int64_t tiles, kb, total;  // row tiles, K blocks per tile, tiles x kb
@@ -194,9 +110,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    tc_fence_before();
+    fence_before();
     __syncthreads();
-    tc_fence_after();
+    fence_after();
     const uint32_t tmem = s_tmem;
     const uint32_t stage_tx = (uint32_t)(3 * kTcPieceA + 3 * Npad * kTcRowB);
 
@@ -249,7 +165,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     if (g >= 2) {
                         ok = mbar_wait(acce(a), (uint32_t)(((g >> 1) - 1) & 1), abort_flag);
                         if (!ok) break;
-                        tc_fence_after();
+                        fence_after();
                     }
                     const uint32_t d = tmem + (uint32_t)(a * kTcMaxN);
                     uint32_t acc = 0;
@@ -257,7 +173,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         const int st = (int)(it % kTcStages);
                         ok = mbar_wait(full(st), (uint32_t)((it / kTcStages) & 1), abort_flag);
                         if (!ok) break;
-                        tc_fence_after();
+                        fence_after();
                         const uint32_t sA = base + (uint32_t)st * kTcStageBytes;
                         const uint32_t sX = sA + 3 * kTcPieceA;
 #pragma unroll
@@ -267,14 +183,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                                 const uint64_t ad = sdesc_sw64(sA + (uint32_t)(kTermA[tm] * kTcPieceA + kk * 32));
                                 const uint64_t bd =
                                     sdesc_sw64(sX + (uint32_t)(kTermX[tm] * Npad * kTcRowB + kk * 32));
-                                tc_mma(d, ad, bd, idesc, acc);
+                                mma_bf16(d, ad, bd, idesc, acc);
                                 acc = 1;
                             }
                         }
-                        tc_commit(empty(st));
+                        commit(empty(st));
                     }
                     if (!ok) break;
-                    tc_commit(accf(a));
+                    commit(accf(a));
                 }
             }
             if (!ok) {
@@ -282,7 +198,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 s_abort = 1;
             }
             // every product issued has finished before the tensor memory is freed
-            tc_commit(drain);
+            commit(drain);
             const long long t0 = clock64();
             while (!mbar_try_wait(drain, 0))
                 if (clock64() - t0 > kTcMaxWait) break;
@@ -320,7 +236,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     ok = false;
                     break;
                 }
-                tc_fence_after();
+                fence_after();
                 const uint32_t taddr = tmem + tlane + (uint32_t)(a * kTcMaxN + half * ncol);
 #pragma unroll
                 for (int c0 = 0; c0 < kTcMaxN / 2; c0 += 16) {
@@ -331,7 +247,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         for (int q = 0; q < 16; ++q) sum[c0 + q] += v[q];
                     }
                 }
-                tc_fence_before();
+                fence_before();
                 mbar_arrive(acce(a));
             }
             if (!ok) break;
@@ -341,10 +257,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 if (c0 < ncol) reinterpret_cast<float4*>(dst)[c0 / 4] = make_float4(sum[c0], sum[c0 + 1], sum[c0 + 2], sum[c0 + 3]);
         }
     }
-    tc_fence_before();
+    fence_before();
     __syncthreads();
     if (warp == 1) {
-        tc_fence_after();
+        fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
     }
 }
@@ -436,35 +352,9 @@ __global__ void split3_kernel(int64_t rows, int64_t cols, const T* __restrict__ 
 }
 
 // ---- host side ---------------------------------------------------------------
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-    static std::once_flag once;
-    static EncodeTiledFn fn = nullptr;
-    std::call_once(once, [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q{};
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    });
-    return fn;
-}
-
 // 3-D map over pieces [3][rows][ld] (BF16), box 32 (K) x box_rows x 3, 64-byte swizzle.
 bool make_map(CUtensorMap* map, const void* base, int64_t cols, int64_t rows, int64_t ld, int box_rows) {
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) return false;
-    const cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, 3};
-    const cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * 2 * (cuuint64_t)rows};
-    const cuuint32_t box[3] = {(cuuint32_t)kTcBK, (cuuint32_t)box_rows, 3};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return make_plane_map(map, base, cols, rows, ld, box_rows, 3);
 }
 
 TcPlan tc_plan(int64_t rows, int64_t cols) {
@@ -558,4 +448,34 @@ cudaError_t tc_mm(tsvd_handle* h, int64_t rows, int64_t cols, const void* pieces
     return cudaSuccess;
 }
 
+namespace tcx {
+
+EncodeTiledFn encode_fn() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+bool make_plane_map(CUtensorMap* map, const void* base, int64_t cols, int64_t rows, int64_t ld, int box_rows,
+                    int planes) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * 2 * (cuuint64_t)rows};
+    const cuuint32_t box[3] = {32u, (cuuint32_t)box_rows, (cuuint32_t)planes};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace tcx
 }  // namespace tsvd

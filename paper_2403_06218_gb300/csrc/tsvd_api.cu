@@ -390,6 +390,46 @@ int tsvd_dense_mm(tsvd_handle* h, int trans, int64_t m, int64_t n, const double*
     return TSVD_OK;
 }
 
+int tsvd_dense_mm_f64tc_workspace(int trans, int64_t m, int64_t n, int w, size_t* bytes) {
+    if (!bytes || m < 0 || n < 0 || w < 0) return TSVD_ERR_INVALID_ARG;
+    // 256 bytes of status words, then the product's scratch
+    *bytes = 256 + (trans ? oz_tn_ws(m, n, w, false) : oz_nn_ws(m, n, w));
+    return TSVD_OK;
+}
+
+int tsvd_dense_mm_f64tc(tsvd_handle* h, int trans, int64_t m, int64_t n, const double* A, int64_t lda, int w,
+                        const double* X, int64_t ldx, double* Y, int64_t ldy, void* ws, size_t ws_bytes,
+                        void* stream) {
+    if (!h || m < 0 || n < 0 || w < 0 || lda < n || ldx < w || ldy < w) return TSVD_ERR_INVALID_ARG;
+    // empty operands may come with null pointers
+    if ((m * n > 0 && !A) || ((trans ? m : n) * w > 0 && !X) || ((trans ? n : m) * w > 0 && !Y))
+        return TSVD_ERR_INVALID_ARG;
+    size_t need = 0;
+    TSVD_TRY(tsvd_dense_mm_f64tc_workspace(trans, m, n, w, &need));
+    TSVD_TRY(check_ws(ws, ws_bytes, need));
+    DeviceGuard dg(h->device);
+    if (!dg.ok()) return TSVD_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t rows = trans ? n : m;
+    if (rows == 0 || w == 0) return TSVD_OK;
+    if ((trans ? m : n) == 0) {
+        for (int64_t i = 0; i < rows; ++i) TSVD_TRY_CUDA(cudaMemsetAsync(Y + i * ldy, 0, sizeof(double) * w, st));
+        TSVD_TRY_CUDA(cudaStreamSynchronize(st));
+        return TSVD_OK;
+    }
+    int* status = static_cast<int*>(ws);
+    char* scratch = static_cast<char*>(ws) + 256;
+    TSVD_TRY_CUDA(cudaMemsetAsync(status, 0, sizeof(int) * kStCount, st));
+    if (trans)
+        TSVD_TRY(oz_gemm_tn(h, m, n, w, A, lda, X, ldx, Y, ldy, false, scratch, need - 256, status, st));
+    else
+        TSVD_TRY(oz_gemm_nn(h, m, n, w, 1.0, A, lda, X, ldx, 0.0, Y, ldy, false, scratch, need - 256, status, st));
+    int hs[kStCount];
+    TSVD_TRY(read_status(st, status, hs));
+    if (hs[kStTimeout]) return TSVD_ERR_TIMEOUT;
+    return TSVD_OK;
+}
+
 int tsvd_dense_mm_f32(tsvd_handle* h, int trans, int64_t m, int64_t n, const float* A, int64_t lda, int w,
                       const float* X, int64_t ldx, float* Y, int64_t ldy, void* ws, size_t ws_bytes, void* stream) {
     if (!h || m < 0 || n < 0 || w < 0 || lda < n || !A || !X || !Y) return TSVD_ERR_INVALID_ARG;

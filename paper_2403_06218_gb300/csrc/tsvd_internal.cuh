@@ -26,6 +26,12 @@ struct tsvd_handle {
     int prof_class = -1;     // when >= 0, the class every ProfScope records (see ProfClass)
     std::vector<tsvd_prof_rec> recs;
     std::vector<cudaEvent_t> pool;
+    // Scratch of the FP64-accurate tensor-core products for the current call
+    // (carved from the caller's workspace by the entry point; null: the FP64
+    // products run on the FP64 pipe), and the status words its kernels report to.
+    void* oz_ws = nullptr;
+    size_t oz_bytes = 0;
+    int* oz_status = nullptr;
 };
 
 namespace tsvd {
@@ -231,6 +237,44 @@ template <typename TI, typename TC>
 cudaError_t gemm_tn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, const TI* X, int64_t ldx,
                     const TI* Z, int64_t ldz, TC* C, int64_t ldc, bool symmetric,
                     double* partial_ws, cudaStream_t st);
+
+// ---- FP64-accurate tensor-core products (k_oz.cu) -------------------------------
+// Worth running on the tensor cores rather than the FP64 pipe (M x N outputs, K deep).
+bool oz_worth(int64_t M, int64_t N, int64_t K);
+// Scratch of C = X^T Z (q rows; s x b outputs) and of Y = X M (q x s times s x b).
+size_t oz_tn_ws(int64_t q, int64_t s, int64_t b, bool symmetric);
+size_t oz_nn_ws(int64_t q, int64_t s, int64_t b);
+// Scratch that covers every product with q <= qmax, s <= smax, b <= bmax (and s, b swapped).
+size_t oz_ws_bound(int64_t qmax, int64_t smax, int64_t bmax);
+// C (s x b, ldc) = X^T Z, X (q x s, ldx), Z (q x b, ldz); symmetric: Z == X, C mirrored.
+int oz_gemm_tn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, const double* X, int64_t ldx, const double* Z,
+               int64_t ldz, double* C, int64_t ldc, bool symmetric, void* ws, size_t ws_bytes, int* status,
+               cudaStream_t st);
+// Y (q x b, ldy) = beta Y + alpha X M; upper: M upper triangular (entries below its
+// diagonal are not read).  Y may alias X.
+int oz_gemm_nn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, double alpha, const double* X, int64_t ldx,
+               const double* Mm, int64_t ldm, double beta, double* Y, int64_t ldy, bool upper, void* ws,
+               size_t ws_bytes, int* status, cudaStream_t st);
+
+// Makes the FP64 products of one call run on the tensor cores with `bytes` of
+// scratch at `ws` (restores the handle's previous setting on destruction).
+struct OzScope {
+    tsvd_handle* h;
+    void* prev_ws;
+    size_t prev_bytes;
+    int* prev_status;
+    OzScope(tsvd_handle* hh, void* ws, size_t bytes, int* status)
+        : h(hh), prev_ws(hh->oz_ws), prev_bytes(hh->oz_bytes), prev_status(hh->oz_status) {
+        h->oz_ws = ws;
+        h->oz_bytes = bytes;
+        h->oz_status = status;
+    }
+    ~OzScope() {
+        h->oz_ws = prev_ws;
+        h->oz_bytes = prev_bytes;
+        h->oz_status = prev_status;
+    }
+};
 
 // Y (q x b, ldy) = beta Y + alpha X M; X (q x s, ldx), M (s x b, ldm).
 // upper: M is upper triangular (entries below the diagonal are not read).

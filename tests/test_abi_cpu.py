@@ -21,6 +21,7 @@ def test_header_declares_the_boundary():
     for must in ("tsvd_rsvd", "tsvd_blanczos", "tsvd_create", "tsvd_destroy", "tsvd_workspace_size",
                  "tsvd_spmm", "tsvd_csr_transpose", "tsvd_cholqr2", "tsvd_cgs_cqr2", "tsvd_cgs_qr",
                  "tsvd_small_svd", "tsvd_gaussian_block", "tsvd_dense_mm", "tsvd_dense_mm_f32",
+                 "tsvd_dense_mm_f64tc", "tsvd_dense_mm_f64tc_workspace",
                  "tsvd_spmm_workspace", "tsvd_bf16x3_split", "tsvd_mm_bf16x6", "tsvd_svd_backward",
                  "tsvd_svd_backward_workspace"):
         assert must in names
