@@ -381,6 +381,16 @@ def run_case(case):
                           "forward_cycles": res.info["iterations"], "cg_iters": [info["cg_iters_u"], info["cg_iters_v"]],
                           "cg_resid": info["cg_resid_u"]}))
         return 0
+    elif case in ("ozt", "ozn"):
+        # FP64-accurate sliced tensor-core products at the shapes of the benchmark solve's
+        # CGS-CQR2 (q = 100,000, s = 576, b = 64): the projection P^T Q and the update P H
+        P = torch.randn(100_000, 576, dtype=torch.float64, device="cuda", generator=g)
+        if case == "ozt":
+            Q = torch.randn(100_000, 64, dtype=torch.float64, device="cuda", generator=g)
+            call = lambda: tsvd.dense_mm(P, Q, trans=True, tensor_cores=True)  # noqa: E731
+        else:
+            H = torch.randn(576, 64, dtype=torch.float64, device="cuda", generator=g)
+            call = lambda: tsvd.dense_mm(P, H, tensor_cores=True)  # noqa: E731
     elif case in ("tc", "f32", "f64"):
         # dense A Q of the 20,000 x 20,000 workload with a 128-column block: split-BF16 tensor
         # cores (tc), FP32 CUDA cores (f32) or FP64 (f64)
@@ -411,6 +421,10 @@ def run_case(case):
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
     info = {"sweeps": out[3]} if case == "svd" else {}
+    if case in ("ozt", "ozn"):
+        best = min(times) * 1e-3
+        flops = 2.0 * 100_000 * 576 * 64
+        info = {"fp64_equiv_tflops": flops / best / 1e12, "bf16_tflops_issued": 28 * flops / best / 1e12}
     if case in ("tc", "f32", "f64"):
         best = min(times) * 1e-3
         info = {"tflops": 2.0 * 20_000 * 20_000 * 128 / best / 1e12,
@@ -428,7 +442,8 @@ def main(argv=None):
     ap.add_argument("--workload", default="sparse100k-lanczos-thick", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clock-ms", type=int, default=200, help="nvidia-smi sampling interval in the timed region")
-    ap.add_argument("--case", default=None, choices=("orth", "svd", "tc", "f32", "f64", "backward", "spmm"),
+    ap.add_argument("--case", default=None,
+                    choices=("orth", "svd", "tc", "f32", "f64", "backward", "spmm", "ozt", "ozn"),
                     help="run one building block at its benchmark shape (for profiler captures) and exit")
     args = ap.parse_args(argv)
     cfg = WORKLOADS[args.workload]

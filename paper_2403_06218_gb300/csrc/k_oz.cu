@@ -35,9 +35,9 @@
 //         B = M of X M: one exponent per source column, from a column-max pass
 //         with atomicMax, then a tiled transpose).
 // The product kernel (one CTA per SM, 320 threads) is the TMA / tcgen05
-// pipeline of the split-BF16 product: warp 0 loads 3-D boxes (32 K x rows x 7
-// planes, 64-byte swizzle) of both operands into a 2-stage ring, warp 1 owns 512
-// TMEM columns and issues the 56 MMAs of each stage from one thread, warps 2-9
+// pipeline of the split-BF16 product: warp 0 loads 3-D boxes (16 K x rows x 7
+// planes, 32-byte swizzle) of both operands into a 5-stage ring, warp 1 owns 512
+// TMEM columns and issues the 28 MMAs of each stage from one thread, warps 2-9
 // drain the accumulators (two warps per 32 TMEM lanes, 32 columns each).  Work units (output tile, 32-wide K block) are split
 // over one wave of CTAs: whole tiles per CTA when there are more tiles than
 // CTAs (the epilogue writes the output itself), an even split of the K blocks
@@ -59,14 +59,14 @@ using namespace tcx;
 constexpr int kOzDig = 7;                                   // digits per operand entry
 constexpr int kOzM = 128;                                   // output rows per tile (TMEM lanes)
 constexpr int kOzN = 64;                                    // output columns per tile
-constexpr int kOzBK = 32;                                   // K per stage (one 64-byte row)
+constexpr int kOzBK = 16;                                   // K per stage (one 32-byte row, one MMA)
 constexpr int kOzRowB = 2 * kOzBK;
-constexpr int kOzStages = 2;
-constexpr int kOzPlaneA = kOzM * kOzRowB;                   // 8 KB
-constexpr int kOzPlaneB = kOzN * kOzRowB;                   // 4 KB
-constexpr int kOzStageBytes = kOzDig * (kOzPlaneA + kOzPlaneB);  // 84 KB
+constexpr int kOzStages = 5;
+constexpr int kOzPlaneA = kOzM * kOzRowB;                   // 4 KB
+constexpr int kOzPlaneB = kOzN * kOzRowB;                   // 2 KB
+constexpr int kOzStageBytes = kOzDig * (kOzPlaneA + kOzPlaneB);  // 42 KB
 constexpr int kOzSmem = kOzStages * kOzStageBytes + 1024;
-constexpr int kOzChunk = 4;          // K blocks per exact accumulation (128 k)
+constexpr int kOzChunk = 8;          // K blocks per exact accumulation (128 k)
 constexpr int kOzFlushChunks = 64;   // chunks between FP64 flushes of the integer sums (8192 k)
 constexpr int kOzSlots = 7;          // accumulators: p+q = 6, 5, 4, 3, 2, 1, 0
 constexpr int kOzEpiWarps = 8;   // two per TMEM lane quarter, 32 columns each
@@ -75,12 +75,6 @@ constexpr int kOzWave = 152;
 constexpr int kOzTmemCols = 512;
 constexpr int kOzNanExp = 1 << 20;      // exponent of a row holding Inf or NaN
 constexpr int kOzZeroExp = -(1 << 20);  // exponent of a zero entry
-
-// Digit pairs (p, q) in issue order, grouped by accumulator slot: slot s holds
-// the pairs with p + q = 6 - s.
-__constant__ int8_t c_pair_p[28] = {0, 1, 2, 3, 4, 5, 6, 0, 1, 2, 3, 4, 5, 0, 1, 2, 3, 4, 0, 1, 2, 3, 0, 1, 2, 0, 1, 0};
-__constant__ int8_t c_pair_q[28] = {6, 5, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0, 4, 3, 2, 1, 0, 3, 2, 1, 0, 2, 1, 0, 1, 0, 0};
-__constant__ int8_t c_slot_end[kOzSlots] = {7, 13, 18, 22, 25, 27, 28};
 
 // ---- digits ------------------------------------------------------------------
 __device__ inline int oz_exp(double x) {
@@ -321,7 +315,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         if (lane == 0) {
             // ---- MMA issuer
             const uint32_t idesc = idesc_bf16(kOzM, a.Npad);
-            const uint32_t planeB = (uint32_t)(a.Npad * kOzRowB);
+            const uint32_t bstep = (uint32_t)(a.Npad * kOzRowB) >> 4;  // one B plane in 16-byte units
             int64_t it = 0, ch = 0;  // K blocks and chunks issued by this CTA
             bool ok = true;
             for (int64_t i = lo; i < hi && ok;) {
@@ -336,9 +330,12 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                         fence_after();
                         const bool first_kb = (i == i0), last_kb = (i + 1 == ce);
                         const uint32_t sA = base + (uint32_t)st * kOzStageBytes;
-                        const uint32_t sB = sA + kOzDig * kOzPlaneA;
-                        int pr = 0;
-                        for (int g = 0; g < kOzSlots && ok; ++g) {
+                        const uint64_t a0 = sdesc_sw32(sA);
+                        const uint64_t b0 = sdesc_sw32(sA + kOzDig * kOzPlaneA);
+                        // slot g accumulates the pairs (p, d - p), d = 6 - g; descriptor start
+                        // addresses advance by whole planes (16-byte units in the low field)
+#pragma unroll
+                        for (int g = 0; g < kOzSlots; ++g) {
                             if (first_kb && ch > 0) {
                                 // the epilogue has drained this accumulator of the previous chunk
                                 ok = mbar_wait(acce(g), (uint32_t)((ch - 1) & 1), abort_flag);
@@ -346,13 +343,11 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                                 fence_after();
                             }
                             const uint32_t d = tmem + (uint32_t)(g * kOzN);
-                            const int pe = c_slot_end[g];
-                            for (; pr < pe; ++pr) {
-                                const uint32_t pA = sA + (uint32_t)c_pair_p[pr] * kOzPlaneA;
-                                const uint32_t pB = sB + (uint32_t)c_pair_q[pr] * planeB;
-                                const bool fresh = first_kb && (pr == (g == 0 ? 0 : c_slot_end[g - 1]));
-                                mma_bf16(d, sdesc_sw64(pA), sdesc_sw64(pB), idesc, fresh ? 0u : 1u);
-                                mma_bf16(d, sdesc_sw64(pA + 32), sdesc_sw64(pB + 32), idesc, 1u);
+#pragma unroll
+                            for (int p = 0; p <= 6 - g; ++p) {
+                                const uint64_t ad = a0 + (uint64_t)(p * (kOzPlaneA >> 4));
+                                const uint64_t bd = b0 + (uint64_t)((6 - g - p) * bstep);
+                                mma_bf16(d, ad, bd, idesc, (first_kb && p == 0) ? 0u : 1u);
                             }
                             if (last_kb) commit(accf(g));
                         }
@@ -400,7 +395,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                 const int64_t ce = min(e, i + kOzChunk);
                 for (int g = 0; g < kOzSlots; ++g) {
                     int w_ok = 1;
-                    if (lane == 0) w_ok = mbar_wait(accf(g), (uint32_t)(ch & 1), abort_flag) ? 1 : 0;
+                    if (lane == 0) w_ok = mbar_wait_sleep(accf(g), (uint32_t)(ch & 1), abort_flag) ? 1 : 0;
                     w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
                     if (!w_ok) {
                         if (lane == 0) {
@@ -603,8 +598,8 @@ int oz_run(tsvd_handle* h, const OzPlan& p, const OzBufs& b, double* out, int64_
         configured = h->device;
     }
     CUtensorMap mA, mB;
-    if (!make_plane_map(&mA, b.pa, p.K, p.M, oz_ld(p.K), kOzM, kOzDig)) return TSVD_ERR_CUDA;
-    if (!make_plane_map(&mB, b.pb, p.K, p.N, oz_ld(p.K), p.Npad, kOzDig)) return TSVD_ERR_CUDA;
+    if (!make_plane_map(&mA, b.pa, p.K, p.M, oz_ld(p.K), kOzM, kOzDig, kOzBK)) return TSVD_ERR_CUDA;
+    if (!make_plane_map(&mB, b.pb, p.K, p.N, oz_ld(p.K), p.Npad, kOzDig, kOzBK)) return TSVD_ERR_CUDA;
     OzArgs a{};
     a.M = p.M;
     a.N = p.N;

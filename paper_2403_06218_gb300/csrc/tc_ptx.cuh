@@ -48,6 +48,18 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* ab
     }
     return true;
 }
+// The same with a short sleep between polls, for roles whose waits are long
+// (frees issue slots for the warps that share the SM sub-partition).
+__device__ inline bool mbar_wait_sleep(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                       long long max_wait = kMaxWait) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > max_wait) return false;
+        __nanosleep(64);
+    }
+    return true;
+}
 // Bounded wait that ignores the abort flag (draining copies or products in flight).
 __device__ inline void mbar_drain(uint32_t bar, uint32_t parity, long long max_wait = kMaxWait) {
     const long long t0 = clock64();
@@ -74,6 +86,16 @@ __device__ inline uint64_t sdesc_sw64(uint32_t addr) {
            | ((uint64_t)(512 >> 4) << 32)     // stride byte offset: 8 rows x 64 B
            | ((uint64_t)1 << 46)              // descriptor version of tcgen05
            | ((uint64_t)4 << 61);             // swizzle mode: 64 B
+}
+
+// The same for rows of 32 bytes (16 BF16) with 32-byte swizzle: 8-row groups 256
+// bytes apart (tile base 256-byte aligned); one K = 16 MMA covers a whole row.
+__device__ inline uint64_t sdesc_sw32(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu)  // start address / 16
+           | ((uint64_t)1 << 16)              // leading byte offset (unused for swizzled K-major)
+           | ((uint64_t)(256 >> 4) << 32)     // stride byte offset: 8 rows x 32 B
+           | ((uint64_t)1 << 46)              // descriptor version of tcgen05
+           | ((uint64_t)6 << 61);             // swizzle mode: 32 B
 }
 
 // Instruction descriptor of kind::f16: FP32 D, BF16 A and B, both K-major, M x N.
@@ -127,10 +149,11 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t
 EncodeTiledFn encode_fn();
 
 // 3-D map over `planes` BF16 matrices stored [planes][rows][ld] (ld in elements,
-// a multiple of 8), K extent `cols`; box 32 (K) x box_rows x planes, 64-byte
-// swizzle.  Loads beyond `cols` or `rows` read zeros.
+// a multiple of 8), K extent `cols`; box box_k (K) x box_rows x planes with a
+// swizzle of 2 box_k bytes (box_k = 32: 64-byte swizzle, 16: 32-byte swizzle).
+// Loads beyond `cols` or `rows` read zeros.
 bool make_plane_map(CUtensorMap* map, const void* base, int64_t cols, int64_t rows, int64_t ld, int box_rows,
-                    int planes);
+                    int planes, int box_k = 32);
 
 }  // namespace tcx
 }  // namespace tsvd
