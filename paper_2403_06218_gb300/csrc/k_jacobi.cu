@@ -16,6 +16,8 @@
 // rotates nothing (or kMaxSweeps).  Then sigma_j = |g_j|, columns are sorted by
 // (sigma descending, index ascending), Ubar_j = g_j / sigma_j, Vbar_j = v_j, and
 // each pair is sign-flipped so the largest-magnitude entry of Vbar_j is positive.
+#include <algorithm>
+
 #include "tsvd_internal.cuh"
 
 namespace tsvd {
@@ -209,68 +211,100 @@ __global__ void jacobi_sweep_kernel(int n, int npad, double* __restrict__ G, dou
 // of npad - 1 and the rotations of a block pair stay on chip.
 constexpr int kJGroup = 4;  // warps per column pair (disjoint row ranges)
 
+// Rotation parameters of one column pair from alpha = |g_p|^2, beta = |g_q|^2 and
+// gamma = g_p.g_q (Rutishauser's formulas); false when |gamma| <= tol sqrt(alpha beta).
+// FP64: zeta = (beta - alpha) / (2 gamma) with the difference in FP64 (it may cancel),
+// the ratio and t in FP32 (relative accuracy 1e-7 keeps the convergence quadratic),
+// c = 1/sqrt(1 + t^2) and s = c t in FP64 so that c^2 + s^2 = 1 to FP64 rounding and
+// the rotation stays orthogonal.  FP32 (the preconditioning sweeps): all in FP32.
+__device__ inline bool rot_params(double al, double be, double ga, double tol2, double& c, double& sn, double& t) {
+    const double big = fmax(al, be);
+    if (!(ga != 0.0 && big > 0.0)) return false;
+    // scale by a power of two so the test and the FP32 ratio cannot over/underflow
+    const int e = ilogb(big);
+    const double as = scalbn(al, -e), bs = scalbn(be, -e), gs = scalbn(ga, -e);
+    if (!(gs * gs > tol2 * as * bs)) return false;
+    const float zf = (float)(bs - as) / (2.0f * (float)gs);
+    const float az = fabsf(zf);
+    const float tf = az > 1e18f ? 0.5f / zf : copysignf(1.0f, zf) / (az + sqrtf(fmaf(az, az, 1.0f)));
+    t = (double)tf;
+    c = rsqrt(fma(t, t, 1.0));
+    sn = c * t;
+    return true;
+}
+__device__ inline bool rot_params(float al, float be, float ga, float tol2, float& c, float& sn, float& t) {
+    const float big = fmaxf(al, be);
+    if (!(ga != 0.0f && big > 0.0f)) return false;
+    const int e = ilogbf(big);
+    const float as = scalbnf(al, -e), bs = scalbnf(be, -e), gs = scalbnf(ga, -e);
+    if (!(gs * gs > tol2 * as * bs)) return false;
+    const float zf = (bs - as) / (2.0f * gs);
+    const float az = fabsf(zf);
+    t = az > 1e18f ? 0.5f / zf : copysignf(1.0f, zf) / (az + sqrtf(fmaf(az, az, 1.0f)));
+    c = rsqrtf(fmaf(t, t, 1.0f));
+    sn = c * t;
+    return true;
+}
+
+template <typename T>
+__device__ inline T warp_sum_t(T v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+    return v;
+}
+
 // Rotations of npair_local disjoint column pairs held in shared memory.  Each pair
 // is served by kJGroup warps over interleaved rows, so every SMSP holds several
-// warps to hide the FP64 latency; the group's partial dot products are summed in
-// a fixed order (bitwise reproducible).
-__device__ inline void block_pair_rotations(double* cols, double* snrm, int n, int npair_local, const int* pp,
-                                            const int* pq, double tol2, double (*s_part)[kJGroup], double* s_c,
-                                            double* s_s, int* s_rot, int* s_any) {
+// warps to hide the arithmetic latency; the group's partial dot products are
+// summed in a fixed order (bitwise reproducible).
+template <typename T>
+__device__ inline void block_pair_rotations(T* cols, T* snrm, int n, int npair_local, const int* pp, const int* pq,
+                                            T tol2, T (*s_part)[kJGroup], T* s_c, T* s_s, int* s_rot, int* s_any) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     const int stride = 32 * kJGroup;
     for (int slot = warp; slot < npair_local * kJGroup; slot += nw) {  // (A) partial gamma
         const int k = slot / kJGroup, sub = slot % kJGroup;
-        const double* gp = cols + (size_t)pp[k] * n;
-        const double* gq = cols + (size_t)pq[k] * n;
-        double g0 = 0.0, g1 = 0.0;
+        const T* gp = cols + (size_t)pp[k] * n;
+        const T* gq = cols + (size_t)pq[k] * n;
+        T g0 = T(0), g1 = T(0);
         int r = sub * 32 + lane;
         for (; r + stride < n; r += 2 * stride) {
             g0 = fma(gp[r], gq[r], g0);
             g1 = fma(gp[r + stride], gq[r + stride], g1);
         }
         if (r < n) g0 = fma(gp[r], gq[r], g0);
-        const double ga = warp_sum(g0 + g1);
+        const T ga = warp_sum_t<T>(g0 + g1);
         if (lane == 0) s_part[k][sub] = ga;
     }
     __syncthreads();
     if (warp == 0) {  // (B) rotation parameters, one lane per pair
         for (int k = lane; k < npair_local; k += 32) {
-            double ga = 0.0;
+            T ga = T(0);
 #pragma unroll
             for (int t = 0; t < kJGroup; ++t) ga += s_part[k][t];
-            const double al = snrm[pp[k]], be = snrm[pq[k]];
-            int rot = 0;
-            const double big = fmax(al, be);
-            if (ga != 0.0 && big > 0.0) {
-                const int e = ilogb(big);
-                const double as = scalbn(al, -e), bs = scalbn(be, -e), gs = scalbn(ga, -e);
-                if (gs * gs > tol2 * as * bs) {
-                    const float zf = (float)(bs - as) / (2.0f * (float)gs);
-                    const float az = fabsf(zf);
-                    const float tf = az > 1e18f ? 0.5f / zf : copysignf(1.0f, zf) / (az + sqrtf(fmaf(az, az, 1.0f)));
-                    const double t = (double)tf;
-                    const double c = rsqrt(fma(t, t, 1.0));
-                    s_c[k] = c;
-                    s_s[k] = c * t;
-                    snrm[pp[k]] = fma(-t, ga, al);
-                    snrm[pq[k]] = fma(t, ga, be);
-                    rot = 1;
-                    *s_any = 1;
-                }
+            const T al = snrm[pp[k]], be = snrm[pq[k]];
+            T c, sn, t;
+            const bool rot = rot_params(al, be, ga, tol2, c, sn, t);
+            if (rot) {
+                s_c[k] = c;
+                s_s[k] = sn;
+                snrm[pp[k]] = fma(-t, ga, al);
+                snrm[pq[k]] = fma(t, ga, be);
+                *s_any = 1;
             }
-            s_rot[k] = rot;
+            s_rot[k] = rot ? 1 : 0;
         }
     }
     __syncthreads();
     for (int slot = warp; slot < npair_local * kJGroup; slot += nw) {  // (C) rotate
         const int k = slot / kJGroup, sub = slot % kJGroup;
         if (!s_rot[k]) continue;
-        const double c = s_c[k], sn = s_s[k];
-        double* gp = cols + (size_t)pp[k] * n;
-        double* gq = cols + (size_t)pq[k] * n;
+        const T c = s_c[k], sn = s_s[k];
+        T* gp = cols + (size_t)pp[k] * n;
+        T* gq = cols + (size_t)pq[k] * n;
         for (int r = sub * 32 + lane; r < n; r += stride) {
-            const double x = gp[r], y = gq[r];
+            const T x = gp[r], y = gq[r];
             gp[r] = fma(c, x, -sn * y);
             gq[r] = fma(sn, x, c * y);
         }
@@ -280,23 +314,24 @@ __device__ inline void block_pair_rotations(double* cols, double* snrm, int n, i
 
 constexpr int kJBlkMaxW = 8;
 
-__global__ void jacobi_block_kernel(int n, int npad, int w, double* __restrict__ G, double* __restrict__ nrm,
-                                    unsigned* ctl, double tol) {
-    extern __shared__ double jsm[];
-    double* cols = jsm;                         // 2w columns of n
-    double* snrm = jsm + (size_t)2 * w * n;     // their squared norms
-    __shared__ double s_part[kJBlkMaxW][kJGroup], s_c[kJBlkMaxW], s_s[kJBlkMaxW];
+template <typename T>
+__global__ void jacobi_block_kernel(int n, int npad, int w, T* __restrict__ G, T* __restrict__ nrm, unsigned* ctl,
+                                    T tol) {
+    extern __shared__ __align__(16) unsigned char jsm_raw[];
+    T* cols = reinterpret_cast<T*>(jsm_raw);  // 2w columns of n
+    T* snrm = cols + (size_t)2 * w * n;       // their squared norms
+    __shared__ T s_part[kJBlkMaxW][kJGroup], s_c[kJBlkMaxW], s_s[kJBlkMaxW];
     __shared__ int s_rot[kJBlkMaxW], s_pp[kJBlkMaxW], s_pq[kJBlkMaxW];
     __shared__ int s_any;
-    const double tol2 = tol * tol;
+    const T tol2 = tol * tol;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nblk = npad / w;
     for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
         for (int c = blockIdx.x * nw + warp; c < npad; c += gridDim.x * nw) {  // exact norms
-            const double* g = G + (int64_t)c * n;
-            double acc = 0.0;
+            const T* g = G + (int64_t)c * n;
+            T acc = T(0);
             for (int r = lane; r < n; r += 32) acc = fma(g[r], g[r], acc);
-            acc = warp_sum(acc);
+            acc = warp_sum_t<T>(acc);
             if (lane == 0) nrm[c] = acc;
         }
         if (threadIdx.x == 0) s_any = 0;
@@ -322,7 +357,7 @@ __global__ void jacobi_block_kernel(int n, int npad, int w, double* __restrict__
                         s_pq[k] = blk * w + max(a, b2);
                     }
                     __syncthreads();
-                    block_pair_rotations(cols, snrm, n, w, s_pp, s_pq, tol2, s_part, s_c, s_s, s_rot, &s_any);
+                    block_pair_rotations<T>(cols, snrm, n, w, s_pp, s_pq, tol2, s_part, s_c, s_s, s_rot, &s_any);
                 }
             }
             for (int mr = 0; mr < w; ++mr) {  // rotations between I and J
@@ -331,7 +366,7 @@ __global__ void jacobi_block_kernel(int n, int npad, int w, double* __restrict__
                     s_pq[threadIdx.x] = w + (threadIdx.x + mr) % w;
                 }
                 __syncthreads();
-                block_pair_rotations(cols, snrm, n, w, s_pp, s_pq, tol2, s_part, s_c, s_s, s_rot, &s_any);
+                block_pair_rotations<T>(cols, snrm, n, w, s_pp, s_pq, tol2, s_part, s_c, s_s, s_rot, &s_any);
             }
             for (int idx = threadIdx.x; idx < 2 * w * n; idx += blockDim.x) {
                 const int lc = idx / n, r = idx % n;
@@ -350,6 +385,55 @@ __global__ void jacobi_block_kernel(int n, int npad, int w, double* __restrict__
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl[kCtlSweeps] = (unsigned)kMaxSweeps;
+}
+
+// FP32 copy of B^T in the Jacobi layout: column c of G32 (ld n) = row c of B,
+// padded columns zero.
+__global__ void jacobi_init_t32_kernel(int n, int npad, const double* __restrict__ B, int64_t ldb,
+                                       float* __restrict__ G) {
+    const int64_t tot = (int64_t)npad * n;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(idx / n), r = (int)(idx % n);
+        G[idx] = c < n ? (float)B[(int64_t)c * ldb + r] : 0.0f;
+    }
+}
+
+// V (n x n row-major, FP64): V[:, j] = G32[:, j] / |G32[:, j]| for j < n; a zero
+// column leaves e_j.  Also hands a timeout of the FP32 sweeps to the status words.
+__global__ void __launch_bounds__(128) jacobi_vinit_kernel(int n, const float* __restrict__ G, double* __restrict__ V,
+                                                           const unsigned* ctl32, int* status) {
+    __shared__ double red[4];
+    const int j = blockIdx.x;
+    const float* g = G + (int64_t)j * n;
+    double acc = 0.0;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) acc = fma((double)g[r], (double)g[r], acc);
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    const double nr = sqrt(red[0] + red[1] + red[2] + red[3]);
+    const double inv = nr > 0.0 ? 1.0 / nr : 0.0;
+    for (int r = threadIdx.x; r < n; r += blockDim.x)
+        V[(int64_t)r * n + j] = nr > 0.0 ? (double)g[r] * inv : (r == j ? 1.0 : 0.0);
+    if (j == 0 && threadIdx.x == 0 && ctl32[kCtlErr]) atomicOr(&status[kStTimeout], 1);
+}
+
+// After the polar iterations: if V^T V (in T) is not the identity to 1e-12, V = I
+// (the FP64 sweeps then start from B itself).  One CTA.
+__global__ void __launch_bounds__(1024) jacobi_vcheck_kernel(int n, const double* __restrict__ Tm,
+                                                             double* __restrict__ V) {
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int64_t idx = threadIdx.x; idx < (int64_t)n * n; idx += blockDim.x) {
+        const int i = (int)(idx / n), j = (int)(idx % n);
+        const double d = Tm[idx] - (i == j ? 1.0 : 0.0);
+        if (!(fabs(d) <= 1e-12)) bad = 1;
+    }
+    __syncthreads();
+    if (!bad) return;
+    for (int64_t idx = threadIdx.x; idx < (int64_t)n * n; idx += blockDim.x)
+        V[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
 }
 
 // One CTA (1024 threads): column norms, then a bitonic sort of (sigma desc, index asc).
@@ -500,27 +584,76 @@ __global__ void __launch_bounds__(128) jacobi_vfix_kernel(int n, const double* _
 
 }  // namespace
 
-size_t small_svd_ws(int n) {
-    const int npad = n + 2 * kJBlkMaxW;
-    Arena ar;
-    ar.take<double>((size_t)n * npad);
-    ar.take<double>((size_t)npad * npad);
-    ar.take<double>(npad);
-    ar.take<double>(npad);
-    ar.take<int>(npad);
-    ar.take<unsigned>(kCtlWords);
-    size_t part = 0;
-    for (int nv = 1; nv <= n; ++nv) {
-        const size_t v = gemm_tn_ws(nullptr, n, n, nv, false);
-        if (v > part) part = v;
+// Block width of the FP64 block-Jacobi kernel for an order-n SVD without V (at most
+// one wave of 152 CTAs, each owning a pair of blocks), or 0 when the per-pair kernel
+// is used (small n, or V accumulated).
+static int block_width(int n) {
+    if (n <= 64 || n > 1024) return 0;
+    int w = 1;
+    while (w < kJBlkMaxW && (n + 2 * w - 1) / (2 * w) > 152) w *= 2;
+    return w;
+}
+// Block width of the FP32 preconditioning sweeps: the widest blocks (fewest rounds).
+constexpr int kJW32 = kJBlkMaxW;
+
+static int pad_to(int n, int w) { return (n + 2 * w - 1) / (2 * w) * (2 * w); }
+
+template <typename T>
+static size_t block_smem(int n, int w) {
+    return sizeof(T) * ((size_t)2 * w * n + 2 * w);
+}
+
+// Buffers of one small SVD, carved identically by the sizing and the run.
+struct SvdBufs {
+    double *G, *V, *nrm, *sig, *part;
+    int* perm;
+    unsigned *ctl, *ctl32;
+    float *G32, *nrm32;
+    double *Vp, *Tm, *Y;  // preconditioner: V, V^T V, B V (n x n row-major)
+    void* oz;
+    size_t oz_bytes;
+};
+
+static SvdBufs carve_svd(Arena& ar, int n, int npad, int nv, bool precond) {
+    SvdBufs b{};
+    b.G = ar.take<double>((size_t)n * npad);
+    b.V = ar.take<double>((size_t)npad * npad);
+    b.nrm = ar.take<double>(npad);
+    b.sig = ar.take<double>(npad);
+    b.perm = ar.take<int>(npad);
+    b.ctl = ar.take<unsigned>(kCtlWords);
+    b.part = ar.take<double>(gemm_tn_ws(nullptr, n, n, nv > 0 ? nv : 1, false) / sizeof(double) + 1);
+    if (precond) {
+        const int np32 = pad_to(n, kJW32);
+        b.ctl32 = ar.take<unsigned>(kCtlWords);
+        b.G32 = ar.take<float>((size_t)n * np32);
+        b.nrm32 = ar.take<float>(np32);
+        b.Vp = ar.take<double>((size_t)n * n);
+        b.Tm = ar.take<double>((size_t)n * n);
+        b.Y = ar.take<double>((size_t)n * n);
+        b.oz_bytes = std::max(oz_tn_ws(n, n, n, true), oz_nn_ws(n, n, n));
+        b.oz = ar.take<char>(b.oz_bytes);
     }
-    ar.take<char>(part + sizeof(double));
-    // re-orthonormalisation of the computed right vectors (block CGS-QR, blocks of 128)
-    const int bw = n < TSVD_MAX_BLOCK ? n : TSVD_MAX_BLOCK;
-    ar.take<double>((size_t)n * n);
-    ar.take<double>((size_t)(n - bw) * bw);
-    ar.take<char>(orth_ws(nullptr, n, n - bw, bw));
-    return ar.off;
+    return b;
+}
+
+size_t small_svd_ws(int n) {
+    size_t best = 0;
+    for (int nv : {n, n - 1}) {
+        if (nv < 0) continue;
+        const bool acc = nv == n;
+        const int w = acc ? 0 : block_width(n);
+        const int npad = w ? pad_to(n, w) : n + (n & 1);
+        Arena ar;
+        carve_svd(ar, n, npad, n, w > 0);
+        // re-orthonormalisation of the computed right vectors (block CGS-QR, blocks of 128)
+        const int bw = n < TSVD_MAX_BLOCK ? n : TSVD_MAX_BLOCK;
+        ar.take<double>((size_t)n * n);
+        ar.take<double>((size_t)(n - bw) * bw);
+        ar.take<char>(orth_ws(nullptr, n, n - bw, bw));
+        best = std::max(best, ar.off);
+    }
+    return best;
 }
 
 static int jacobi_grid(const tsvd_handle* h, int npairs, int& block) {
@@ -537,16 +670,32 @@ static int jacobi_grid(const tsvd_handle* h, int npairs, int& block) {
     return nb;
 }
 
-// Block width of the block-Jacobi kernel for an order-n SVD without V, or 0 when
-// the per-pair kernel is used (small n, or V accumulated).
-static int block_width(int n) {
-    if (n <= 64 || n > 1024) return 0;
-    int w = 1;
-    while (w < kJBlkMaxW && (n + 2 * w - 1) / (2 * w) * 2 > 256) w *= 2;  // at most 256 blocks -> 128 CTAs
-    return w;
+// Cooperative launch of the block-Jacobi sweeps on G (n x npad, column-major) in T.
+template <typename T>
+static int run_block_sweeps(tsvd_handle* h, int n, int npad, int w, T* G, T* nrm, unsigned* ctl, T tol,
+                            cudaStream_t st) {
+    const int nb = npad / w / 2;
+    const size_t smem = block_smem<T>(n, w);
+    static thread_local int configured = -1;
+    if (configured != h->device) {
+        TSVD_TRY_CUDA(cudaFuncSetAttribute(jacobi_block_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)block_smem<double>(1024, kJBlkMaxW)));
+        TSVD_TRY_CUDA(cudaFuncSetAttribute(jacobi_block_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)block_smem<float>(1024, kJBlkMaxW)));
+        configured = h->device;
+    }
+    int per_sm = 0;
+    TSVD_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_block_kernel<T>, 32 * w * kJGroup,
+                                                                smem));
+    if (per_sm * h->sm_count < nb) return TSVD_ERR_UNSUPPORTED;
+    int nn = n, np = npad, ww = w;
+    T t = tol;
+    void* args[] = {(void*)&nn, (void*)&np, (void*)&ww, (void*)&G, (void*)&nrm, (void*)&ctl, (void*)&t};
+    h->launches++;
+    TSVD_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_block_kernel<T>, dim3(nb), dim3(32 * w * kJGroup),
+                                              args, smem, st));
+    return TSVD_OK;
 }
-
-static size_t block_smem(int n, int w) { return sizeof(double) * ((size_t)2 * w * n + 2 * w); }
 
 int small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* Ubar, double* sigma, double* Vbar, int nv,
               Arena& ar, int* status, cudaStream_t st) {
@@ -554,69 +703,83 @@ int small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* Ubar,
     if (nv < 0 || nv > n) return TSVD_ERR_INVALID_ARG;
     const bool accumulate = (nv == n);
     const int w = accumulate ? 0 : block_width(n);
-    const int npad = w ? (n + 2 * w - 1) / (2 * w) * (2 * w) : n + (n & 1);
-    double* G = ar.take<double>((size_t)n * npad);
-    double* V = ar.take<double>((size_t)npad * npad);
-    double* nrm = ar.take<double>(npad);
-    double* sig = ar.take<double>(npad);
-    int* perm = ar.take<int>(npad);
-    unsigned* ctl = ar.take<unsigned>(kCtlWords);
-    double* part = ar.take<double>(gemm_tn_ws(h, n, n, nv > 0 ? nv : 1, false) / sizeof(double) + 1);
+    const int npad = w ? pad_to(n, w) : n + (n & 1);
+    const SvdBufs bf = carve_svd(ar, n, npad, nv, w > 0);
     if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+    double* G = bf.G;
+    double* V = bf.V;
     {  // the Jacobi sweeps (the right-vector products below are timed as products)
         ProfScope prof(h, TSVD_K_SVD, 0.0, 0.0, st);
-        TSVD_TRY_CUDA(cudaMemsetAsync(ctl, 0, sizeof(unsigned) * kCtlWords, st));
+        TSVD_TRY_CUDA(cudaMemsetAsync(bf.ctl, 0, sizeof(unsigned) * kCtlWords, st));
         const int64_t tot = (int64_t)npad * npad;
-        h->launches += 4;
-        jacobi_init_kernel<<<(unsigned)((tot + 255) / 256 < 4096 ? (tot + 255) / 256 : 4096), 256, 0, st>>>(
-            n, npad, B, ldb, G, V);
-        TSVD_TRY_CUDA(cudaGetLastError());
+        const unsigned ib = (unsigned)((tot + 255) / 256 < 4096 ? (tot + 255) / 256 : 4096);
         const double tol = (double)(n > 16 ? n : 16) * kEps;
         double* Vacc = accumulate ? V : nullptr;
         if (w > 0) {
-            const int nblk = npad / w;
-            const int nb = nblk / 2;
-            const size_t smem = block_smem(n, w);
-            static thread_local int configured = -1;
-            if (configured != h->device) {
-                TSVD_TRY_CUDA(cudaFuncSetAttribute(jacobi_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)block_smem(1024, kJBlkMaxW)));
-                configured = h->device;
+            // (1) FP32 block-Jacobi sweeps on B^T: its orthogonalised columns are the right
+            //     singular directions of B to FP32 accuracy
+            const int np32 = pad_to(n, kJW32);
+            TSVD_TRY_CUDA(cudaMemsetAsync(bf.ctl32, 0, sizeof(unsigned) * kCtlWords, st));
+            h->launches += 2;
+            jacobi_init_t32_kernel<<<(unsigned)std::min<int64_t>(4096, ((int64_t)n * np32 + 255) / 256), 256, 0, st>>>(
+                n, np32, B, ldb, bf.G32);
+            TSVD_TRY_CUDA(cudaGetLastError());
+            const float tol32 = (float)(n > 16 ? n : 16) * 5.9604645e-08f;  // n 2^-24
+            TSVD_TRY(run_block_sweeps<float>(h, n, np32, kJW32, bf.G32, bf.nrm32, bf.ctl32, tol32, st));
+            jacobi_vinit_kernel<<<n, 128, 0, st>>>(n, bf.G32, bf.Vp, bf.ctl32, status);
+            TSVD_TRY_CUDA(cudaGetLastError());
+            // (2) V orthogonal to FP64 rounding: two polar (Newton-Schulz) steps
+            //     V <- V (3 I - V^T V) / 2 with FP64-accurate tensor-core products, then a
+            //     check that falls back to V = I if V^T V is not the identity to 1e-12
+            for (int itn = 0; itn < 2; ++itn) {
+                TSVD_TRY(oz_gemm_tn(h, n, n, n, bf.Vp, n, bf.Vp, n, bf.Tm, n, true, bf.oz, bf.oz_bytes, status, st));
+                TSVD_TRY(oz_gemm_nn(h, n, n, n, -0.5, bf.Vp, n, bf.Tm, n, 1.5, bf.Vp, n, false, bf.oz, bf.oz_bytes,
+                                    status, st));
             }
-            int per_sm = 0;
-            TSVD_TRY_CUDA(
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_block_kernel, 32 * w * kJGroup, smem));
-            if (per_sm * h->sm_count < nb) return TSVD_ERR_UNSUPPORTED;
-            int nn = n, np = npad, ww = w;
-            double t = tol;
-            void* args[] = {(void*)&nn, (void*)&np, (void*)&ww, (void*)&G, (void*)&nrm, (void*)&ctl, (void*)&t};
-            TSVD_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_block_kernel, dim3(nb), dim3(32 * w * kJGroup),
-                                                      args, smem, st));
+            TSVD_TRY(oz_gemm_tn(h, n, n, n, bf.Vp, n, bf.Vp, n, bf.Tm, n, true, bf.oz, bf.oz_bytes, status, st));
+            h->launches++;
+            jacobi_vcheck_kernel<<<1, 1024, 0, st>>>(n, bf.Tm, bf.Vp);
+            TSVD_TRY_CUDA(cudaGetLastError());
+            // (3) FP64 sweeps on B V: the SVD of B V is that of B with the right vectors
+            //     rotated by V, and its columns start orthogonal to FP32 accuracy
+            TSVD_TRY(oz_gemm_nn(h, n, n, n, 1.0, B, ldb, bf.Vp, n, 0.0, bf.Y, n, false, bf.oz, bf.oz_bytes, status,
+                                st));
+            h->launches++;
+            jacobi_init_kernel<<<ib, 256, 0, st>>>(n, npad, bf.Y, n, G, V);
+            TSVD_TRY_CUDA(cudaGetLastError());
+            TSVD_TRY(run_block_sweeps<double>(h, n, npad, w, G, bf.nrm, bf.ctl, tol, st));
         } else {
+            h->launches++;
+            jacobi_init_kernel<<<ib, 256, 0, st>>>(n, npad, B, ldb, G, V);
+            TSVD_TRY_CUDA(cudaGetLastError());
             const int npairs = npad / 2;
             int block = 0;
             const int nblocks = jacobi_grid(h, npairs, block);
             if (nblocks < 1) return TSVD_ERR_UNSUPPORTED;
             const int ppb = (npairs + nblocks - 1) / nblocks;
+            h->launches++;
             if (nblocks == 1) {
-                jacobi_sweep_kernel<<<1, block, 0, st>>>(n, npad, G, Vacc, nrm, ctl, tol, ppb);
+                jacobi_sweep_kernel<<<1, block, 0, st>>>(n, npad, G, Vacc, bf.nrm, bf.ctl, tol, ppb);
                 TSVD_TRY_CUDA(cudaGetLastError());
             } else {
                 int nn = n, np = npad, pp = ppb;
                 double t = tol;
+                double* nrm = bf.nrm;
+                unsigned* ctl = bf.ctl;
                 void* args[] = {(void*)&nn, (void*)&np, (void*)&G, (void*)&Vacc, (void*)&nrm, (void*)&ctl, (void*)&t,
                                 (void*)&pp};
                 TSVD_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_sweep_kernel, dim3(nblocks), dim3(block),
                                                           args, 0, st));
             }
         }
-        jacobi_sort_kernel<<<1, 1024, 0, st>>>(n, npad, G, sig, perm, ctl, status);
-        jacobi_out_kernel<<<n, 128, 0, st>>>(n, npad, G, Vacc, sig, perm, Ubar, sigma, Vbar);
+        h->launches += 2;
+        jacobi_sort_kernel<<<1, 1024, 0, st>>>(n, npad, G, bf.sig, bf.perm, bf.ctl, status);
+        jacobi_out_kernel<<<n, 128, 0, st>>>(n, npad, G, Vacc, bf.sig, bf.perm, Ubar, sigma, Vbar);
         TSVD_TRY_CUDA(cudaGetLastError());
     }
     if (!accumulate && nv > 0) {
         // right vectors of the leading nv triplets: vbar_j = B^T ubar_j / sigma_j
-        TSVD_TRY_CUDA(gemm_tn(h, n, n, nv, B, ldb, Ubar, n, Vbar, n, false, part, st));
+        TSVD_TRY_CUDA(gemm_tn(h, n, n, nv, B, ldb, Ubar, n, Vbar, n, false, bf.part, st));
         h->launches++;
         jacobi_vfix_kernel<<<nv, 128, 0, st>>>(n, sigma, Ubar, Vbar);
         TSVD_TRY_CUDA(cudaGetLastError());

@@ -653,13 +653,14 @@ size_t oz_nn_ws(int64_t q, int64_t s, int64_t b) {
 }
 
 size_t oz_ws_bound(int64_t qmax, int64_t smax, int64_t bmax) {
-    size_t w = 0;
-    for (int64_t s : {smax, bmax})
-        for (int64_t b : {bmax, smax}) {
-            w = std::max(w, oz_tn_ws(qmax, s, b, false));
-            w = std::max(w, oz_nn_ws(qmax, s, b));
-        }
-    return w + 4096;
+    // planes and exponents of the largest operands of either product, and split-K
+    // partial tiles for at most (tiles + 2 per CTA of one wave) tiles
+    const size_t tn = oz_planes_bytes(smax, qmax) + oz_planes_bytes(bmax, qmax);
+    const size_t nn = oz_planes_bytes(qmax, smax) + oz_planes_bytes(bmax, smax);
+    const size_t ex = align256(sizeof(int) * (size_t)(qmax + smax)) + align256(sizeof(int) * (size_t)(smax + bmax));
+    const int64_t tiles = ((smax + kOzM - 1) / kOzM) * ((bmax + kOzN - 1) / kOzN);
+    const size_t part = align256(sizeof(double) * (size_t)(tiles + 2 * kOzWave) * kOzM * kOzN);
+    return std::max(tn, nn) + ex + part + 4096;
 }
 
 int oz_gemm_tn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, const double* X, int64_t ldx, const double* Z,

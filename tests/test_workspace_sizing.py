@@ -1,4 +1,5 @@
-"""Workspace sizing on CPU (host-only calls): the sizes cover the Lanczos bases,
+"""Workspace sizing on CPU (host-only calls): the sizes cover the Lanczos bases
+and the digit planes of the FP64 tensor-core products,
 grow linearly with the tall dimension, and stay in 64-bit arithmetic at sizes
 beyond 2^31 rows and 2^31 - 1 stored entries."""
 
@@ -29,7 +30,10 @@ def test_lanczos_workspace_holds_both_bases(tsvd, keep):
     r = 9 if keep else 16
     ws = _ws(lib, m, n, _capi.TSVD_CSR, 1_000_000, _capi.TSVD_METHOD_BLANCZOS, 64, 64, r, keep=keep)
     bases = 8 * (m + n) * r * 64                       # P (n x rb) and Pbar (m x rb), FP64
-    assert bases < ws < 2 * bases
+    # BF16 digit planes (7 x 2 bytes an entry) of the tensor-core products' largest
+    # operands: the q x rb basis prefix and a q x max(b, k, keep) block
+    planes = 14 * max(m, n) * (r * 64 + max(64, keep))
+    assert bases + planes < ws < 1.5 * (bases + planes)
 
 
 @pytest.mark.parametrize("method,a,c", [(_capi.TSVD_METHOD_BLANCZOS, 64, 4), (_capi.TSVD_METHOD_RSVD, 64, 2)])
