@@ -637,6 +637,7 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
     double* Vb = ar.take<double>((size_t)rb * rb);
     double* sig = ar.take<double>(rb);
     double* Rr = ar.take<double>((size_t)b * b);
+    double* Bsave = ar.take<double>((size_t)rb * rb);  // B at the start of a cycle (redo after a breakdown)
     double* rho = ar.take<double>(k);
     double* g64 = kMixed ? ar.take<double>((size_t)m * b) : nullptr;
     Final f;
@@ -674,43 +675,60 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
     double rho_last = NAN, resid = NAN;
     std::vector<double> hrho(k), hsig(1);
     int hs[kStCount];
-    // Every orthogonalisation is checked as it completes: near convergence the first
-    // S5 after a restart breaks down in most cycles (converged Ritz vectors deflate
-    // the new block), so its fallback must run at once.
+    // A cycle first runs deferred: its orthogonalisations are not synchronised, a
+    // Cholesky breakdown only sets the sticky status word, and the word is read once,
+    // with the Lanczos estimate, after the cycle.  If it is set, the cycle is redone
+    // from its saved start (the bases' leading columns and the start block are not
+    // written by the cycle; B is restored) with every orthogonalisation checked, so
+    // that the fallback runs where it is needed; later cycles then stay checked (with
+    // basic restart, the first S5 after a restart breaks down in most cycles near
+    // convergence: converged Ritz vectors deflate the new block).
     // s0 = Ritz pairs carried into the current cycle (thick restart), d = its dimension:
     // basis [P~ (s0), Q_1 .. Q_nblk], [Pbar~ (s0), Qbar_1 .. Qbar_nblk], B d x d with
     // diag(S_s0) and the coupling block G below it (see the thick-restart reading)
     int s0 = 0;
+    bool defer = true;
     for (;;) {
         const int nblk = s0 == 0 ? r : (rb - s0) / b;
         const int d = s0 + nblk * b;
         if (s0 == 0) TSVD_TRY_CUDA(cudaMemsetAsync(B, 0, sizeof(double) * (size_t)rb * rb, st));
-        for (int i = 0; i < nblk; ++i) {
-            const int c0 = s0 + i * b;
-            T* Qi = P + c0;
-            TSVD_TRY(op_tmul<T>(h, op, b, Pbar + c0, rb, Qi, rb, status, st));                    // S2
-            double* Lii = B + (int64_t)c0 * rb + c0;
-            const bool couple = (i == 0 && s0 > 0);
-            TSVD_TRY(cgs_cqr2<T>(h, n, c0, b, P, rb, Qi, rb, couple ? Hk : nullptr, Lii, rb, true, ctx, ar, status,
-                                 st));                                                                // S3
-            if (couple) TSVD_TRY_CUDA(put_transposed(h, s0, b, Hk, b, B + (int64_t)c0 * rb, rb, st));  // G
-            const bool last = (i + 1 == nblk);
-            T* dst = last ? Qnext : Pbar + c0 + b;
-            const int64_t ldd = last ? b : rb;
-            TSVD_TRY(op_mul<T>(h, op, b, Qi, rb, dst, ldd, status, st));                             // S4
-            double* Ri = last ? Rr : B + (int64_t)(c0 + b) * rb + c0;
-            TSVD_TRY(cgs_cqr2<T>(h, m, c0 + b, b, Pbar, rb, dst, ldd, nullptr, Ri, last ? b : rb, false, ctx, ar,
-                                 status, st));                                                       // S5
+        if (defer)
+            TSVD_TRY_CUDA(cudaMemcpyAsync(Bsave, B, sizeof(double) * (size_t)rb * rb, cudaMemcpyDeviceToDevice, st));
+        for (int pass = 0; pass < 2; ++pass) {
+            ctx.deferred = defer && pass == 0;
+            for (int i = 0; i < nblk; ++i) {
+                const int c0 = s0 + i * b;
+                T* Qi = P + c0;
+                TSVD_TRY(op_tmul<T>(h, op, b, Pbar + c0, rb, Qi, rb, status, st));                    // S2
+                double* Lii = B + (int64_t)c0 * rb + c0;
+                const bool couple = (i == 0 && s0 > 0);
+                TSVD_TRY(cgs_cqr2<T>(h, n, c0, b, P, rb, Qi, rb, couple ? Hk : nullptr, Lii, rb, true, ctx, ar, status,
+                                     st));                                                                // S3
+                if (couple) TSVD_TRY_CUDA(put_transposed(h, s0, b, Hk, b, B + (int64_t)c0 * rb, rb, st));  // G
+                const bool last = (i + 1 == nblk);
+                T* dst = last ? Qnext : Pbar + c0 + b;
+                const int64_t ldd = last ? b : rb;
+                TSVD_TRY(op_mul<T>(h, op, b, Qi, rb, dst, ldd, status, st));                             // S4
+                double* Ri = last ? Rr : B + (int64_t)(c0 + b) * rb + c0;
+                TSVD_TRY(cgs_cqr2<T>(h, m, c0 + b, b, Pbar, rb, dst, ldd, nullptr, Ri, last ? b : rb, false, ctx, ar,
+                                     status, st));                                                       // S5
+            }
+            {
+                Arena sv = ar;
+                TSVD_TRY(small_svd(h, d, B, rb, Ub, sig, Vb, nv, sv, status, st, ctx.deferred));        // S6
+            }
+            TSVD_TRY_CUDA(lanczos_rho(h, b, k, Rr, Vb + (int64_t)(d - b) * d, d, rho, st));
+            TSVD_TRY_CUDA(cudaMemcpyAsync(hrho.data(), rho, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+            TSVD_TRY_CUDA(cudaMemcpyAsync(hsig.data(), sig, sizeof(double), cudaMemcpyDeviceToHost, st));
+            TSVD_TRY(read_status(st, status, hs));
+            if (!(ctx.deferred && hs[kStBreakdown])) break;
+            // a deferred cycle met a breakdown: redo it checked
+            TSVD_TRY_CUDA(cudaMemsetAsync(status + kStBreakdown, 0, 2 * sizeof(int), st));
+            TSVD_TRY_CUDA(cudaMemcpyAsync(B, Bsave, sizeof(double) * (size_t)rb * rb, cudaMemcpyDeviceToDevice, st));
+            defer = false;
         }
+        ctx.deferred = false;
         ++cycles;
-        {
-            Arena sv = ar;
-            TSVD_TRY(small_svd(h, d, B, rb, Ub, sig, Vb, nv, sv, status, st));                      // S6
-        }
-        TSVD_TRY_CUDA(lanczos_rho(h, b, k, Rr, Vb + (int64_t)(d - b) * d, d, rho, st));
-        TSVD_TRY_CUDA(cudaMemcpyAsync(hrho.data(), rho, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
-        TSVD_TRY_CUDA(cudaMemcpyAsync(hsig.data(), sig, sizeof(double), cudaMemcpyDeviceToHost, st));
-        TSVD_TRY(read_status(st, status, hs));
         TSVD_TRY(status_code(hs));
         sweeps = hs[kStSweeps];
         prof_set_last_flops(h, TSVD_K_SVD, jacobi_flops(d, nv, sweeps));

@@ -542,6 +542,12 @@ __global__ void __launch_bounds__(128) jacobi_out_kernel(int n, int npad, const 
     if (threadIdx.x == 0) sigma[j] = sj;
 }
 
+// Breakdown, non-finite and timeout words of a private status block OR-ed into the caller's.
+__global__ void fold_status_kernel(const int* __restrict__ from, int* __restrict__ to) {
+    const int w = threadIdx.x;
+    if ((w == kStBreakdown || w == kStNonfinite || w == kStTimeout) && from[w]) atomicOr(&to[w], 1);
+}
+
 // Vbar[:, j] (held unscaled as B^T ubar_j) /= sigma_j, then the pair (ubar_j, vbar_j)
 // is flipped so the largest-magnitude entry of vbar_j (first on ties) is positive.
 __global__ void __launch_bounds__(128) jacobi_vfix_kernel(int n, const double* __restrict__ sigma,
@@ -649,6 +655,7 @@ size_t small_svd_ws(int n) {
         // re-orthonormalisation of the computed right vectors (block CGS-QR, blocks of 128)
         const int bw = n < TSVD_MAX_BLOCK ? n : TSVD_MAX_BLOCK;
         ar.take<double>((size_t)n * n);
+        ar.take<int>(kStCount);
         ar.take<double>((size_t)(n - bw) * bw);
         ar.take<char>(orth_ws(nullptr, n, n - bw, bw));
         best = std::max(best, ar.off);
@@ -698,7 +705,7 @@ static int run_block_sweeps(tsvd_handle* h, int n, int npad, int w, T* G, T* nrm
 }
 
 int small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* Ubar, double* sigma, double* Vbar, int nv,
-              Arena& ar, int* status, cudaStream_t st) {
+              Arena& ar, int* status, cudaStream_t st, bool deferred) {
     if (n < 1 || n > TSVD_MAX_SMALL_SVD) return TSVD_ERR_UNSUPPORTED;
     if (nv < 0 || nv > n) return TSVD_ERR_INVALID_ARG;
     const bool accumulate = (nv == n);
@@ -786,12 +793,20 @@ int small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* Ubar,
         // The columns of Ubar are orthonormal to the sweep tolerance tau, those of
         // B^T Ubar Sigma^-1 only to tau sigma_1 / sigma_j: one block CGS-QR (Alg. 3)
         // pass restores orthonormal right vectors (R = I + O(tau sigma_1 / sigma_nv)).
+        // It reports to status words of its own, so that it never consumes the caller's
+        // pending breakdown flag; deferred: unsynchronised, its breakdown folded into the
+        // caller's flag (the caller then redoes its work checked).
         OrthCtx vctx;
         vctx.seed = 0x5eedULL;
+        vctx.deferred = deferred;
         double* Rv = ar.take<double>((size_t)nv * nv);
+        int* vst = ar.take<int>(kStCount);
         if (!ar.fits()) return TSVD_ERR_WORKSPACE;
-        TSVD_TRY(cgs_qr<double>(h, n, nv, nv < TSVD_MAX_BLOCK ? nv : TSVD_MAX_BLOCK, Vbar, n, Rv, vctx, ar, status,
-                                st));
+        TSVD_TRY_CUDA(cudaMemsetAsync(vst, 0, sizeof(int) * kStCount, st));
+        TSVD_TRY(cgs_qr<double>(h, n, nv, nv < TSVD_MAX_BLOCK ? nv : TSVD_MAX_BLOCK, Vbar, n, Rv, vctx, ar, vst, st));
+        h->launches++;
+        fold_status_kernel<<<1, 32, 0, st>>>(vst, status);
+        TSVD_TRY_CUDA(cudaGetLastError());
     }
     return TSVD_OK;
 }

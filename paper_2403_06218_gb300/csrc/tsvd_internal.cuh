@@ -302,8 +302,10 @@ cudaError_t gaussian(tsvd_handle* h, int64_t rows, int64_t cols, uint64_t seed, 
 // recovers only the leading nv right vectors as B^T ubar_j / sigma_j (columns
 // j >= nv of Vbar are left undefined and those of Ubar carry no sign convention).
 size_t small_svd_ws(int n);
+// deferred: the re-orthonormalisation of the recovered right vectors runs unsynchronised
+// and a breakdown there only sets the caller's breakdown flag.
 int small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* Ubar, double* sigma,
-              double* Vbar, int nv, Arena& ar, int* status, cudaStream_t st);
+              double* Vbar, int nv, Arena& ar, int* status, cudaStream_t st, bool deferred = false);
 
 // out[j] = sum_i (Y[i,j] - U[i,j] * sigma[j])^2 for j < k  (deterministic).
 size_t colres_ws(int64_t q, int k);
