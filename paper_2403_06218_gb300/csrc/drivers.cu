@@ -79,6 +79,10 @@ struct Op {
     const void* pA = nullptr;
     const void* pAt = nullptr;
     void* tcws = nullptr;
+    // FP64 method, dense A: digit planes of A (rows layout, for A X) and of A^T (cols
+    // layout, for A^T X), sliced once per solve for the tensor-core products
+    bool oz = false;
+    OzCache ozA[2];
 };
 
 // Y (op.m x w) = op(A) X ; in precision TV with values V (sparse) or D (dense).
@@ -160,7 +164,7 @@ size_t tn_partial_max(tsvd_handle* h, int64_t q, int64_t s, int wmax) {
 // value conversions between FP64 and FP32, dense split-K scratch.
 template <typename T>
 int setup_op(tsvd_handle* h, const tsvd_matrix* A, int wmax, Arena& ar, Op<T>& op, int* status, cudaStream_t st,
-             bool run, float* ms_transpose) {
+             bool run, float* ms_transpose, bool oz_planes = false) {
     constexpr bool kF64 = sizeof(T) == sizeof(double);
     const bool in64 = A->dtype == TSVD_F64;
     const bool host = A->location == TSVD_HOST;
@@ -311,6 +315,16 @@ int setup_op(tsvd_handle* h, const tsvd_matrix* A, int wmax, Arena& ar, Op<T>& o
             op.pAt = pat;
         }
         op.partial = ar.take<double>(tn_partial_max(h, M, N, wmax) / sizeof(double) + 1);
+        if (oz_planes) {
+            op.oz = true;
+            oz_cache_carve(op.ozA[0], ar, op.dA64, op.lda64, M, N, false, kOzNoFixedExp);
+            oz_cache_carve(op.ozA[1], ar, op.dA64, op.lda64, M, N, true, kOzNoFixedExp);
+            if (run) {
+                if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+                TSVD_TRY(oz_cache_slice(h, op.ozA[0], 0, N, st));
+                TSVD_TRY(oz_cache_slice(h, op.ozA[1], 0, N, st));
+            }
+        }
     }
     return TSVD_OK;
 }
@@ -492,7 +506,13 @@ int rsvd_run(tsvd_handle* h, const tsvd_matrix* A, int k, int p, int q, int bq, 
     } del{total};
     Op<T> op;
     float ms_t = 0.f;
-    TSVD_TRY(setup_op<T>(h, A, ell > k ? ell : k, ar, op, status, st, run, A->format == TSVD_CSR ? &ms_t : nullptr));
+    TSVD_TRY(setup_op<T>(h, A, ell > k ? ell : k, ar, op, status, st, run, A->format == TSVD_CSR ? &ms_t : nullptr,
+                         true));
+    OzCacheScope ocs(h);
+    if (op.oz && run) {
+        ocs.add(&op.ozA[0]);
+        ocs.add(&op.ozA[1]);
+    }
     const int64_t m = op.m, n = op.n;
     T* Qn = ar.take<T>((size_t)n * ell);
     T* Qm = ar.take<T>((size_t)m * ell);
@@ -504,9 +524,10 @@ int rsvd_run(tsvd_handle* h, const tsvd_matrix* A, int k, int p, int q, int bq, 
     T* Qsave = ar.take<T>((size_t)n * ell);
     Final f;
     carve_final(ar, o, m, n, k, kMixed, f);
-    // FP64 method: scratch of the FP64-accurate tensor-core products
-    const size_t ozb = kMixed ? 0 : oz_ws_bound(std::max(m, n), ell, ell);
-    void* ozws = kMixed ? nullptr : ar.take<char>(ozb);
+    // scratch of the FP64-accurate tensor-core products (the mixed form's FP64 final
+    // Rayleigh-Ritz step and residual use them too)
+    const size_t ozb = oz_ws_bound(std::max(m, n), kMixed ? k : ell, kMixed ? k : ell);
+    void* ozws = ar.take<char>(ozb);
     if (!run) {
         const int64_t qmax = m > n ? m : n;
         size_t t1 = orth_ws(h, qmax, ell > bq ? ell - bq : 0, bq) + align256(sizeof(double) * (size_t)ell * bq);
@@ -611,7 +632,13 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
     } del{total};
     Op<T> op;
     float ms_t = 0.f;
-    TSVD_TRY(setup_op<T>(h, A, b > k ? b : k, ar, op, status, st, run, A->format == TSVD_CSR ? &ms_t : nullptr));
+    TSVD_TRY(setup_op<T>(h, A, b > k ? b : k, ar, op, status, st, run, A->format == TSVD_CSR ? &ms_t : nullptr,
+                         true));
+    OzCacheScope ocs(h);
+    if (op.oz && run) {
+        ocs.add(&op.ozA[0]);
+        ocs.add(&op.ozA[1]);
+    }
     const int64_t m = op.m, n = op.n;
     const int keep = o->restart_keep;                   // thick restart when > 0
     const int nv = std::max(std::max(k, b), keep);      // right vectors the small SVD must return
@@ -642,9 +669,36 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
     double* g64 = kMixed ? ar.take<double>((size_t)m * b) : nullptr;
     Final f;
     carve_final(ar, o, m, n, k, kMixed, f);
-    // FP64 method: scratch of the FP64-accurate tensor-core products
-    const size_t ozb = kMixed ? 0 : oz_ws_bound(std::max(m, n), rb, std::max(std::max(b, k), keep));
-    void* ozws = kMixed ? nullptr : ar.take<char>(ozb);
+    // FP64 method: scratch of the FP64-accurate tensor-core products, and the digit
+    // planes of both bases, kept up to date block by block: cols layout (per-column
+    // exponents) for P^T Y, rows layout (the fixed exponent 1 of an orthonormal basis,
+    // |entries| < 2) for P H and the Ritz products
+    const size_t ozb = kMixed ? oz_ws_bound(std::max(m, n), std::max(k, keep), std::max(k, keep))
+                              : oz_ws_bound(std::max(m, n), rb, std::max(std::max(b, k), keep));
+    void* ozws = ar.take<char>(ozb);
+    OzCache cP[2], cPb[2];
+    if (!kMixed) {
+        for (int l = 0; l < 2; ++l) {
+            oz_cache_carve(cP[l], ar, reinterpret_cast<const double*>(P), rb, n, rb, l == 0, l == 0 ? kOzNoFixedExp : 1);
+            oz_cache_carve(cPb[l], ar, reinterpret_cast<const double*>(Pbar), rb, m, rb, l == 0,
+                           l == 0 ? kOzNoFixedExp : 1);
+        }
+        if (run)
+            for (int l = 0; l < 2; ++l) {
+                ocs.add(&cP[l]);
+                ocs.add(&cPb[l]);
+            }
+    }
+    // columns [c0, c1) of a basis were written: slice them (c0 <= the current prefix)
+    auto slice_cols = [&](OzCache* c, int64_t c0, int64_t c1) -> int {
+        if (kMixed) return TSVD_OK;
+        for (int l = 0; l < 2; ++l) TSVD_TRY(oz_cache_slice(h, c[l], c0, c1, st));
+        return TSVD_OK;
+    };
+    // columns from v on are about to be rewritten: the caches no longer cover them
+    auto keep_cols = [&](OzCache* c, int64_t v) {
+        for (int l = 0; l < 2; ++l) c[l].valid = std::min<int64_t>(c[l].valid, v);
+    };
     if (!run) {
         size_t t1 = orth_ws(h, m, rb, b);
         const size_t t2 = orth_ws(h, n, rb, b), t3 = small_svd_ws(rb), t4 = final_tail_ws(h, m, n, k, kMixed);
@@ -671,6 +725,7 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
         TSVD_TRY_CUDA(gaussian(h, m, b, seed, 2u, reinterpret_cast<double*>(Pbar), rb, st));
     }
     TSVD_TRY(cgs_cqr2<T>(h, m, 0, b, nullptr, 0, Pbar, rb, nullptr, Rr, b, false, ctx, ar, status, st));
+    TSVD_TRY(slice_cols(cPb, 0, b));
     int cycles = 0, restarts = 0, sweeps = 0, converged = 0;
     double rho_last = NAN, resid = NAN;
     std::vector<double> hrho(k), hsig(1);
@@ -696,6 +751,8 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
             TSVD_TRY_CUDA(cudaMemcpyAsync(Bsave, B, sizeof(double) * (size_t)rb * rb, cudaMemcpyDeviceToDevice, st));
         for (int pass = 0; pass < 2; ++pass) {
             ctx.deferred = defer && pass == 0;
+            keep_cols(cP, s0);
+            keep_cols(cPb, s0 + b);
             for (int i = 0; i < nblk; ++i) {
                 const int c0 = s0 + i * b;
                 T* Qi = P + c0;
@@ -705,6 +762,7 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
                 TSVD_TRY(cgs_cqr2<T>(h, n, c0, b, P, rb, Qi, rb, couple ? Hk : nullptr, Lii, rb, true, ctx, ar, status,
                                      st));                                                                // S3
                 if (couple) TSVD_TRY_CUDA(put_transposed(h, s0, b, Hk, b, B + (int64_t)c0 * rb, rb, st));  // G
+                TSVD_TRY(slice_cols(cP, c0, c0 + b));
                 const bool last = (i + 1 == nblk);
                 T* dst = last ? Qnext : Pbar + c0 + b;
                 const int64_t ldd = last ? b : rb;
@@ -712,6 +770,7 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
                 double* Ri = last ? Rr : B + (int64_t)(c0 + b) * rb + c0;
                 TSVD_TRY(cgs_cqr2<T>(h, m, c0 + b, b, Pbar, rb, dst, ldd, nullptr, Ri, last ? b : rb, false, ctx, ar,
                                      status, st));                                                       // S5
+                if (!last) TSVD_TRY(slice_cols(cPb, c0 + b, c0 + 2 * b));
             }
             {
                 Arena sv = ar;
@@ -773,18 +832,26 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
             } else {
                 TSVD_TRY_CUDA((gemm_nn<T, double, T>(h, n, d, keep, 1.0, P, rb, Vb, d, 0.0, Pk, keep, false, st)));
                 TSVD_TRY_CUDA((gemm_nn<T, double, T>(h, m, d, keep, 1.0, Pbar, rb, Ub, d, 0.0, Pbk, keep, false, st)));
+                keep_cols(cP, 0);
+                keep_cols(cPb, 0);
                 TSVD_TRY_CUDA(copy_block<T>(Pk, keep, P, rb, n, keep, st));
                 TSVD_TRY_CUDA(copy_block<T>(Pbk, keep, Pbar, rb, m, keep, st));
             }
+            keep_cols(cPb, keep);
             TSVD_TRY_CUDA(copy_block<T>(Qnext, b, Pbar + keep, rb, m, b, st));
+            TSVD_TRY(slice_cols(cP, 0, keep));
+            TSVD_TRY(slice_cols(cPb, 0, keep + b));
             TSVD_TRY_CUDA(cudaMemsetAsync(B, 0, sizeof(double) * (size_t)rb * rb, st));
             TSVD_TRY_CUDA(put_diagonal(h, keep, sig, B, rb, st));
             s0 = keep;
         } else {
             // S7: Qbar_1 = Pbar Ubar_1, re-orthonormalised by CholeskyQR2
             TSVD_TRY_CUDA((gemm_nn<T, double, T>(h, m, rb, b, 1.0, Pbar, rb, Ub, rb, 0.0, Qnext, b, false, st)));
+            keep_cols(cP, 0);
+            keep_cols(cPb, 0);
             TSVD_TRY_CUDA(copy_block<T>(Qnext, b, Pbar, rb, m, b, st));
             TSVD_TRY(cgs_cqr2<T>(h, m, 0, b, nullptr, 0, Pbar, rb, nullptr, Rr, b, false, ctx, ar, status, st));
+            TSVD_TRY(slice_cols(cPb, 0, b));
         }
     }
     TSVD_TRY(read_status(st, status, hs));

@@ -511,9 +511,10 @@ cudaError_t gemm_tn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, const TI* X
     ProfScope prof(h, TSVD_K_GEMM_TN, symmetric ? (double)q * b * (b + 1) : 2.0 * q * s * b,
                    (double)sizeof(TI) * (double)q * (symmetric ? b : s + b) + (double)sizeof(TC) * s * b, st);
     if constexpr (std::is_same<TI, double>::value && std::is_same<TC, double>::value) {
-        if (h->oz_ws && oz_worth(s, b, q) && oz_tn_ws(q, s, b, symmetric) <= h->oz_bytes) {
+        const OzCache* xc = h->oz_ws ? oz_find_cache(h, X, ldx, q, s, true) : nullptr;
+        if (h->oz_ws && oz_worth(s, b, q) && oz_tn_ws(q, s, b, symmetric, xc != nullptr) <= h->oz_bytes) {
             const int rc = oz_gemm_tn(h, q, s, b, X, ldx, Z, ldz, C, ldc, symmetric, h->oz_ws, h->oz_bytes,
-                                      h->oz_status, st);
+                                      h->oz_status, st, xc);
             return rc == TSVD_OK ? cudaSuccess : cudaErrorUnknown;
         }
     }
@@ -559,9 +560,10 @@ cudaError_t gemm_nn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, double alph
                        (double)sizeof(TY) * q * b * (beta != 0.0 ? 2 : 1), st);
     if constexpr (std::is_same<TX, double>::value && std::is_same<TM, double>::value &&
                   std::is_same<TY, double>::value) {
-        if (h->oz_ws && s > 0 && oz_worth(q, b, s) && oz_nn_ws(q, s, b) <= h->oz_bytes) {
+        const OzCache* xc = h->oz_ws ? oz_find_cache(h, X, ldx, q, s, false) : nullptr;
+        if (h->oz_ws && s > 0 && oz_worth(q, b, s) && oz_nn_ws(q, s, b, xc != nullptr) <= h->oz_bytes) {
             const int rc = oz_gemm_nn(h, q, s, b, alpha, X, ldx, M, ldm, beta, Y, ldy, upper, h->oz_ws, h->oz_bytes,
-                                      h->oz_status, st);
+                                      h->oz_status, st, xc);
             return rc == TSVD_OK ? cudaSuccess : cudaErrorUnknown;
         }
     }

@@ -150,6 +150,29 @@ __global__ void __launch_bounds__(256) oz_slice_rows_kernel(int64_t R, int64_t K
     }
 }
 
+// Rows slicer with one fixed exponent e for every row (an orthonormal basis: every
+// entry below 2^e in magnitude), over a window of K columns of S (R x K, lds) written
+// to columns [0, K) of planes (already offset to the window).  A row holding an entry
+// at or above 2^e, or Inf/NaN, gets the exponent of a non-finite row.
+__global__ void __launch_bounds__(256) oz_slice_rows_fixed_kernel(int64_t R, int64_t K, const double* __restrict__ S,
+                                                                  int64_t lds, __nv_bfloat16* __restrict__ planes,
+                                                                  int64_t ldk, int64_t pstride, int e,
+                                                                  int* __restrict__ eexp) {
+    const int64_t halfk = (K + 1) / 2;
+    const int64_t tot = R * halfk;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / halfk, k = 2 * (t % halfk);
+        const double x0 = S[i * lds + k], x1 = k + 1 < K ? S[i * lds + k + 1] : 0.0;
+        if (oz_exp(x0) > e || oz_exp(x1) > e) eexp[i] = kOzNanExp;
+        int da[kOzDig], db[kOzDig];
+        oz_digits(x0, e, da);
+        oz_digits(x1, e, db);
+        __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(planes + i * ldk + k);
+#pragma unroll
+        for (int p = 0; p < kOzDig; ++p) dst[p * (pstride / 2)] = oz_pack(da[p], db[p], p);
+    }
+}
+
 // Column maxima of the exponents of S (K x R, lds); upper: entries with k > j are zero.
 __global__ void __launch_bounds__(256) oz_colmax_kernel(int64_t K, int64_t R, const double* __restrict__ S,
                                                         int64_t lds, int upper, int64_t rows_per,
@@ -542,22 +565,13 @@ inline size_t oz_partial_bytes(const OzPlan& p) {
     return needs ? align256(sizeof(double) * (size_t)p.G * p.maxseg * kOzM * kOzN) : 0;
 }
 
-struct OzBufs {
-    __nv_bfloat16 *pa, *pb;
-    int *ea, *eb;
-    double* partial;
+// One operand of the product kernel: `rows` stored rows of K digits each, planes
+// [7][.][ldk] with plane stride pstride (elements), one exponent per stored row.
+struct OzView {
+    const __nv_bfloat16* planes;
+    int64_t rows, K, ldk, pstride;
+    const int* exps;
 };
-
-OzBufs oz_carve(Arena& ar, const OzPlan& p, bool shared_ab) {
-    OzBufs b{};
-    b.pa = reinterpret_cast<__nv_bfloat16*>(ar.take<char>(oz_planes_bytes(p.M, p.K)));
-    b.pb = shared_ab ? b.pa : reinterpret_cast<__nv_bfloat16*>(ar.take<char>(oz_planes_bytes(p.N, p.K)));
-    b.ea = ar.take<int>((size_t)p.M);
-    b.eb = shared_ab ? b.ea : ar.take<int>((size_t)p.N);
-    const size_t pb = oz_partial_bytes(p);
-    b.partial = pb ? reinterpret_cast<double*>(ar.take<char>(pb)) : nullptr;
-    return b;
-}
 
 int oz_slice_rows(tsvd_handle* h, int64_t R, int64_t K, const double* S, int64_t lds, __nv_bfloat16* planes,
                   int* eexp, cudaStream_t st) {
@@ -571,9 +585,10 @@ int oz_slice_rows(tsvd_handle* h, int64_t R, int64_t K, const double* S, int64_t
 }
 
 int oz_slice_cols(tsvd_handle* h, int64_t K, int64_t R, const double* S, int64_t lds, bool upper,
-                  __nv_bfloat16* planes, int* eexp, cudaStream_t st) {
+                  __nv_bfloat16* planes, int* eexp, cudaStream_t st, int64_t pstride = -1) {
     if (R == 0) return TSVD_OK;
     const int64_t ldk = oz_ld(K);
+    if (pstride < 0) pstride = R * ldk;
     const unsigned gx = (unsigned)((R + 31) / 32);
     int64_t gy = std::min<int64_t>((K + 255) / 256, std::max<int64_t>(1, (int64_t)h->sm_count * 8 / gx));
     const int64_t rows_per = (K + gy - 1) / gy;
@@ -584,13 +599,13 @@ int oz_slice_cols(tsvd_handle* h, int64_t K, int64_t R, const double* S, int64_t
                                                                                            upper ? 1 : 0, rows_per,
                                                                                            eexp);
     const dim3 sg((unsigned)((oz_ld(K) + 63) / 64), gx);
-    oz_slice_cols_kernel<<<sg, 256, 0, st>>>(K, R, S, lds, upper ? 1 : 0, eexp, planes, ldk, R * ldk);
+    oz_slice_cols_kernel<<<sg, 256, 0, st>>>(K, R, S, lds, upper ? 1 : 0, eexp, planes, ldk, pstride);
     TSVD_TRY_CUDA(cudaGetLastError());
     return TSVD_OK;
 }
 
-int oz_run(tsvd_handle* h, const OzPlan& p, const OzBufs& b, double* out, int64_t ldo, double alpha, double beta,
-           bool symmetric, int* status, cudaStream_t st) {
+int oz_run(tsvd_handle* h, const OzPlan& p, const OzView& va, const OzView& vb, double* partial, double* out,
+           int64_t ldo, double alpha, double beta, bool symmetric, int* status, cudaStream_t st) {
     if (p.tiles > 65535) return TSVD_ERR_UNSUPPORTED;  // one fix-up grid row per tile
     static thread_local int configured = -1;
     if (configured != h->device) {
@@ -598,8 +613,8 @@ int oz_run(tsvd_handle* h, const OzPlan& p, const OzBufs& b, double* out, int64_
         configured = h->device;
     }
     CUtensorMap mA, mB;
-    if (!make_plane_map(&mA, b.pa, p.K, p.M, oz_ld(p.K), kOzM, kOzDig, kOzBK)) return TSVD_ERR_CUDA;
-    if (!make_plane_map(&mB, b.pb, p.K, p.N, oz_ld(p.K), p.Npad, kOzDig, kOzBK)) return TSVD_ERR_CUDA;
+    if (!make_plane_map(&mA, va.planes, p.K, p.M, va.ldk, kOzM, kOzDig, kOzBK, va.pstride)) return TSVD_ERR_CUDA;
+    if (!make_plane_map(&mB, vb.planes, p.K, p.N, vb.ldk, p.Npad, kOzDig, kOzBK, vb.pstride)) return TSVD_ERR_CUDA;
     OzArgs a{};
     a.M = p.M;
     a.N = p.N;
@@ -611,19 +626,19 @@ int oz_run(tsvd_handle* h, const OzPlan& p, const OzBufs& b, double* out, int64_
     a.G = p.G;
     a.aligned = p.aligned ? 1 : 0;
     a.maxseg = p.maxseg;
-    a.ea = b.ea;
-    a.eb = b.eb;
+    a.ea = va.exps;
+    a.eb = vb.exps;
     a.out = out;
     a.ldo = ldo;
     a.alpha = alpha;
     a.beta = beta;
     a.symmetric = symmetric ? 1 : 0;
-    a.partial = b.partial;
+    a.partial = partial;
     a.status = status;
     h->launches++;
     oz_gemm_kernel<<<p.G, kOzThreads, kOzSmem, st>>>(mA, mB, a);
     TSVD_TRY_CUDA(cudaGetLastError());
-    if (b.partial) {
+    if (partial) {
         h->launches++;
         oz_fixup_kernel<<<dim3((kOzM * kOzN + 255) / 256, (unsigned)p.tiles), 256, 0, st>>>(a);
         TSVD_TRY_CUDA(cudaGetLastError());
@@ -640,18 +655,6 @@ bool oz_worth(int64_t M, int64_t N, int64_t K) {
     return M > 0 && N > 0 && K >= 32 && tiles <= 65535 && N <= 65535 * 32 && 2.0 * (double)M * N * K >= 3.0e7;
 }
 
-size_t oz_tn_ws(int64_t q, int64_t s, int64_t b, bool symmetric) {
-    Arena ar;
-    oz_carve(ar, oz_plan(s, b, q), symmetric);
-    return ar.off;
-}
-
-size_t oz_nn_ws(int64_t q, int64_t s, int64_t b) {
-    Arena ar;
-    oz_carve(ar, oz_plan(q, b, s), false);
-    return ar.off;
-}
-
 size_t oz_ws_bound(int64_t qmax, int64_t smax, int64_t bmax) {
     // planes and exponents of the largest operands of either product, and split-K
     // partial tiles for at most (tiles + 2 per CTA of one wave) tiles
@@ -663,28 +666,162 @@ size_t oz_ws_bound(int64_t qmax, int64_t smax, int64_t bmax) {
     return std::max(tn, nn) + ex + part + 4096;
 }
 
+namespace {
+
+OzView view_of(const __nv_bfloat16* planes, int64_t rows, int64_t K, const int* exps) {
+    return OzView{planes, rows, K, oz_ld(K), rows * oz_ld(K), exps};
+}
+
+// The cached planes of columns [0, s) (cols layout: stored rows) or of the first s
+// columns of every row (rows layout: K = s).
+OzView view_of_cache(const OzCache& c, int64_t s) {
+    return c.cols_layout ? OzView{c.planes, s, c.rows, c.ldk, c.pstride, c.exps}
+                         : OzView{c.planes, c.rows, s, c.ldk, c.pstride, c.exps};
+}
+
+}  // namespace
+
+size_t oz_tn_ws(int64_t q, int64_t s, int64_t b, bool symmetric, bool cached_x) {
+    const OzPlan p = oz_plan(s, b, q);
+    Arena ar;
+    if (!cached_x) {
+        ar.take<char>(oz_planes_bytes(p.M, p.K));
+        ar.take<int>((size_t)p.M);
+    }
+    if (!symmetric || cached_x) {
+        ar.take<char>(oz_planes_bytes(p.N, p.K));
+        ar.take<int>((size_t)p.N);
+    }
+    ar.take<char>(oz_partial_bytes(p));
+    return ar.off;
+}
+
+size_t oz_nn_ws(int64_t q, int64_t s, int64_t b, bool cached_x) {
+    const OzPlan p = oz_plan(q, b, s);
+    Arena ar;
+    if (!cached_x) {
+        ar.take<char>(oz_planes_bytes(p.M, p.K));
+        ar.take<int>((size_t)p.M);
+    }
+    ar.take<char>(oz_planes_bytes(p.N, p.K));
+    ar.take<int>((size_t)p.N);
+    ar.take<char>(oz_partial_bytes(p));
+    return ar.off;
+}
+
 int oz_gemm_tn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, const double* X, int64_t ldx, const double* Z,
                int64_t ldz, double* C, int64_t ldc, bool symmetric, void* ws, size_t ws_bytes, int* status,
-               cudaStream_t st) {
+               cudaStream_t st, const OzCache* xc) {
     const OzPlan p = oz_plan(s, b, q);
     Arena ar{static_cast<char*>(ws), ws_bytes, 0};
-    const OzBufs bf = oz_carve(ar, p, symmetric);
+    OzView va{}, vb{};
+    if (xc) {
+        va = view_of_cache(*xc, s);
+    } else {
+        __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(ar.take<char>(oz_planes_bytes(p.M, p.K)));
+        int* ea = ar.take<int>((size_t)p.M);
+        if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+        TSVD_TRY(oz_slice_cols(h, q, s, X, ldx, false, pa, ea, st));
+        va = view_of(pa, s, q, ea);
+    }
+    if (symmetric && !xc) {
+        vb = va;
+    } else {
+        __nv_bfloat16* pb = reinterpret_cast<__nv_bfloat16*>(ar.take<char>(oz_planes_bytes(p.N, p.K)));
+        int* eb = ar.take<int>((size_t)p.N);
+        if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+        TSVD_TRY(oz_slice_cols(h, q, b, Z, ldz, false, pb, eb, st));
+        vb = view_of(pb, b, q, eb);
+    }
+    const size_t pbytes = oz_partial_bytes(p);
+    double* part = pbytes ? reinterpret_cast<double*>(ar.take<char>(pbytes)) : nullptr;
     if (!ar.fits()) return TSVD_ERR_WORKSPACE;
-    TSVD_TRY(oz_slice_cols(h, q, s, X, ldx, false, bf.pa, bf.ea, st));
-    if (!symmetric) TSVD_TRY(oz_slice_cols(h, q, b, Z, ldz, false, bf.pb, bf.eb, st));
-    return oz_run(h, p, bf, C, ldc, 1.0, 0.0, symmetric, status, st);
+    return oz_run(h, p, va, vb, part, C, ldc, 1.0, 0.0, symmetric, status, st);
 }
 
 int oz_gemm_nn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, double alpha, const double* X, int64_t ldx,
                const double* Mm, int64_t ldm, double beta, double* Y, int64_t ldy, bool upper, void* ws,
-               size_t ws_bytes, int* status, cudaStream_t st) {
+               size_t ws_bytes, int* status, cudaStream_t st, const OzCache* xc) {
     const OzPlan p = oz_plan(q, b, s);
     Arena ar{static_cast<char*>(ws), ws_bytes, 0};
-    const OzBufs bf = oz_carve(ar, p, false);
+    OzView va{};
+    if (xc) {
+        va = view_of_cache(*xc, s);
+    } else {
+        __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(ar.take<char>(oz_planes_bytes(p.M, p.K)));
+        int* ea = ar.take<int>((size_t)p.M);
+        if (!ar.fits()) return TSVD_ERR_WORKSPACE;
+        TSVD_TRY(oz_slice_rows(h, q, s, X, ldx, pa, ea, st));
+        va = view_of(pa, q, s, ea);
+    }
+    __nv_bfloat16* pb = reinterpret_cast<__nv_bfloat16*>(ar.take<char>(oz_planes_bytes(p.N, p.K)));
+    int* eb = ar.take<int>((size_t)p.N);
+    const size_t pbytes = oz_partial_bytes(p);
+    double* part = pbytes ? reinterpret_cast<double*>(ar.take<char>(pbytes)) : nullptr;
     if (!ar.fits()) return TSVD_ERR_WORKSPACE;
-    TSVD_TRY(oz_slice_rows(h, q, s, X, ldx, bf.pa, bf.ea, st));
-    TSVD_TRY(oz_slice_cols(h, s, b, Mm, ldm, upper, bf.pb, bf.eb, st));
-    return oz_run(h, p, bf, Y, ldy, alpha, beta, false, status, st);
+    TSVD_TRY(oz_slice_cols(h, s, b, Mm, ldm, upper, pb, eb, st));
+    return oz_run(h, p, va, view_of(pb, b, s, eb), part, Y, ldy, alpha, beta, false, status, st);
+}
+
+// ---- caches of operands that many products read ----------------------------------
+size_t oz_cache_bytes(int64_t rows, int64_t cols, bool cols_layout) {
+    Arena ar;
+    OzCache c;
+    oz_cache_carve(c, ar, nullptr, 0, rows, cols, cols_layout, kOzNoFixedExp);
+    return ar.off;
+}
+
+void oz_cache_carve(OzCache& c, Arena& ar, const double* src, int64_t ld, int64_t rows, int64_t cols,
+                    bool cols_layout, int fixed_exp) {
+    c = OzCache{};
+    c.src = src;
+    c.ld = ld;
+    c.rows = rows;
+    c.cols = cols;
+    c.cols_layout = cols_layout;
+    c.fixed_exp = fixed_exp;
+    const int64_t srows = cols_layout ? cols : rows, K = cols_layout ? rows : cols;
+    c.ldk = oz_ld(K);
+    c.pstride = srows * c.ldk;
+    c.planes = reinterpret_cast<__nv_bfloat16*>(ar.take<char>(oz_planes_bytes(srows, K)));
+    c.exps = ar.take<int>((size_t)srows);
+    c.valid = 0;
+}
+
+int oz_cache_slice(tsvd_handle* h, OzCache& c, int64_t c0, int64_t c1, cudaStream_t st) {
+    if (c0 > c.valid || c1 > c.cols || c0 > c1) return TSVD_ERR_INVALID_ARG;
+    if (c1 > c0) {
+        if (c.cols_layout) {
+            // stored rows [c0, c1): the columns' own exponents
+            TSVD_TRY(oz_slice_cols(h, c.rows, c1 - c0, c.src + c0, c.ld, false, c.planes + c0 * c.ldk, c.exps + c0,
+                                   st, c.pstride));
+        } else if (c.fixed_exp != kOzNoFixedExp) {
+            if (c0 == 0) {
+                h->launches++;
+                oz_fill_kernel<<<(unsigned)((c.rows + 255) / 256), 256, 0, st>>>(c.rows, c.fixed_exp, c.exps);
+            }
+            const int64_t tot = c.rows * ((c1 - c0 + 1) / 2);
+            const int64_t blocks = std::min<int64_t>((tot + 255) / 256, (int64_t)h->sm_count * 32);
+            h->launches++;
+            oz_slice_rows_fixed_kernel<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, st>>>(
+                c.rows, c1 - c0, c.src + c0, c.ld, c.planes + c0, c.ldk, c.pstride, c.fixed_exp, c.exps);
+            TSVD_TRY_CUDA(cudaGetLastError());
+        } else {
+            // per-row exponents need the whole rows at once
+            if (c0 != 0 || c1 != c.cols) return TSVD_ERR_INVALID_ARG;
+            TSVD_TRY(oz_slice_rows(h, c.rows, c.cols, c.src, c.ld, c.planes, c.exps, st));
+        }
+    }
+    c.valid = c1;
+    return TSVD_OK;
+}
+
+const OzCache* oz_find_cache(const tsvd_handle* h, const double* X, int64_t ldx, int64_t rows, int64_t s,
+                             bool cols_layout) {
+    for (const OzCache* c : h->oz_caches)
+        if (c && c->src == X && c->ld == ldx && c->rows == rows && c->cols_layout == cols_layout && s <= c->valid)
+            return c;
+    return nullptr;
 }
 
 }  // namespace tsvd

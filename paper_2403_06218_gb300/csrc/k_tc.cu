@@ -465,11 +465,12 @@ EncodeTiledFn encode_fn() {
 }
 
 bool make_plane_map(CUtensorMap* map, const void* base, int64_t cols, int64_t rows, int64_t ld, int box_rows,
-                    int planes, int box_k) {
+                    int planes, int box_k, int64_t pstride) {
     EncodeTiledFn fn = encode_fn();
     if (!fn || (box_k != 32 && box_k != 16)) return false;
+    if (pstride < 0) pstride = ld * rows;
     const cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)planes};
-    const cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)ld * 2 * (cuuint64_t)rows};
+    const cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)pstride * 2};
     const cuuint32_t box[3] = {(cuuint32_t)box_k, (cuuint32_t)box_rows, (cuuint32_t)planes};
     const cuuint32_t estr[3] = {1, 1, 1};
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,

@@ -152,8 +152,9 @@ EncodeTiledFn encode_fn();
 // a multiple of 8), K extent `cols`; box box_k (K) x box_rows x planes with a
 // swizzle of 2 box_k bytes (box_k = 32: 64-byte swizzle, 16: 32-byte swizzle).
 // Loads beyond `cols` or `rows` read zeros.
+// pstride: elements between planes (default rows x ld).
 bool make_plane_map(CUtensorMap* map, const void* base, int64_t cols, int64_t rows, int64_t ld, int box_rows,
-                    int planes, int box_k = 32);
+                    int planes, int box_k = 32, int64_t pstride = -1);
 
 }  // namespace tcx
 }  // namespace tsvd

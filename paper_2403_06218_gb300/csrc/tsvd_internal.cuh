@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of the library.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -9,6 +10,25 @@
 #include <vector>
 
 #include "tsvd.h"
+
+namespace tsvd {
+// A matrix whose BF16 digit planes (the FP64-accurate tensor-core product's input
+// form) are kept for many products: a Lanczos basis, or a dense A.  Rows layout:
+// planes [7][rows][ldk], one exponent per row (K = the columns); cols layout: planes
+// [7][cols][ldk], one exponent per column (K = the rows).  Columns [0, valid) are
+// current; the owner slices columns as it writes them (oz_cache_slice).
+struct OzCache {
+    const double* src = nullptr;
+    int64_t ld = 0, rows = 0, cols = 0;
+    bool cols_layout = false;
+    int fixed_exp = 0;  // rows layout of an orthonormal basis: every row's exponent
+    __nv_bfloat16* planes = nullptr;
+    int* exps = nullptr;
+    int64_t ldk = 0, pstride = 0;
+    int64_t valid = 0;
+};
+constexpr int kOzNoFixedExp = -(1 << 30);
+}  // namespace tsvd
 
 // CUDA-event timing per kernel class (TSVD_FLAG_PROFILE).
 struct tsvd_prof_rec {
@@ -32,6 +52,8 @@ struct tsvd_handle {
     void* oz_ws = nullptr;
     size_t oz_bytes = 0;
     int* oz_status = nullptr;
+    // operands whose digit planes are kept for the current call (owned by the caller)
+    std::vector<const tsvd::OzCache*> oz_caches;
 };
 
 namespace tsvd {
@@ -241,20 +263,39 @@ cudaError_t gemm_tn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, const TI* X
 // ---- FP64-accurate tensor-core products (k_oz.cu) -------------------------------
 // Worth running on the tensor cores rather than the FP64 pipe (M x N outputs, K deep).
 bool oz_worth(int64_t M, int64_t N, int64_t K);
-// Scratch of C = X^T Z (q rows; s x b outputs) and of Y = X M (q x s times s x b).
-size_t oz_tn_ws(int64_t q, int64_t s, int64_t b, bool symmetric);
-size_t oz_nn_ws(int64_t q, int64_t s, int64_t b);
+// Scratch of C = X^T Z (q rows; s x b outputs) and of Y = X M (q x s times s x b);
+// cached_x: the planes of X come from a cache.
+size_t oz_tn_ws(int64_t q, int64_t s, int64_t b, bool symmetric, bool cached_x = false);
+size_t oz_nn_ws(int64_t q, int64_t s, int64_t b, bool cached_x = false);
 // Scratch that covers every product with q <= qmax, s <= smax, b <= bmax (and s, b swapped).
 size_t oz_ws_bound(int64_t qmax, int64_t smax, int64_t bmax);
 // C (s x b, ldc) = X^T Z, X (q x s, ldx), Z (q x b, ldz); symmetric: Z == X, C mirrored.
+// xc: cached planes of X (cols layout, s <= xc->valid) instead of slicing X.
 int oz_gemm_tn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, const double* X, int64_t ldx, const double* Z,
                int64_t ldz, double* C, int64_t ldc, bool symmetric, void* ws, size_t ws_bytes, int* status,
-               cudaStream_t st);
+               cudaStream_t st, const OzCache* xc = nullptr);
 // Y (q x b, ldy) = beta Y + alpha X M; upper: M upper triangular (entries below its
 // diagonal are not read).  Y may alias X.
+// xc: cached planes of X (rows layout, s <= xc->valid).
 int oz_gemm_nn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, double alpha, const double* X, int64_t ldx,
                const double* Mm, int64_t ldm, double beta, double* Y, int64_t ldy, bool upper, void* ws,
-               size_t ws_bytes, int* status, cudaStream_t st);
+               size_t ws_bytes, int* status, cudaStream_t st, const OzCache* xc = nullptr);
+// Caches: bytes, carving (no device work), slicing of columns [c0, c1) (c0 <= valid;
+// then valid = c1), and the lookup the products use.
+size_t oz_cache_bytes(int64_t rows, int64_t cols, bool cols_layout);
+void oz_cache_carve(OzCache& c, Arena& ar, const double* src, int64_t ld, int64_t rows, int64_t cols,
+                    bool cols_layout, int fixed_exp);
+int oz_cache_slice(tsvd_handle* h, OzCache& c, int64_t c0, int64_t c1, cudaStream_t st);
+const OzCache* oz_find_cache(const tsvd_handle* h, const double* X, int64_t ldx, int64_t rows, int64_t s,
+                             bool cols_layout);
+// Registers caches with the handle for its lifetime.
+struct OzCacheScope {
+    tsvd_handle* h;
+    size_t n0;
+    explicit OzCacheScope(tsvd_handle* hh) : h(hh), n0(hh->oz_caches.size()) {}
+    void add(const OzCache* c) { h->oz_caches.push_back(c); }
+    ~OzCacheScope() { h->oz_caches.resize(n0); }
+};
 
 // Makes the FP64 products of one call run on the tensor cores with `bytes` of
 // scratch at `ws` (restores the handle's previous setting on destruction).
