@@ -696,8 +696,10 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
         return TSVD_OK;
     };
     // columns from v on are about to be rewritten: the caches no longer cover them
-    auto keep_cols = [&](OzCache* c, int64_t v) {
-        for (int l = 0; l < 2; ++l) c[l].valid = std::min<int64_t>(c[l].valid, v);
+    auto keep_cols = [&](OzCache* c, int64_t v) -> int {
+        if (kMixed) return TSVD_OK;
+        for (int l = 0; l < 2; ++l) TSVD_TRY(oz_cache_truncate(h, c[l], v, st));
+        return TSVD_OK;
     };
     if (!run) {
         size_t t1 = orth_ws(h, m, rb, b);
@@ -751,8 +753,8 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
             TSVD_TRY_CUDA(cudaMemcpyAsync(Bsave, B, sizeof(double) * (size_t)rb * rb, cudaMemcpyDeviceToDevice, st));
         for (int pass = 0; pass < 2; ++pass) {
             ctx.deferred = defer && pass == 0;
-            keep_cols(cP, s0);
-            keep_cols(cPb, s0 + b);
+            TSVD_TRY(keep_cols(cP, s0));
+            TSVD_TRY(keep_cols(cPb, s0 + b));
             for (int i = 0; i < nblk; ++i) {
                 const int c0 = s0 + i * b;
                 T* Qi = P + c0;
@@ -832,12 +834,12 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
             } else {
                 TSVD_TRY_CUDA((gemm_nn<T, double, T>(h, n, d, keep, 1.0, P, rb, Vb, d, 0.0, Pk, keep, false, st)));
                 TSVD_TRY_CUDA((gemm_nn<T, double, T>(h, m, d, keep, 1.0, Pbar, rb, Ub, d, 0.0, Pbk, keep, false, st)));
-                keep_cols(cP, 0);
-                keep_cols(cPb, 0);
+                TSVD_TRY(keep_cols(cP, 0));
+                TSVD_TRY(keep_cols(cPb, 0));
                 TSVD_TRY_CUDA(copy_block<T>(Pk, keep, P, rb, n, keep, st));
                 TSVD_TRY_CUDA(copy_block<T>(Pbk, keep, Pbar, rb, m, keep, st));
             }
-            keep_cols(cPb, keep);
+            TSVD_TRY(keep_cols(cPb, keep));
             TSVD_TRY_CUDA(copy_block<T>(Qnext, b, Pbar + keep, rb, m, b, st));
             TSVD_TRY(slice_cols(cP, 0, keep));
             TSVD_TRY(slice_cols(cPb, 0, keep + b));
@@ -847,8 +849,8 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
         } else {
             // S7: Qbar_1 = Pbar Ubar_1, re-orthonormalised by CholeskyQR2
             TSVD_TRY_CUDA((gemm_nn<T, double, T>(h, m, rb, b, 1.0, Pbar, rb, Ub, rb, 0.0, Qnext, b, false, st)));
-            keep_cols(cP, 0);
-            keep_cols(cPb, 0);
+            TSVD_TRY(keep_cols(cP, 0));
+            TSVD_TRY(keep_cols(cPb, 0));
             TSVD_TRY_CUDA(copy_block<T>(Qnext, b, Pbar, rb, m, b, st));
             TSVD_TRY(cgs_cqr2<T>(h, m, 0, b, nullptr, 0, Pbar, rb, nullptr, Rr, b, false, ctx, ar, status, st));
             TSVD_TRY(slice_cols(cPb, 0, b));

@@ -226,9 +226,15 @@ __global__ void __launch_bounds__(128) gemm_nn_kernel(int64_t q, int64_t s, int6
 }
 
 // ---------------------------------------------------------------------------
-// chol_inv: one CTA.  Right-looking Cholesky in shared memory, breakdown test
-// d <= b*eps*max_i W_ii, then in-place inversion of L (column j from the last
-// to the first, using the already inverted trailing block).
+// chol_inv: one CTA of 256 threads.  Right-looking Cholesky of the lower triangle
+// in shared memory (breakdown test d <= b*eps*max_i W_ii), then L^{-1} by
+// right-looking forward substitution, stored transposed in the upper triangle of
+// the same array (row k of L^{-1} is final once scaled; the rows below it take
+// a rank-1 update).  GB300's FP64 pipe costs a warp instruction 16 cycles
+// whatever its active lanes, so every FP64 phase is a flat loop over whole
+// warps of independent elements (no per-thread chains of varying length), and
+// the one scalar step per column (1/sqrt of the pivot) is an FP32 estimate with
+// two FP64 Newton steps.
 // ---------------------------------------------------------------------------
 __device__ inline void tri_decode(int idx, int& ii, int& kk) {
     int r = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
@@ -238,16 +244,30 @@ __device__ inline void tri_decode(int idx, int& ii, int& kk) {
     kk = idx - r * (r + 1) / 2;
 }
 
+// 1/sqrt(d) for finite d > 0: FP32 estimate of the scaled value, two Newton steps
+// y <- y (3 - d y^2) / 2 in FP64 (24 -> 48 -> beyond 53 bits), rescaled.
+__device__ inline double rsqrt_fp64(double d) {
+    const int e = ilogb(d) & ~1;  // even exponent: d = dd 2^e, dd in [1, 4)
+    const double dd = scalbn(d, -e);
+    double y = (double)rsqrtf((float)dd);
+    y = y * fma(-0.5 * dd, y * y, 1.5);
+    y = y * fma(-0.5 * dd, y * y, 1.5);
+    return scalbn(y, -e / 2);
+}
+
 __global__ void __launch_bounds__(256) chol_inv_kernel(int b, const double* __restrict__ W, double* __restrict__ Lt,
                                                        double* __restrict__ Mt, int* status) {
     extern __shared__ double sm[];
     const int ld = b + 1;
-    double* A = sm;
-    double* tmp = sm + (size_t)b * ld;
+    double* A = sm;                    // lower: L; upper (transposed): L^{-1}
+    double* dinv = sm + (size_t)b * ld; // 1 / L_jj
     __shared__ double s_thresh;
     __shared__ int s_bad;
-    const int tid = threadIdx.x;
-    for (int idx = tid; idx < b * b; idx += blockDim.x) A[(idx / b) * ld + idx % b] = W[idx];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int idx = tid; idx < b * b; idx += nt) {
+        const int i = idx / b, j = idx % b;
+        A[i * ld + j] = (j <= i) ? W[idx] : 0.0;  // the upper part starts as zero (L^{-1} = I - ...)
+    }
     __syncthreads();
     if (tid == 0) {
         double wmax = 0.0;
@@ -262,29 +282,25 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(int b, const double* __re
         s_thresh = (double)b * kEps * wmax;
     }
     __syncthreads();
-    __shared__ double s_inv;
     for (int j = 0; j < b && s_bad == 0; ++j) {
-        const double d = A[j * ld + j];
-        if (!isfinite(d) || !(d > s_thresh)) {
-            __syncthreads();
-            if (tid == 0) s_bad = isfinite(d) ? 1 : 2;
-            __syncthreads();
-            break;
-        }
-        // one thread does the scalar FP64 work (a warp-wide sqrt/divide costs the
-        // 2-lane FP64 pipe as much as 32 of them)
         if (tid == 0) {
-            const double ljj = sqrt(d);
-            A[j * ld + j] = ljj;
-            s_inv = 1.0 / ljj;
+            const double d = A[j * ld + j];
+            if (!isfinite(d) || !(d > s_thresh)) {
+                s_bad = isfinite(d) ? 1 : 2;
+            } else {
+                const double y = rsqrt_fp64(d);
+                A[j * ld + j] = d * y;  // L_jj
+                dinv[j] = y;
+            }
         }
         __syncthreads();
-        const double inv = s_inv;
-        for (int i = j + 1 + tid; i < b; i += blockDim.x) A[i * ld + j] *= inv;
+        if (s_bad) break;
+        const double inv = dinv[j];
+        for (int i = j + 1 + tid; i < b; i += nt) A[i * ld + j] *= inv;
         __syncthreads();
         const int nn = b - j - 1;
         const int cnt = nn * (nn + 1) / 2;
-        for (int idx = tid; idx < cnt; idx += blockDim.x) {
+        for (int idx = tid; idx < cnt; idx += nt) {
             int ii, kk;
             tri_decode(idx, ii, kk);
             const int i = j + 1 + ii, k = j + 1 + kk;
@@ -294,36 +310,33 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(int b, const double* __re
     }
     if (s_bad) {
         if (tid == 0) atomicOr(&status[s_bad == 2 ? kStNonfinite : kStBreakdown], 1);
-        for (int idx = tid; idx < b * b; idx += blockDim.x) {
+        for (int idx = tid; idx < b * b; idx += nt) {
             const double v = (idx / b == idx % b) ? 1.0 : 0.0;
             Lt[idx] = v;
             Mt[idx] = v;
         }
         return;
     }
-    // Lt = L^T (upper)
-    for (int idx = tid; idx < b * b; idx += blockDim.x) {
-        const int i = idx / b, j = idx % b;
-        Lt[idx] = (j >= i) ? A[j * ld + i] : 0.0;
-    }
-    __syncthreads();
-    // in-place inverse of the lower triangle
-    for (int j = b - 1; j >= 0; --j) {
-        if (tid == 0) A[j * ld + j] = 1.0 / A[j * ld + j];
-        for (int i = j + 1 + tid; i < b; i += blockDim.x) tmp[i] = A[i * ld + j];
+    // X = L^{-1}: for k = 0..b-1, row k of X (columns c <= k) is scaled by 1/L_kk and
+    // is then final; rows i > k take X[i][c] -= L[i][k] X[k][c].  X[i][c] (c < i) is
+    // held at A[c][i]; the diagonal of X is dinv.
+    for (int k = 0; k < b; ++k) {
+        const double ik = dinv[k];
+        for (int c = tid; c < k; c += nt) A[c * ld + k] *= ik;
         __syncthreads();
-        const double ajj = -A[j * ld + j];
-        for (int i = j + 1 + tid; i < b; i += blockDim.x) {
-            double acc = 0.0;
-            for (int k = j + 1; k <= i; ++k) acc = fma(A[i * ld + k], tmp[k], acc);
-            A[i * ld + j] = ajj * acc;
+        const int rows = b - k - 1, cols = k + 1;
+        for (int idx = tid; idx < rows * cols; idx += nt) {
+            const int i = k + 1 + idx / cols, c = idx % cols;
+            const double xkc = (c == k) ? ik : A[c * ld + k];
+            A[c * ld + i] = fma(-A[i * ld + k], xkc, A[c * ld + i]);
         }
         __syncthreads();
     }
-    // Mt = L^{-T} (upper)
-    for (int idx = tid; idx < b * b; idx += blockDim.x) {
+    // Lt = L^T and Mt = L^{-T} = X^T, both upper
+    for (int idx = tid; idx < b * b; idx += nt) {
         const int i = idx / b, j = idx % b;
-        Mt[idx] = (j >= i) ? A[j * ld + i] : 0.0;
+        Lt[idx] = (j >= i) ? A[j * ld + i] : 0.0;
+        Mt[idx] = (j > i) ? A[i * ld + j] : (j == i ? dinv[i] : 0.0);
     }
 }
 

@@ -151,18 +151,19 @@ __global__ void __launch_bounds__(256) oz_slice_rows_kernel(int64_t R, int64_t K
 }
 
 // Rows slicer with one fixed exponent e for every row (an orthonormal basis: every
-// entry below 2^e in magnitude), over a window of K columns of S (R x K, lds) written
-// to columns [0, K) of planes (already offset to the window).  A row holding an entry
-// at or above 2^e, or Inf/NaN, gets the exponent of a non-finite row.
-__global__ void __launch_bounds__(256) oz_slice_rows_fixed_kernel(int64_t R, int64_t K, const double* __restrict__ S,
-                                                                  int64_t lds, __nv_bfloat16* __restrict__ planes,
-                                                                  int64_t ldk, int64_t pstride, int e,
-                                                                  int* __restrict__ eexp) {
-    const int64_t halfk = (K + 1) / 2;
+// entry below 2^e in magnitude), over the columns [a0, a1) of S (R x cols, lds), a0
+// even so that every 4-byte pair store is aligned (a column a0 - 1 or a1 slices
+// again the source's own value, or zero past the last column).  A row holding an
+// entry at or above 2^e, or Inf/NaN, gets the exponent of a non-finite row.
+__global__ void __launch_bounds__(256) oz_slice_rows_fixed_kernel(int64_t R, int64_t cols, int64_t a0, int64_t a1,
+                                                                  const double* __restrict__ S, int64_t lds,
+                                                                  __nv_bfloat16* __restrict__ planes, int64_t ldk,
+                                                                  int64_t pstride, int e, int* __restrict__ eexp) {
+    const int64_t halfk = (a1 - a0 + 1) / 2;
     const int64_t tot = R * halfk;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = t / halfk, k = 2 * (t % halfk);
-        const double x0 = S[i * lds + k], x1 = k + 1 < K ? S[i * lds + k + 1] : 0.0;
+        const int64_t i = t / halfk, k = a0 + 2 * (t % halfk);
+        const double x0 = k < cols ? S[i * lds + k] : 0.0, x1 = k + 1 < cols ? S[i * lds + k + 1] : 0.0;
         if (oz_exp(x0) > e || oz_exp(x1) > e) eexp[i] = kOzNanExp;
         int da[kOzDig], db[kOzDig];
         oz_digits(x0, e, da);
@@ -508,17 +509,32 @@ __global__ void oz_fixup_kernel(OzArgs a) {
     }
     __syncthreads();
     if (s_c0 == s_c1 && KB <= (int64_t)kOzChunk * kOzFlushChunks) return;  // written by its CTA
+    // the partial tile of each contributing CTA (in CTA order)
+    __shared__ int64_t s_slot[kOzWave];
+    const int nc = s_c1 - s_c0 + 1;
+    for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+        const int cc = s_c0 + j;
+        const int seg = (int)(t - oz_lo(cc, a) / KB);
+        s_slot[j] = ((int64_t)cc * a.maxseg + seg) * kOzM * kOzN;
+    }
+    __syncthreads();
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= kOzM * kOzN) return;
     const int r = idx / kOzN, cl = idx % kOzN;
     const int mt = (int)(t / a.NT), nt = (int)(t % a.NT);
     const int64_t row = (int64_t)mt * kOzM + r, col = (int64_t)nt * kOzN + cl;
     if (row >= a.M || col >= a.N) return;
+    // eight loads in flight, added in CTA order (the same sum as a sequential loop)
     double acc = 0.0;
-    for (int cc = s_c0; cc <= s_c1; ++cc) {
-        const int seg = (int)(t - oz_lo(cc, a) / KB);
-        acc += a.partial[(((int64_t)cc * a.maxseg + seg) * kOzM + r) * kOzN + cl];
+    int j = 0;
+    for (; j + 8 <= nc; j += 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = a.partial[s_slot[j + u] + idx];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += v[u];
     }
+    for (; j < nc; ++j) acc += a.partial[s_slot[j] + idx];
     oz_store(a, row, col, acc);
 }
 
@@ -800,11 +816,12 @@ int oz_cache_slice(tsvd_handle* h, OzCache& c, int64_t c0, int64_t c1, cudaStrea
                 h->launches++;
                 oz_fill_kernel<<<(unsigned)((c.rows + 255) / 256), 256, 0, st>>>(c.rows, c.fixed_exp, c.exps);
             }
-            const int64_t tot = c.rows * ((c1 - c0 + 1) / 2);
+            const int64_t a0 = c0 & ~int64_t(1), a1 = (c1 + 1) & ~int64_t(1);  // a1 <= ldk (a multiple of 8)
+            const int64_t tot = c.rows * ((a1 - a0) / 2);
             const int64_t blocks = std::min<int64_t>((tot + 255) / 256, (int64_t)h->sm_count * 32);
             h->launches++;
             oz_slice_rows_fixed_kernel<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, st>>>(
-                c.rows, c1 - c0, c.src + c0, c.ld, c.planes + c0, c.ldk, c.pstride, c.fixed_exp, c.exps);
+                c.rows, c.cols, a0, a1, c.src, c.ld, c.planes, c.ldk, c.pstride, c.fixed_exp, c.exps);
             TSVD_TRY_CUDA(cudaGetLastError());
         } else {
             // per-row exponents need the whole rows at once
@@ -813,6 +830,20 @@ int oz_cache_slice(tsvd_handle* h, OzCache& c, int64_t c0, int64_t c1, cudaStrea
         }
     }
     c.valid = c1;
+    return TSVD_OK;
+}
+
+int oz_cache_truncate(tsvd_handle* h, OzCache& c, int64_t v, cudaStream_t st) {
+    if (v >= c.valid) return TSVD_OK;
+    c.valid = v < 0 ? 0 : v;
+    if (!c.cols_layout && c.fixed_exp != kOzNoFixedExp) {
+        // a row's exponent may carry the mark of an entry out of range in the columns
+        // dropped here (a block that was not orthonormal yet): start again from the
+        // fixed exponent; the dropped columns are sliced again when rewritten
+        h->launches++;
+        oz_fill_kernel<<<(unsigned)((c.rows + 255) / 256), 256, 0, st>>>(c.rows, c.fixed_exp, c.exps);
+        TSVD_TRY_CUDA(cudaGetLastError());
+    }
     return TSVD_OK;
 }
 

@@ -286,6 +286,8 @@ size_t oz_cache_bytes(int64_t rows, int64_t cols, bool cols_layout);
 void oz_cache_carve(OzCache& c, Arena& ar, const double* src, int64_t ld, int64_t rows, int64_t cols,
                     bool cols_layout, int fixed_exp);
 int oz_cache_slice(tsvd_handle* h, OzCache& c, int64_t c0, int64_t c1, cudaStream_t st);
+// Columns from v on are about to be rewritten: valid = min(valid, v).
+int oz_cache_truncate(tsvd_handle* h, OzCache& c, int64_t v, cudaStream_t st);
 const OzCache* oz_find_cache(const tsvd_handle* h, const double* X, int64_t ldx, int64_t rows, int64_t s,
                              bool cols_layout);
 // Registers caches with the handle for its lifetime.
