@@ -27,13 +27,16 @@
 // rounded once to FP64: normwise FP64 accuracy (checked against exact products
 // in the CPU tests of the scheme and on the GPU).
 //
-// Layout: every operand is sliced into 7 BF16 planes stored K-major,
-// [7][rows][ld] (ld = K rounded up to 8), by one of two slicing kernels:
+// Layout: every operand is sliced into 7 BF16 digit planes stored K-block major
+// (the 7 planes of each 16-wide K block are [7][rows][16], so one TMA box reads
+// contiguous runs), by one of two slicing kernels:
 //   rows  the source rows are the stored rows (A = X of X M: one exponent per
 //         source row, computed by the warp that slices the row);
 //   cols  the source columns are the stored rows (A = X^T and B = Z of X^T Z,
 //         B = M of X M: one exponent per source column, from a column-max pass
 //         with atomicMax, then a tiled transpose).
+// Operands that many products read (a Lanczos basis, a dense A) keep their planes
+// in a cache that the owner extends block by block.
 // The product kernel (one CTA per SM, 320 threads) is the TMA / tcgen05
 // pipeline of the split-BF16 product: warp 0 loads 3-D boxes (16 K x rows x 7
 // planes, 32-byte swizzle) of both operands into a 5-stage ring, warp 1 owns 512
@@ -125,12 +128,32 @@ __device__ inline __nv_bfloat162 oz_pack(int d0, int d1, int p) {
     return __floats2bfloat162_rn((float)d0 * s, (float)d1 * s);  // exact: |d| <= 128
 }
 
+// Global layout of the digit planes: K-block major.  Element (digit p, stored row r,
+// column k) of an operand with Ra allocated stored rows sits at
+//   ((k / 16) * 7 + p) * Ra * 16 + r * 16 + k % 16,
+// so the 7 planes of one 16-wide K block are [7][Ra][16] and a TMA box of 16 K x
+// 128 rows x 7 planes reads 7 contiguous runs of 4 KB.  Columns past K up to the
+// next multiple of 16 hold zeros.
+__host__ __device__ inline int64_t oz_off(int64_t Ra, int64_t r, int64_t k, int p) {
+    return ((k >> 4) * kOzDig + p) * Ra * 16 + r * 16 + (k & 15);
+}
+__host__ __device__ inline int64_t oz_k16(int64_t K) { return (K + 15) / 16 * 16; }
+
+// Stores the digits of (x0, x1) at columns (k, k + 1), k even, of stored row r.
+__device__ inline void oz_store_pair(__nv_bfloat16* planes, int64_t Ra, int64_t r, int64_t k, const int* da,
+                                     const int* db) {
+    __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(planes + oz_off(Ra, r, k, 0));
+#pragma unroll
+    for (int p = 0; p < kOzDig; ++p) dst[p * Ra * 8] = oz_pack(da[p], db[p], p);  // plane step Ra*16 elements
+}
+
 // Rows slicer: row i of S (R x K, lds) -> stored row i; one warp per row.
-__global__ void __launch_bounds__(256) oz_slice_rows_kernel(int64_t R, int64_t K, const double* __restrict__ S,
+__global__ void __launch_bounds__(256, 4) oz_slice_rows_kernel(int64_t R, int64_t K, const double* __restrict__ S,
                                                             int64_t lds, __nv_bfloat16* __restrict__ planes,
-                                                            int64_t ldk, int64_t pstride, int* __restrict__ eexp) {
+                                                            int64_t Ra, int* __restrict__ eexp) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t K16 = oz_k16(K);
     for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < R; i += nw) {
         const double* src = S + i * lds;
         int e = kOzZeroExp;
@@ -139,38 +162,47 @@ __global__ void __launch_bounds__(256) oz_slice_rows_kernel(int64_t R, int64_t K
         for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
         e = oz_norm_exp(e);
         if (lane == 0) eexp[i] = e;
-        for (int64_t k = 2 * lane; k < K; k += 64) {
+        for (int64_t k = 2 * lane; k < K16; k += 64) {
             int da[kOzDig], db[kOzDig];
-            oz_digits(src[k], e, da);
+            oz_digits(k < K ? src[k] : 0.0, e, da);
             oz_digits(k + 1 < K ? src[k + 1] : 0.0, e, db);
-            __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(planes + i * ldk + k);
-#pragma unroll
-            for (int p = 0; p < kOzDig; ++p) dst[p * (pstride / 2)] = oz_pack(da[p], db[p], p);
+            oz_store_pair(planes, Ra, i, k, da, db);
         }
     }
 }
 
 // Rows slicer with one fixed exponent e for every row (an orthonormal basis: every
-// entry below 2^e in magnitude), over the columns [a0, a1) of S (R x cols, lds), a0
-// even so that every 4-byte pair store is aligned (a column a0 - 1 or a1 slices
-// again the source's own value, or zero past the last column).  A row holding an
-// entry at or above 2^e, or Inf/NaN, gets the exponent of a non-finite row.
-__global__ void __launch_bounds__(256) oz_slice_rows_fixed_kernel(int64_t R, int64_t cols, int64_t a0, int64_t a1,
+// entry below 2^e in magnitude), over the columns [a0, a1) of S (R rows, lds), a0
+// even and a1 a multiple of 16; columns from c1 on are written as zeros (a column
+// a0 - 1 < c1 is sliced again with its own value).  A row holding an entry at or
+// above 2^e, or Inf/NaN, gets the exponent of a non-finite row.
+__global__ void __launch_bounds__(256) oz_slice_rows_fixed_kernel(int64_t R, int64_t a0, int64_t a1, int64_t c1,
                                                                   const double* __restrict__ S, int64_t lds,
-                                                                  __nv_bfloat16* __restrict__ planes, int64_t ldk,
-                                                                  int64_t pstride, int e, int* __restrict__ eexp) {
-    const int64_t halfk = (a1 - a0 + 1) / 2;
+                                                                  __nv_bfloat16* __restrict__ planes, int64_t Ra,
+                                                                  int e, int* __restrict__ eexp) {
+    const int64_t halfk = (a1 - a0) / 2;
     const int64_t tot = R * halfk;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = t / halfk, k = a0 + 2 * (t % halfk);
-        const double x0 = k < cols ? S[i * lds + k] : 0.0, x1 = k + 1 < cols ? S[i * lds + k + 1] : 0.0;
+        const double x0 = k < c1 ? S[i * lds + k] : 0.0, x1 = k + 1 < c1 ? S[i * lds + k + 1] : 0.0;
         if (oz_exp(x0) > e || oz_exp(x1) > e) eexp[i] = kOzNanExp;
         int da[kOzDig], db[kOzDig];
         oz_digits(x0, e, da);
         oz_digits(x1, e, db);
-        __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(planes + i * ldk + k);
-#pragma unroll
-        for (int p = 0; p < kOzDig; ++p) dst[p * (pstride / 2)] = oz_pack(da[p], db[p], p);
+        oz_store_pair(planes, Ra, i, k, da, db);
+    }
+}
+
+// Zeros of columns [v, v16) of every stored row (rows layout; v16 a multiple of 16).
+__global__ void oz_zero_cols_kernel(int64_t R, int64_t v, int64_t v16, __nv_bfloat16* __restrict__ planes,
+                                    int64_t Ra) {
+    const int64_t w = v16 - v;
+    const int64_t tot = R * w * kOzDig;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+        const int p = (int)(t % kOzDig);
+        const int64_t rest = t / kOzDig;
+        const int64_t i = rest / w, k = v + rest % w;
+        planes[oz_off(Ra, i, k, p)] = __float2bfloat16_rn(0.0f);
     }
 }
 
@@ -194,11 +226,12 @@ __global__ void __launch_bounds__(256) oz_colmax_kernel(int64_t K, int64_t R, co
     }
 }
 
-// Cols slicer: column j of S (K x R, lds) -> stored row j, tiles of 64 k x 32 j.
+// Cols slicer: column j of S (K x R, lds) -> stored row r0 + j, tiles of 64 k x 32 j,
+// zeros past K up to the next multiple of 16.
 __global__ void __launch_bounds__(256) oz_slice_cols_kernel(int64_t K, int64_t R, const double* __restrict__ S,
                                                             int64_t lds, int upper, const int* __restrict__ eexp,
-                                                            __nv_bfloat16* __restrict__ planes, int64_t ldk,
-                                                            int64_t pstride) {
+                                                            __nv_bfloat16* __restrict__ planes, int64_t Ra,
+                                                            int64_t r0) {
     __shared__ double tile[64][33];
     const int64_t k0 = (int64_t)blockIdx.x * 64, j0 = (int64_t)blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -211,7 +244,7 @@ __global__ void __launch_bounds__(256) oz_slice_cols_kernel(int64_t K, int64_t R
     __syncthreads();
     const int kp = tx;  // k pair within the tile
     const int64_t k = k0 + 2 * kp;
-    if (k >= ldk) return;
+    if (k >= oz_k16(K)) return;
     for (int jj = ty; jj < 32; jj += 8) {
         const int64_t j = j0 + jj;
         if (j >= R) break;
@@ -219,9 +252,7 @@ __global__ void __launch_bounds__(256) oz_slice_cols_kernel(int64_t K, int64_t R
         int da[kOzDig], db[kOzDig];
         oz_digits(tile[2 * kp][jj], e, da);
         oz_digits(tile[2 * kp + 1][jj], e, db);
-        __nv_bfloat162* dst = reinterpret_cast<__nv_bfloat162*>(planes + j * ldk + k);
-#pragma unroll
-        for (int p = 0; p < kOzDig; ++p) dst[p * (pstride / 2)] = oz_pack(da[p], db[p], p);
+        oz_store_pair(planes, Ra, r0 + j, k, da, db);
     }
 }
 
@@ -320,12 +351,12 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                 if (it >= kOzStages) ok = mbar_wait(empty(st), (uint32_t)(((it / kOzStages) - 1) & 1), abort_flag);
                 if (!ok) break;
                 const int64_t t = i / KB;
-                const int kx = (int)((i - t * KB) * kOzBK);
+                const int kz = (int)((i - t * KB) * kOzDig);  // the 7 planes of K block i - t KB
                 const int mt = (int)(t / a.NT), nt = (int)(t % a.NT);
                 const uint32_t sA = base + (uint32_t)st * kOzStageBytes;
                 mbar_arrive_expect_tx(full(st), stage_tx);
-                tma_load_3d(sA, &tmA, kx, mt * kOzM, 0, full(st));
-                tma_load_3d(sA + kOzDig * kOzPlaneA, &tmB, kx, nt * kOzN, 0, full(st));
+                tma_load_3d(sA, &tmA, 0, mt * kOzM, kz, full(st));
+                tma_load_3d(sA + kOzDig * kOzPlaneA, &tmB, 0, nt * kOzN, kz, full(st));
             }
             if (!ok) {
                 atomicOr(&a.status[kStTimeout], 1);
@@ -572,39 +603,51 @@ OzPlan oz_plan(int64_t M, int64_t N, int64_t K) {
     return p;
 }
 
-inline int64_t oz_ld(int64_t K) { return (K + 7) / 8 * 8; }
 inline size_t oz_planes_bytes(int64_t rows, int64_t K) {
-    return align256((size_t)kOzDig * (size_t)rows * (size_t)oz_ld(K) * 2);
+    return align256((size_t)kOzDig * (size_t)rows * (size_t)oz_k16(K) * 2);
+}
+
+// 3-D tensor map of one operand: dims {16, rows, 7 x K blocks}, strides {32 B,
+// Ra x 32 B}, box 16 x box_rows x 7, 32-byte swizzle (rows past `rows` read zeros).
+bool make_oz_map(CUtensorMap* map, const void* planes, int64_t rows, int64_t Ra, int64_t K, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {16, (cuuint64_t)rows, (cuuint64_t)(kOzDig * (oz_k16(K) / 16))};
+    const cuuint64_t strides[2] = {32, (cuuint64_t)Ra * 32};
+    const cuuint32_t box[3] = {16u, (cuuint32_t)box_rows, (cuuint32_t)kOzDig};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(planes), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 inline size_t oz_partial_bytes(const OzPlan& p) {
     const bool needs = !p.aligned || p.KB > (int64_t)kOzChunk * kOzFlushChunks;
     return needs ? align256(sizeof(double) * (size_t)p.G * p.maxseg * kOzM * kOzN) : 0;
 }
 
-// One operand of the product kernel: `rows` stored rows of K digits each, planes
-// [7][.][ldk] with plane stride pstride (elements), one exponent per stored row.
+// One operand of the product kernel: `rows` stored rows of K digits each in the
+// K-block-major layout with Ra allocated stored rows, one exponent per stored row.
 struct OzView {
     const __nv_bfloat16* planes;
-    int64_t rows, K, ldk, pstride;
+    int64_t rows, K, Ra;
     const int* exps;
 };
 
 int oz_slice_rows(tsvd_handle* h, int64_t R, int64_t K, const double* S, int64_t lds, __nv_bfloat16* planes,
                   int* eexp, cudaStream_t st) {
     if (R == 0) return TSVD_OK;
-    const int64_t ldk = oz_ld(K);
     const int64_t blocks = std::min<int64_t>((R + 7) / 8, (int64_t)h->sm_count * 16);
     h->launches++;
-    oz_slice_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(R, K, S, lds, planes, ldk, R * ldk, eexp);
+    oz_slice_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(R, K, S, lds, planes, R, eexp);
     TSVD_TRY_CUDA(cudaGetLastError());
     return TSVD_OK;
 }
 
+// Ra: allocated stored rows of `planes` (default R); r0: first stored row written.
 int oz_slice_cols(tsvd_handle* h, int64_t K, int64_t R, const double* S, int64_t lds, bool upper,
-                  __nv_bfloat16* planes, int* eexp, cudaStream_t st, int64_t pstride = -1) {
+                  __nv_bfloat16* planes, int* eexp, cudaStream_t st, int64_t Ra = -1, int64_t r0 = 0) {
     if (R == 0) return TSVD_OK;
-    const int64_t ldk = oz_ld(K);
-    if (pstride < 0) pstride = R * ldk;
+    if (Ra < 0) Ra = R;
     const unsigned gx = (unsigned)((R + 31) / 32);
     int64_t gy = std::min<int64_t>((K + 255) / 256, std::max<int64_t>(1, (int64_t)h->sm_count * 8 / gx));
     const int64_t rows_per = (K + gy - 1) / gy;
@@ -614,8 +657,8 @@ int oz_slice_cols(tsvd_handle* h, int64_t K, int64_t R, const double* S, int64_t
     oz_colmax_kernel<<<dim3(gx, (unsigned)std::max<int64_t>(1, gy)), dim3(32, 8), 0, st>>>(K, R, S, lds,
                                                                                            upper ? 1 : 0, rows_per,
                                                                                            eexp);
-    const dim3 sg((unsigned)((oz_ld(K) + 63) / 64), gx);
-    oz_slice_cols_kernel<<<sg, 256, 0, st>>>(K, R, S, lds, upper ? 1 : 0, eexp, planes, ldk, pstride);
+    const dim3 sg((unsigned)((oz_k16(K) + 63) / 64), gx);
+    oz_slice_cols_kernel<<<sg, 256, 0, st>>>(K, R, S, lds, upper ? 1 : 0, eexp, planes, Ra, r0);
     TSVD_TRY_CUDA(cudaGetLastError());
     return TSVD_OK;
 }
@@ -629,8 +672,8 @@ int oz_run(tsvd_handle* h, const OzPlan& p, const OzView& va, const OzView& vb, 
         configured = h->device;
     }
     CUtensorMap mA, mB;
-    if (!make_plane_map(&mA, va.planes, p.K, p.M, va.ldk, kOzM, kOzDig, kOzBK, va.pstride)) return TSVD_ERR_CUDA;
-    if (!make_plane_map(&mB, vb.planes, p.K, p.N, vb.ldk, p.Npad, kOzDig, kOzBK, vb.pstride)) return TSVD_ERR_CUDA;
+    if (!make_oz_map(&mA, va.planes, p.M, va.Ra, p.K, kOzM)) return TSVD_ERR_CUDA;
+    if (!make_oz_map(&mB, vb.planes, p.N, vb.Ra, p.K, p.Npad)) return TSVD_ERR_CUDA;
     OzArgs a{};
     a.M = p.M;
     a.N = p.N;
@@ -685,14 +728,13 @@ size_t oz_ws_bound(int64_t qmax, int64_t smax, int64_t bmax) {
 namespace {
 
 OzView view_of(const __nv_bfloat16* planes, int64_t rows, int64_t K, const int* exps) {
-    return OzView{planes, rows, K, oz_ld(K), rows * oz_ld(K), exps};
+    return OzView{planes, rows, K, rows, exps};
 }
 
 // The cached planes of columns [0, s) (cols layout: stored rows) or of the first s
 // columns of every row (rows layout: K = s).
 OzView view_of_cache(const OzCache& c, int64_t s) {
-    return c.cols_layout ? OzView{c.planes, s, c.rows, c.ldk, c.pstride, c.exps}
-                         : OzView{c.planes, c.rows, s, c.ldk, c.pstride, c.exps};
+    return c.cols_layout ? OzView{c.planes, s, c.rows, c.cols, c.exps} : OzView{c.planes, c.rows, s, c.rows, c.exps};
 }
 
 }  // namespace
@@ -797,8 +839,6 @@ void oz_cache_carve(OzCache& c, Arena& ar, const double* src, int64_t ld, int64_
     c.cols_layout = cols_layout;
     c.fixed_exp = fixed_exp;
     const int64_t srows = cols_layout ? cols : rows, K = cols_layout ? rows : cols;
-    c.ldk = oz_ld(K);
-    c.pstride = srows * c.ldk;
     c.planes = reinterpret_cast<__nv_bfloat16*>(ar.take<char>(oz_planes_bytes(srows, K)));
     c.exps = ar.take<int>((size_t)srows);
     c.valid = 0;
@@ -809,19 +849,20 @@ int oz_cache_slice(tsvd_handle* h, OzCache& c, int64_t c0, int64_t c1, cudaStrea
     if (c1 > c0) {
         if (c.cols_layout) {
             // stored rows [c0, c1): the columns' own exponents
-            TSVD_TRY(oz_slice_cols(h, c.rows, c1 - c0, c.src + c0, c.ld, false, c.planes + c0 * c.ldk, c.exps + c0,
-                                   st, c.pstride));
+            TSVD_TRY(oz_slice_cols(h, c.rows, c1 - c0, c.src + c0, c.ld, false, c.planes, c.exps + c0, st, c.cols,
+                                   c0));
         } else if (c.fixed_exp != kOzNoFixedExp) {
             if (c0 == 0) {
                 h->launches++;
                 oz_fill_kernel<<<(unsigned)((c.rows + 255) / 256), 256, 0, st>>>(c.rows, c.fixed_exp, c.exps);
             }
-            const int64_t a0 = c0 & ~int64_t(1), a1 = (c1 + 1) & ~int64_t(1);  // a1 <= ldk (a multiple of 8)
+            // the window with the rest of its last 16-wide K block (written as zeros)
+            const int64_t a0 = c0 & ~int64_t(1), a1 = oz_k16(c1);
             const int64_t tot = c.rows * ((a1 - a0) / 2);
             const int64_t blocks = std::min<int64_t>((tot + 255) / 256, (int64_t)h->sm_count * 32);
             h->launches++;
             oz_slice_rows_fixed_kernel<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, st>>>(
-                c.rows, c.cols, a0, a1, c.src, c.ld, c.planes, c.ldk, c.pstride, c.fixed_exp, c.exps);
+                c.rows, a0, a1, c1, c.src, c.ld, c.planes, c.rows, c.fixed_exp, c.exps);
             TSVD_TRY_CUDA(cudaGetLastError());
         } else {
             // per-row exponents need the whole rows at once
@@ -836,6 +877,14 @@ int oz_cache_slice(tsvd_handle* h, OzCache& c, int64_t c0, int64_t c1, cudaStrea
 int oz_cache_truncate(tsvd_handle* h, OzCache& c, int64_t v, cudaStream_t st) {
     if (v >= c.valid) return TSVD_OK;
     c.valid = v < 0 ? 0 : v;
+    if (!c.cols_layout && c.valid % 16 != 0) {
+        // a product of the first `valid` columns reads the whole last K block: zero its rest
+        const int64_t tot = c.rows * (oz_k16(c.valid) - c.valid) * kOzDig;
+        h->launches++;
+        oz_zero_cols_kernel<<<(unsigned)std::min<int64_t>((tot + 255) / 256, (int64_t)h->sm_count * 32), 256, 0,
+                              st>>>(c.rows, c.valid, oz_k16(c.valid), c.planes, c.rows);
+        TSVD_TRY_CUDA(cudaGetLastError());
+    }
     if (!c.cols_layout && c.fixed_exp != kOzNoFixedExp) {
         // a row's exponent may carry the mark of an entry out of range in the columns
         // dropped here (a block that was not orthonormal yet): start again from the
@@ -850,7 +899,9 @@ int oz_cache_truncate(tsvd_handle* h, OzCache& c, int64_t v, cudaStream_t st) {
 const OzCache* oz_find_cache(const tsvd_handle* h, const double* X, int64_t ldx, int64_t rows, int64_t s,
                              bool cols_layout) {
     for (const OzCache* c : h->oz_caches)
-        if (c && c->src == X && c->ld == ldx && c->rows == rows && c->cols_layout == cols_layout && s <= c->valid)
+        if (c && c->src == X && c->ld == ldx && c->rows == rows && c->cols_layout == cols_layout && s <= c->valid &&
+            // rows layout: the product reads whole 16-wide K blocks, zero past `valid` only
+            (cols_layout || s == c->valid || s % 16 == 0))
             return c;
     return nullptr;
 }

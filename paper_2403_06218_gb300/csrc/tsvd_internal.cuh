@@ -14,9 +14,10 @@
 namespace tsvd {
 // A matrix whose BF16 digit planes (the FP64-accurate tensor-core product's input
 // form) are kept for many products: a Lanczos basis, or a dense A.  Rows layout:
-// planes [7][rows][ldk], one exponent per row (K = the columns); cols layout: planes
-// [7][cols][ldk], one exponent per column (K = the rows).  Columns [0, valid) are
-// current; the owner slices columns as it writes them (oz_cache_slice).
+// one stored row per row, one exponent per row (K = the columns); cols layout: one
+// stored row per column, one exponent per column (K = the rows); planes in the
+// K-block-major layout of k_oz.cu.  Columns [0, valid) are current; the owner slices
+// columns as it writes them (oz_cache_slice).
 struct OzCache {
     const double* src = nullptr;
     int64_t ld = 0, rows = 0, cols = 0;
@@ -24,7 +25,6 @@ struct OzCache {
     int fixed_exp = 0;  // rows layout of an orthonormal basis: every row's exponent
     __nv_bfloat16* planes = nullptr;
     int* exps = nullptr;
-    int64_t ldk = 0, pstride = 0;
     int64_t valid = 0;
 };
 constexpr int kOzNoFixedExp = -(1 << 30);
