@@ -13,8 +13,9 @@
 //    split into 7 balanced base-256 digits d_0..d_6 (F = sum d_p 2^(8(6-p)),
 //    |d_p| <= 128).  Digit p is stored as the BF16 value d_p 2^(-8p) (exact);
 //  * the 28 digit products with p + q <= 6 are issued as tcgen05 MMAs (M = 128,
-//    N <= 64, K = 16, FP32 accumulators in tensor memory), one accumulator per
-//    value of p + q (7 accumulators, 448 TMEM columns).  Over 128 consecutive k
+//    K = 16, FP32 accumulators in tensor memory), one accumulator per value of
+//    p + q (7 accumulators side by side, 448 TMEM columns); the products of one
+//    A digit plane with all its B planes form a single MMA of N up to 256.  Over 128 consecutive k
 //    each product is an integer times 2^(-8(p+q)) of magnitude <= 2^14 and each
 //    group sum T_{p+q} is an integer below 2^24, so every accumulation is exact
 //    whatever the tensor core's internal rounding;
@@ -40,7 +41,7 @@
 // The product kernel (one CTA per SM, 320 threads) is the TMA / tcgen05
 // pipeline of the split-BF16 product: warp 0 loads 3-D boxes (16 K x rows x 7
 // planes, 32-byte swizzle) of both operands into a 5-stage ring, warp 1 owns 512
-// TMEM columns and issues the 28 MMAs of each stage from one thread, warps 2-9
+// TMEM columns and issues the 10 MMAs of each stage from one thread, warps 2-9
 // drain the accumulators (two warps per 32 TMEM lanes, 32 columns each).  Work units (output tile, 32-wide K block) are split
 // over one wave of CTAs: whole tiles per CTA when there are more tiles than
 // CTAs (the epilogue writes the output itself), an even split of the K blocks
@@ -71,7 +72,7 @@ constexpr int kOzStageBytes = kOzDig * (kOzPlaneA + kOzPlaneB);  // 42 KB
 constexpr int kOzSmem = kOzStages * kOzStageBytes + 1024;
 constexpr int kOzChunk = 8;          // K blocks per exact accumulation (128 k)
 constexpr int kOzFlushChunks = 64;   // chunks between FP64 flushes of the integer sums (8192 k)
-constexpr int kOzSlots = 7;          // accumulators: p+q = 6, 5, 4, 3, 2, 1, 0
+constexpr int kOzSlots = 7;          // accumulators: p + q = 0 .. 6
 constexpr int kOzEpiWarps = 8;   // two per TMEM lane quarter, 32 columns each
 constexpr int kOzThreads = 64 + 32 * kOzEpiWarps;
 constexpr int kOzWave = 152;
@@ -369,7 +370,6 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer
-            const uint32_t idesc = idesc_bf16(kOzM, a.Npad);
             const uint32_t bstep = (uint32_t)(a.Npad * kOzRowB) >> 4;  // one B plane in 16-byte units
             int64_t it = 0, ch = 0;  // K blocks and chunks issued by this CTA
             bool ok = true;
@@ -387,24 +387,34 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                         const uint32_t sA = base + (uint32_t)st * kOzStageBytes;
                         const uint64_t a0 = sdesc_sw32(sA);
                         const uint64_t b0 = sdesc_sw32(sA + kOzDig * kOzPlaneA);
-                        // slot g accumulates the pairs (p, d - p), d = 6 - g; descriptor start
-                        // addresses advance by whole planes (16-byte units in the low field)
+                        // Digit plane p of A meets B planes q = 0 .. 6 - p; their products go to
+                        // the accumulators of p + q, which sit side by side in TMEM (slot d at
+                        // column d Npad), and the B planes sit side by side in shared memory, so
+                        // one MMA with N = (7 - p) Npad (cut at 256 columns) covers them all:
+                        // 10 MMAs a stage instead of 28, each reading its A plane once.  Slot p is
+                        // final once the MMAs of plane p are done (later planes start at p + 1).
 #pragma unroll
-                        for (int g = 0; g < kOzSlots; ++g) {
-                            if (first_kb && ch > 0) {
-                                // the epilogue has drained this accumulator of the previous chunk
-                                ok = mbar_wait(acce(g), (uint32_t)((ch - 1) & 1), abort_flag);
-                                if (!ok) break;
-                                fence_after();
-                            }
-                            const uint32_t d = tmem + (uint32_t)(g * kOzN);
+                        for (int p = 0; p < kOzDig; ++p) {
+                            const uint64_t ad = a0 + (uint64_t)(p * (kOzPlaneA >> 4));
 #pragma unroll
-                            for (int p = 0; p <= 6 - g; ++p) {
-                                const uint64_t ad = a0 + (uint64_t)(p * (kOzPlaneA >> 4));
-                                const uint64_t bd = b0 + (uint64_t)((6 - g - p) * bstep);
-                                mma_bf16(d, ad, bd, idesc, (first_kb && p == 0) ? 0u : 1u);
+                            for (int q0 = 0; q0 < kOzDig - p; q0 += 4) {
+                                const int cnt = min(4, kOzDig - p - q0);  // slots p + q0 .. + cnt - 1
+                                const bool piece_ok = cnt * a.Npad <= 256;
+                                if (first_kb && ch > 0 && p == 0) {
+                                    // the epilogue has drained these accumulators of the previous chunk
+                                    for (int dd = q0; dd < q0 + cnt && ok; ++dd) {
+                                        ok = mbar_wait(acce(dd), (uint32_t)((ch - 1) & 1), abort_flag);
+                                    }
+                                    if (!ok) break;
+                                    fence_after();
+                                }
+                                if (!piece_ok) continue;  // (Npad <= 64 and cnt <= 4 keep N <= 256)
+                                const uint32_t d = tmem + (uint32_t)((p + q0) * a.Npad);
+                                const uint64_t bd = b0 + (uint64_t)(q0 * bstep);
+                                mma_bf16(d, ad, bd, idesc_bf16(kOzM, cnt * a.Npad), (first_kb && p == 0) ? 0u : 1u);
                             }
-                            if (last_kb) commit(accf(g));
+                            if (!ok) break;
+                            if (last_kb) commit(accf(p));
                         }
                         if (!ok) break;
                         commit(empty(st));
@@ -461,10 +471,10 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                         break;
                     }
                     fence_after();
-                    // slot g holds T_d 2^(-8d), d = 6 - g, with T_d an integer below 2^24
-                    const int d = 6 - g;
+                    // slot g holds T_g 2^(-8g), T_g an integer below 2^24
+                    const int d = g;
                     const float mul = oz_digit_scale(-d);
-                    const uint32_t taddr = tmem + tlane + (uint32_t)(g * kOzN + cg * ncol);
+                    const uint32_t taddr = tmem + tlane + (uint32_t)(g * a.Npad + cg * ncol);
 #pragma unroll
                     for (int c0 = 0; c0 < 32; c0 += 16) {
                         if (c0 < ncol) {
