@@ -170,6 +170,19 @@ int tsvd_create(tsvd_handle** out, int device);
 /* Frees the handle (host memory only).  NULL is accepted. */
 int tsvd_destroy(tsvd_handle* h);
 
+/* Sets the limit, in SM clock cycles, of every bounded device-side wait of the
+ * kernels this handle launches afterwards: the mbarrier waits of the pipelined
+ * tensor-core products (tsvd_mm_bf16x6, tsvd_dense_mm_f64tc and the solvers'
+ * products) and the grid barrier of the block Jacobi SVD.  cycles <= 0 restores
+ * the default of 2e9 cycles (about 1 s).  A wait that reaches the limit gives
+ * up, the kernel stops its pipeline (copies and products already issued are
+ * waited for with the default limit, tensor memory is freed) and the call
+ * returns TSVD_ERR_TIMEOUT; the outputs are then undefined and the context stays
+ * usable.  This is a test hook (a short limit makes the waits run out without
+ * any fault); the paper has no counterpart.  TSVD_ERR_INVALID_ARG for a NULL
+ * handle. */
+int tsvd_set_wait_limit(tsvd_handle* h, long long cycles);
+
 /* Static text for a status code. */
 const char* tsvd_status_string(int status);
 

@@ -27,9 +27,11 @@ from .api import (  # noqa: F401
     cgs_qr,
     small_svd,
     handle,
+    wait_limit,
 )
 
 __all__ = [
     "TsvdError", "CsrMatrix", "SvdResult", "blanczos", "rsvd", "gaussian_block", "csr_transpose", "spmm",
-    "dense_mm", "svd_backward", "truncated_svd", "Bf16x3", "bf16x3_split", "mm_bf16x6", "cholqr2", "cgs_cqr2", "cgs_qr", "small_svd", "handle", "load", "LIB_PATH",
+    "dense_mm", "svd_backward", "truncated_svd", "Bf16x3", "bf16x3_split", "mm_bf16x6", "cholqr2", "cgs_cqr2", "cgs_qr", "small_svd", "handle", "wait_limit", "load",
+    "LIB_PATH",
 ]

@@ -94,6 +94,7 @@ SIGNATURES = [
     ("tsvd_default_opts", None, [C.POINTER(TsvdOpts)]),
     ("tsvd_create", _I, [C.POINTER(_P), _I]),
     ("tsvd_destroy", _I, [_P]),
+    ("tsvd_set_wait_limit", _I, [_P, C.c_longlong]),
     ("tsvd_status_string", C.c_char_p, [_I]),
     ("tsvd_workspace_size", _I, [C.POINTER(TsvdMatrix), _I, _I, _I, _I, C.POINTER(TsvdOpts), _PSZ]),
     ("tsvd_rsvd", _I, [_P, C.POINTER(TsvdMatrix), _I, _I, _I, C.c_uint64, C.POINTER(TsvdOpts), _P, _SZ,

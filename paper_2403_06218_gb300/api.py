@@ -17,6 +17,7 @@ returns numpy arrays copied back inside the call.
 
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import dataclasses
 from typing import Optional
@@ -47,6 +48,20 @@ def handle(device=None):
         h = hp
         _handles[idx] = h
     return h
+
+
+@contextlib.contextmanager
+def wait_limit(cycles: int, device=None):
+    """Within the block, every bounded device-side wait of the kernels launched through
+    this device's handle gives up after ``cycles`` SM clock cycles (a test hook: the
+    calls then return TSVD_ERR_TIMEOUT).  The default limit is restored on exit."""
+    lib = capi.load()
+    h = handle(device)
+    capi.check(lib.tsvd_set_wait_limit(h, int(cycles)), "tsvd_set_wait_limit")
+    try:
+        yield
+    finally:
+        capi.check(lib.tsvd_set_wait_limit(h, 0), "tsvd_set_wait_limit")
 
 
 def _stream_ptr(device) -> int:

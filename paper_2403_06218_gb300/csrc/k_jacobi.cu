@@ -25,20 +25,23 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxSweeps = 40;
-constexpr long long kMaxWaitCycles = 2000000000LL;  // bound of one barrier wait, ~1 s
 
 enum Ctl : int { kCtlCount = 0, kCtlGen = 1, kCtlErr = 2, kCtlSweeps = 3, kCtlRot = 8 };
 constexpr int kCtlWords = kCtlRot + kMaxSweeps;
 
 __device__ inline unsigned vload(const unsigned* p) { return *reinterpret_cast<const volatile unsigned*>(p); }
 
-// Grid-wide barrier for a cooperative launch (all CTAs co-resident).
-// Returns false once any CTA has timed out.
-__device__ bool grid_sync(unsigned* ctl) {
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident); one wait
+// gives up after max_wait SM clock cycles (the handle's limit, about 1 s by
+// default).  Returns false once any CTA has timed out; the answer is read once
+// per CTA (by thread 0, through shared memory), so every thread of a CTA takes
+// the same branch and none is left at a later __syncthreads.
+__device__ bool grid_sync(unsigned* ctl, long long max_wait) {
     if (gridDim.x == 1) {
         __syncthreads();
         return true;
     }
+    __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned g = vload(&ctl[kCtlGen]);
@@ -49,19 +52,20 @@ __device__ bool grid_sync(unsigned* ctl) {
             __threadfence();
             atomicAdd(&ctl[kCtlGen], 1u);
         } else {
-            // busy-wait (naps wake late), bounded by the SM clock: ~1 s at 2 GHz
+            // busy-wait (naps wake late), bounded by the SM clock
             const long long t0 = clock64();
             while (vload(&ctl[kCtlGen]) == g) {
-                if (clock64() - t0 > kMaxWaitCycles) {
+                if (clock64() - t0 > max_wait) {
                     atomicOr(&ctl[kCtlErr], 1u);
                     break;
                 }
             }
         }
         __threadfence();
+        s_ok = vload(&ctl[kCtlErr]) == 0u ? 1 : 0;
     }
     __syncthreads();
-    return vload(&ctl[kCtlErr]) == 0u;
+    return s_ok != 0;
 }
 
 __device__ inline double warp_sum(double v) {
@@ -98,7 +102,8 @@ constexpr int kMaxSlots = 64;  // column pairs one CTA owns per round
 // 2-lane FP64 pipe the same whatever its active lanes, so the scalar work of (B)
 // is done once per pair, and its divide and square roots run in FP32 (see (B)).
 __global__ void jacobi_sweep_kernel(int n, int npad, double* __restrict__ G, double* __restrict__ V,
-                                    double* __restrict__ nrm, unsigned* ctl, double tol, int ppb) {
+                                    double* __restrict__ nrm, unsigned* ctl, double tol, int ppb,
+                                    long long max_wait) {
     const double tol2 = tol * tol;
     __shared__ double s_gam[kMaxSlots], s_c[kMaxSlots], s_s[kMaxSlots];
     __shared__ int s_rot[kMaxSlots];
@@ -118,7 +123,7 @@ __global__ void jacobi_sweep_kernel(int n, int npad, double* __restrict__ G, dou
             if (lane == 0) nrm[c] = acc;
         }
         if (threadIdx.x == 0) s_any = 0;
-        if (!grid_sync(ctl)) return;
+        if (!grid_sync(ctl, max_wait)) return;
         for (int rnd = 0; rnd < npad - 1; ++rnd) {
             for (int slot = warp; slot < cnt; slot += wpb) {                     // (A)
                 const int pi = base + slot;
@@ -189,10 +194,10 @@ __global__ void jacobi_sweep_kernel(int n, int npad, double* __restrict__ G, dou
                     }
                 }
             }
-            if (!grid_sync(ctl)) return;
+            if (!grid_sync(ctl, max_wait)) return;
         }
         if (threadIdx.x == 0 && s_any) atomicAdd(&ctl[kCtlRot + sweep], 1u);
-        if (!grid_sync(ctl)) return;
+        if (!grid_sync(ctl, max_wait)) return;
         if (vload(&ctl[kCtlRot + sweep]) == 0u) {
             if (blockIdx.x == 0 && threadIdx.x == 0) ctl[kCtlSweeps] = (unsigned)(sweep + 1);
             return;
@@ -201,15 +206,25 @@ __global__ void jacobi_sweep_kernel(int n, int npad, double* __restrict__ G, dou
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl[kCtlSweeps] = (unsigned)kMaxSweeps;
 }
 
-// Block variant (right vectors not accumulated).  The npad columns form nblk
-// blocks of w columns; in each round of a round-robin over blocks, CTA c owns one
-// pair of blocks (I, J), copies their 2w columns into shared memory, applies all
-// w*w rotations between I and J (w mini-rounds of w disjoint pairs, one warp per
-// pair) -- plus, in the first round of a sweep, the rotations inside I and inside
-// J -- and writes the columns back.  Every column pair meets once per sweep, so a
-// sweep is still a full cyclic sweep, but it needs nblk - 1 grid barriers instead
-// of npad - 1 and the rotations of a block pair stay on chip.
-constexpr int kJGroup = 4;  // warps per column pair (disjoint row ranges)
+// Block variant (right vectors not accumulated): the block one-sided method of
+// Hari and Veselic with the rotations of a block pair done on its Gram matrix.
+// The npad columns form nblk blocks of W columns; in each round of a
+// round-robin over blocks, CTA c owns one pair of blocks (I, J).  It copies their
+// 2W columns C into shared memory and forms M = C^T C from them; one warp then
+// runs the round's rotations (the W mini-rounds of W disjoint pairs between I
+// and J, and in the first round of a sweep the W - 1 mini-rounds inside I and
+// inside J) two-sided on M, M <- R^T M R, accumulating Z = R_1 R_2 ...; finally
+// C Z replaces the columns.  Each rotation is computed from the same
+// alpha = |g_p|^2, beta = |g_q|^2, gamma = g_p.g_q as in the one-sided method
+// (M holds exactly the Gram matrix of the rotated columns, to rounding, and a
+// rotation's update of M has errors relative to the norms of the columns it
+// mixes, so the relative accuracy is that of the one-sided method).  Every column
+// pair meets once per sweep, as in a cyclic sweep; the n-length work of a round
+// is two small dense products (the Gram matrix and C Z) over all the CTA's
+// threads, and the sequential rotations touch only the 2W x 2W matrices of one
+// warp, so a sweep costs nblk - 1 grid barriers and about n warp-local
+// mini-rounds instead of n CTA-wide ones.
+constexpr int kJGThreads = 256;  // threads of the block kernel
 
 // Rotation parameters of one column pair from alpha = |g_p|^2, beta = |g_q|^2 and
 // gamma = g_p.g_q (Rutishauser's formulas); false when |gamma| <= tol sqrt(alpha beta).
@@ -253,132 +268,344 @@ __device__ inline T warp_sum_t(T v) {
     return v;
 }
 
-// Rotations of npair_local disjoint column pairs held in shared memory.  Each pair
-// is served by kJGroup warps over interleaved rows, so every SMSP holds several
-// warps to hide the arithmetic latency; the group's partial dot products are
-// summed in a fixed order (bitwise reproducible).
-template <typename T>
-__device__ inline void block_pair_rotations(T* cols, T* snrm, int n, int npair_local, const int* pp, const int* pq,
-                                            T tol2, T (*s_part)[kJGroup], T* s_c, T* s_s, int* s_rot, int* s_any) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
-    const int stride = 32 * kJGroup;
-    for (int slot = warp; slot < npair_local * kJGroup; slot += nw) {  // (A) partial gamma
-        const int k = slot / kJGroup, sub = slot % kJGroup;
-        const T* gp = cols + (size_t)pp[k] * n;
-        const T* gq = cols + (size_t)pq[k] * n;
-        T g0 = T(0), g1 = T(0);
-        int r = sub * 32 + lane;
-        for (; r + stride < n; r += 2 * stride) {
-            g0 = fma(gp[r], gq[r], g0);
-            g1 = fma(gp[r + stride], gq[r + stride], g1);
-        }
-        if (r < n) g0 = fma(gp[r], gq[r], g0);
-        const T ga = warp_sum_t<T>(g0 + g1);
-        if (lane == 0) s_part[k][sub] = ga;
-    }
-    __syncthreads();
-    if (warp == 0) {  // (B) rotation parameters, one lane per pair
-        for (int k = lane; k < npair_local; k += 32) {
-            T ga = T(0);
-#pragma unroll
-            for (int t = 0; t < kJGroup; ++t) ga += s_part[k][t];
-            const T al = snrm[pp[k]], be = snrm[pq[k]];
-            T c, sn, t;
-            const bool rot = rot_params(al, be, ga, tol2, c, sn, t);
-            if (rot) {
-                s_c[k] = c;
-                s_s[k] = sn;
-                snrm[pp[k]] = fma(-t, ga, al);
-                snrm[pq[k]] = fma(t, ga, be);
-                *s_any = 1;
-            }
-            s_rot[k] = rot ? 1 : 0;
-        }
-    }
-    __syncthreads();
-    for (int slot = warp; slot < npair_local * kJGroup; slot += nw) {  // (C) rotate
-        const int k = slot / kJGroup, sub = slot % kJGroup;
-        if (!s_rot[k]) continue;
-        const T c = s_c[k], sn = s_s[k];
-        T* gp = cols + (size_t)pp[k] * n;
-        T* gq = cols + (size_t)pq[k] * n;
-        for (int r = sub * 32 + lane; r < n; r += stride) {
-            const T x = gp[r], y = gq[r];
-            gp[r] = fma(c, x, -sn * y);
-            gq[r] = fma(sn, x, c * y);
-        }
-    }
-    __syncthreads();
+// Column stride (elements) of the block's columns in shared memory: odd, so that
+// the same row of different columns falls in different banks.
+__host__ __device__ inline int gram_ld(int n) { return n | 1; }
+
+template <typename T, int W>
+__host__ __device__ constexpr size_t gram_smem(int n) {
+    return sizeof(T) * (size_t)(2 * W) * (size_t)gram_ld(n);
 }
 
-constexpr int kJBlkMaxW = 8;
-
-template <typename T>
-__global__ void jacobi_block_kernel(int n, int npad, int w, T* __restrict__ G, T* __restrict__ nrm, unsigned* ctl,
-                                    T tol) {
-    extern __shared__ __align__(16) unsigned char jsm_raw[];
-    T* cols = reinterpret_cast<T*>(jsm_raw);  // 2w columns of n
-    T* snrm = cols + (size_t)2 * w * n;       // their squared norms
-    __shared__ T s_part[kJBlkMaxW][kJGroup], s_c[kJBlkMaxW], s_s[kJBlkMaxW];
-    __shared__ int s_rot[kJBlkMaxW], s_pp[kJBlkMaxW], s_pq[kJBlkMaxW];
-    __shared__ int s_any;
-    const T tol2 = tol * tol;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int nblk = npad / w;
-    for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
-        for (int c = blockIdx.x * nw + warp; c < npad; c += gridDim.x * nw) {  // exact norms
-            const T* g = G + (int64_t)c * n;
-            T acc = T(0);
-            for (int r = lane; r < n; r += 32) acc = fma(g[r], g[r], acc);
-            acc = warp_sum_t<T>(acc);
-            if (lane == 0) nrm[c] = acc;
+// M = C^T C for the 2W columns in shared memory (stride ld): the tiles on and
+// above the diagonal of TM x TM register tiles (the others mirrored), each tile's
+// rows split over S interleaved lane slices that a shuffle tree sums in a fixed
+// order.  A diagonal tile is symmetric bit for bit (x_a x_b = x_b x_a in every fma).
+template <typename T, int W>
+__device__ inline void gram_form(const T* cols, int n, int ld, T (*M)[2 * W + 1]) {
+    constexpr int W2 = 2 * W;
+    constexpr int TM = W2 >= 32 ? 8 : (W2 >= 8 ? 4 : 2);
+    constexpr int NTS = W2 / TM;
+    constexpr int NT = NTS * (NTS + 1) / 2;
+    constexpr int S0 = kJGThreads / NT;
+    constexpr int S = S0 >= 32 ? 32 : (S0 >= 16 ? 16 : (S0 >= 8 ? 8 : (S0 >= 4 ? 4 : (S0 >= 2 ? 2 : 1))));
+    static_assert(NT * S <= kJGThreads, "Gram tiling exceeds the block");
+    const int t = threadIdx.x;
+    int u = t / S;
+    const int s = t % S;
+    // lanes of one warp share their tile group: a warp is wholly in or out when S
+    // divides 32; with S < 32 the last warp may be partly idle, so idle lanes run the
+    // loop on tile 0 and drop their sums (the shuffles need every lane)
+    const bool live = u < NT;
+    if (!live) u = 0;
+    if ((t & ~31) >= NT * S) return;  // whole idle warps
+    int ti = 0;
+    while (u >= NTS - ti) {
+        u -= NTS - ti;
+        ++ti;
+    }
+    const int tj = ti + u;
+    T acc[TM][TM];
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TM; ++b) acc[a][b] = T(0);
+    const T* ca = cols + (size_t)(ti * TM) * ld;
+    const T* cb = cols + (size_t)(tj * TM) * ld;
+    for (int r = s; r < n; r += S) {
+        T x[TM], y[TM];
+#pragma unroll
+        for (int a = 0; a < TM; ++a) {
+            x[a] = ca[(size_t)a * ld + r];
+            y[a] = cb[(size_t)a * ld + r];
         }
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+            for (int b = 0; b < TM; ++b) acc[a][b] = fma(x[a], y[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int b = 0; b < TM; ++b) {
+            T v = acc[a][b];
+#pragma unroll
+            for (int d = S / 2; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+            if (s == 0 && live) {
+                M[ti * TM + a][tj * TM + b] = v;
+                M[tj * TM + b][ti * TM + a] = v;
+            }
+        }
+}
+
+// Row stride of Z: 16-byte rows, so that the C Z products read a row of Z four
+// floats (two doubles) at a time.
+template <typename T, int W>
+__host__ __device__ constexpr int gram_zs() {
+    return 2 * W + (int)(16 / sizeof(T));
+}
+
+// acc[j] += x Z_k[j] for j < W2, Z_k a 16-byte aligned row (vector loads, broadcast
+// to the warp).
+template <typename T, int W2>
+__device__ inline void gram_axpy_row(T x, const T* zk, T* acc) {
+    if constexpr (sizeof(T) == 4 && W2 % 4 == 0) {
+#pragma unroll
+        for (int j = 0; j < W2; j += 4) {
+            const float4 z = *reinterpret_cast<const float4*>(zk + j);
+            acc[j] = fma(x, (T)z.x, acc[j]);
+            acc[j + 1] = fma(x, (T)z.y, acc[j + 1]);
+            acc[j + 2] = fma(x, (T)z.z, acc[j + 2]);
+            acc[j + 3] = fma(x, (T)z.w, acc[j + 3]);
+        }
+    } else if constexpr (sizeof(T) == 8 && W2 % 2 == 0) {
+#pragma unroll
+        for (int j = 0; j < W2; j += 2) {
+            const double2 z = *reinterpret_cast<const double2*>(zk + j);
+            acc[j] = fma(x, (T)z.x, acc[j]);
+            acc[j + 1] = fma(x, (T)z.y, acc[j + 1]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < W2; ++j) acc[j] = fma(x, zk[j], acc[j]);
+    }
+}
+
+// One mini-round on the block's Gram matrix by warp 0: npr disjoint pairs
+// (pp[k], pq[k]) rotated at once; M <- R^T M R and Z <- Z R.  Returns whether any
+// pair rotated (warp-uniform).
+template <typename T, int W>
+__device__ inline bool gram_mini_round(T (*M)[2 * W + 1], T (*Z)[gram_zs<T, W>()], const int* pp, const int* pq,
+                                       int npr,
+                                       T tol2, T* s_c, T* s_s, int* s_rot) {
+    constexpr int W2 = 2 * W;
+    const int lane = threadIdx.x & 31;
+    int rot = 0;
+    if (lane < npr) {
+        const int p = pp[lane], q = pq[lane];
+        T c = T(1), sn = T(0), t = T(0);
+        rot = rot_params(M[p][p], M[q][q], M[p][q], tol2, c, sn, t) ? 1 : 0;
+        s_c[lane] = c;
+        s_s[lane] = sn;
+        s_rot[lane] = rot;
+    }
+    const bool any = __any_sync(kFull, rot != 0);
+    if (!any) return false;
+    __syncwarp();
+    if (lane < W2) {  // columns: lane = row of M and of Z
+        for (int k = 0; k < npr; ++k) {
+            if (!s_rot[k]) continue;
+            const int p = pp[k], q = pq[k];
+            const T c = s_c[k], sn = s_s[k];
+            const T x = M[lane][p], y = M[lane][q];
+            M[lane][p] = fma(c, x, -sn * y);
+            M[lane][q] = fma(sn, x, c * y);
+            const T u = Z[lane][p], v = Z[lane][q];
+            Z[lane][p] = fma(c, u, -sn * v);
+            Z[lane][q] = fma(sn, u, c * v);
+        }
+    }
+    __syncwarp();
+    if (lane < W2) {  // rows: lane = column of M
+        for (int k = 0; k < npr; ++k) {
+            if (!s_rot[k]) continue;
+            const int p = pp[k], q = pq[k];
+            const T c = s_c[k], sn = s_s[k];
+            const T x = M[p][lane], y = M[q][lane];
+            M[p][lane] = fma(c, x, -sn * y);
+            M[q][lane] = fma(sn, x, c * y);
+        }
+    }
+    __syncwarp();
+    return true;
+}
+
+// The W mini-rounds between the blocks (pairs (k, W + (k + mr) mod W)) by warp 0
+// with the block's Gram matrix in registers: lane r < 2W holds row r of M and of
+// Z, the J half of each row stored cyclically shifted by mr (position k holds
+// column W + (k + mr) mod W), so that pair k always meets positions k and k of a
+// row and no register is indexed at run time.  A rotation acts on the columns of
+// M and Z within each lane, and on the rows of M between lane k and its partner
+// lane by shuffles.  M and Z enter and leave in shared memory.  Returns whether
+// any pair rotated (warp-uniform).
+template <typename T, int W>
+__device__ inline bool gram_rounds_ij(T (*M)[2 * W + 1], T (*Z)[gram_zs<T, W>()], T tol2) {
+    constexpr int W2 = 2 * W;
+    const int lane = threadIdx.x & 31;
+    const int r = lane < W2 ? lane : 0;  // lanes past 2W mirror row 0 (their results are dropped)
+    T A[W], J[W], ZA[W], ZJ[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        A[j] = M[r][j];
+        J[j] = M[r][W + j];
+        ZA[j] = Z[r][j];
+        ZJ[j] = Z[r][W + j];
+    }
+    bool any = false;
+    for (int mr = 0; mr < W; ++mr) {
+        // own diagonal entry: column r sits at A[r] (r < W) or at J[(r - W - mr) mod W]
+        const int jpos = r < W ? r : (r - W - mr + 2 * W) % W;
+        T d = T(0), g = T(0);
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            if (j == jpos) d = r < W ? A[j] : J[j];
+            if (j == r) g = J[j];  // M[k][q_k] for the pair's I lane k = r
+        }
+        const int partner = r < W ? W + (r + mr) % W : jpos;
+        const T dq = __shfl_sync(kFull, d, partner);
+        T c = T(1), sn = T(0), t = T(0);
+        int rot = 0;
+        if (lane < W) rot = rot_params(d, dq, g, tol2, c, sn, t) ? 1 : 0;
+        if (!rot) {
+            c = T(1);
+            sn = T(0);
+        }
+        if (!__any_sync(kFull, rot != 0)) {
+            // no pair rotates: only the shift of the J halves
+        } else {
+            any = true;
+            // columns (p, q) = (k, W + (k + mr) mod W) of this lane's rows of M and Z
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                const T ck = __shfl_sync(kFull, c, k), sk = __shfl_sync(kFull, sn, k);
+                const T x = A[k], y = J[k];
+                A[k] = fma(ck, x, -sk * y);
+                J[k] = fma(sk, x, ck * y);
+                const T u = ZA[k], v = ZJ[k];
+                ZA[k] = fma(ck, u, -sk * v);
+                ZJ[k] = fma(sk, u, ck * v);
+            }
+            // rows p and q of M: lane p (r < W) and lane q exchange their rows
+            const int pair = r < W ? r : jpos;
+            const T cp = __shfl_sync(kFull, c, pair), sp = __shfl_sync(kFull, sn, pair);
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                const T oa = __shfl_sync(kFull, A[k], partner), oj = __shfl_sync(kFull, J[k], partner);
+                if (r < W) {
+                    A[k] = fma(cp, A[k], -sp * oa);
+                    J[k] = fma(cp, J[k], -sp * oj);
+                } else {
+                    A[k] = fma(sp, oa, cp * A[k]);
+                    J[k] = fma(sp, oj, cp * J[k]);
+                }
+            }
+        }
+        // next mini-round: position k of the J halves moves to column W + (k + mr + 1) mod W
+        const T j0 = J[0], z0 = ZJ[0];
+#pragma unroll
+        for (int k = 0; k < W - 1; ++k) {
+            J[k] = J[k + 1];
+            ZJ[k] = ZJ[k + 1];
+        }
+        J[W - 1] = j0;
+        ZJ[W - 1] = z0;
+    }
+    __syncwarp();
+    if (lane < W2) {
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            M[r][j] = A[j];
+            M[r][W + j] = J[j];
+            Z[r][j] = ZA[j];
+            Z[r][W + j] = ZJ[j];
+        }
+    }
+    __syncwarp();
+    return any;
+}
+
+template <typename T, int W>
+__global__ void __launch_bounds__(kJGThreads, 1) jacobi_gram_kernel(int n, int npad, T* __restrict__ G,
+                                                                 T* __restrict__ V, unsigned* ctl, T tol,
+                                                                 long long max_wait) {
+    constexpr int W2 = 2 * W;
+    static_assert(W2 <= 32 && (W == 1 || W % 2 == 0), "block width: 1 or even, at most 16");
+    extern __shared__ __align__(16) unsigned char jsm_raw[];
+    T* cols = reinterpret_cast<T*>(jsm_raw);  // 2W columns, stride ld
+    __shared__ T M[W2][W2 + 1];
+    __shared__ __align__(16) T Z[W2][gram_zs<T, W>()];
+    __shared__ T s_c[W], s_s[W];
+    __shared__ int s_rot[W], s_pp[W], s_pq[W];
+    __shared__ int s_any, s_rnd;
+    const T tol2 = tol * tol;
+    const int ld = gram_ld(n);
+    const int nblk = npad / W;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
         if (threadIdx.x == 0) s_any = 0;
-        if (!grid_sync(ctl)) return;
         for (int rnd = 0; rnd < nblk - 1; ++rnd) {
             const int bi = rr_player(blockIdx.x, rnd, nblk), bj = rr_player(nblk - 1 - blockIdx.x, rnd, nblk);
-            // load the 2w columns (I first, then J) and their norms
-            for (int idx = threadIdx.x; idx < 2 * w * n; idx += blockDim.x) {
-                const int lc = idx / n, r = idx % n;
-                const int gc = lc < w ? bi * w + lc : bj * w + (lc - w);
-                cols[idx] = G[(int64_t)gc * n + r];
+            for (int r = threadIdx.x; r < n; r += blockDim.x) {  // all 2W loads in flight at once
+                T v[W2];
+#pragma unroll
+                for (int k = 0; k < W2; ++k) v[k] = G[(int64_t)(k < W ? bi * W + k : bj * W + (k - W)) * n + r];
+#pragma unroll
+                for (int k = 0; k < W2; ++k) cols[(size_t)k * ld + r] = v[k];
             }
-            for (int lc = threadIdx.x; lc < 2 * w; lc += blockDim.x)
-                snrm[lc] = nrm[lc < w ? bi * w + lc : bj * w + (lc - w)];
             __syncthreads();
-            if (rnd == 0) {
-                // rotations inside I and inside J: round-robin on w players, w/2 pairs per block
-                for (int mr = 0; mr < w - 1; ++mr) {
-                    if (threadIdx.x < w) {
-                        const int k = threadIdx.x, blk = k / (w / 2), seat = k % (w / 2);
-                        const int a = rr_player(seat, mr, w), b2 = rr_player(w - 1 - seat, mr, w);
-                        s_pp[k] = blk * w + min(a, b2);
-                        s_pq[k] = blk * w + max(a, b2);
+            gram_form<T, W>(cols, n, ld, M);
+            __syncthreads();
+            if (warp == 0) {
+                for (int e = lane; e < W2 * W2; e += 32) Z[e / W2][e % W2] = (e / W2 == e % W2) ? T(1) : T(0);
+                __syncwarp();
+                bool any = false;
+                if (rnd == 0) {
+                    // rotations inside I and inside J: round-robin on W players, W/2 pairs per block
+                    for (int mr = 0; mr < W - 1; ++mr) {
+                        if (lane < W) {
+                            const int blk = lane / (W / 2), seat = lane % (W / 2);
+                            const int a = rr_player(seat, mr, W), b2 = rr_player(W - 1 - seat, mr, W);
+                            s_pp[lane] = blk * W + min(a, b2);
+                            s_pq[lane] = blk * W + max(a, b2);
+                        }
+                        __syncwarp();
+                        any |= gram_mini_round<T, W>(M, Z, s_pp, s_pq, W, tol2, s_c, s_s, s_rot);
+                        __syncwarp();
                     }
-                    __syncthreads();
-                    block_pair_rotations<T>(cols, snrm, n, w, s_pp, s_pq, tol2, s_part, s_c, s_s, s_rot, &s_any);
+                }
+                any |= gram_rounds_ij<T, W>(M, Z, tol2);  // rotations between I and J
+                if (lane == 0) {
+                    s_rnd = any ? 1 : 0;
+                    if (any) s_any = 1;
                 }
             }
-            for (int mr = 0; mr < w; ++mr) {  // rotations between I and J
-                if (threadIdx.x < w) {
-                    s_pp[threadIdx.x] = threadIdx.x;
-                    s_pq[threadIdx.x] = w + (threadIdx.x + mr) % w;
+            __syncthreads();
+            if (s_rnd) {
+                // C Z: thread r computes row r of the 2W rotated columns (2W independent sums)
+                for (int r = threadIdx.x; r < n; r += blockDim.x) {
+                    T acc[W2];
+#pragma unroll
+                    for (int j = 0; j < W2; ++j) acc[j] = T(0);
+#pragma unroll 2
+                    for (int k = 0; k < W2; ++k) {
+                        const T x = cols[(size_t)k * ld + r];
+                        gram_axpy_row<T, W2>(x, Z[k], acc);
+                    }
+#pragma unroll
+                    for (int j = 0; j < W2; ++j) G[(int64_t)(j < W ? bi * W + j : bj * W + (j - W)) * n + r] = acc[j];
                 }
-                __syncthreads();
-                block_pair_rotations<T>(cols, snrm, n, w, s_pp, s_pq, tol2, s_part, s_c, s_s, s_rot, &s_any);
+                if (V) {
+                    // accumulated rotations (npad x npad, column-major): V <- V Z on the
+                    // block pair's columns, read from global memory row by row
+                    for (int r = threadIdx.x; r < npad; r += blockDim.x) {
+                        T acc[W2];
+#pragma unroll
+                        for (int j = 0; j < W2; ++j) acc[j] = T(0);
+#pragma unroll 4
+                        for (int k = 0; k < W2; ++k) {
+                            const T x = V[(int64_t)(k < W ? bi * W + k : bj * W + (k - W)) * npad + r];
+                            gram_axpy_row<T, W2>(x, Z[k], acc);
+                        }
+#pragma unroll
+                        for (int j = 0; j < W2; ++j)
+                            V[(int64_t)(j < W ? bi * W + j : bj * W + (j - W)) * npad + r] = acc[j];
+                    }
+                }
             }
-            for (int idx = threadIdx.x; idx < 2 * w * n; idx += blockDim.x) {
-                const int lc = idx / n, r = idx % n;
-                const int gc = lc < w ? bi * w + lc : bj * w + (lc - w);
-                G[(int64_t)gc * n + r] = cols[idx];
-            }
-            for (int lc = threadIdx.x; lc < 2 * w; lc += blockDim.x)
-                nrm[lc < w ? bi * w + lc : bj * w + (lc - w)] = snrm[lc];
-            if (!grid_sync(ctl)) return;
+            if (!grid_sync(ctl, max_wait)) return;
         }
         if (threadIdx.x == 0 && s_any) atomicAdd(&ctl[kCtlRot + sweep], 1u);
-        if (!grid_sync(ctl)) return;
+        if (!grid_sync(ctl, max_wait)) return;
         if (vload(&ctl[kCtlRot + sweep]) == 0u) {
             if (blockIdx.x == 0 && threadIdx.x == 0) ctl[kCtlSweeps] = (unsigned)(sweep + 1);
             return;
@@ -387,35 +614,36 @@ __global__ void jacobi_block_kernel(int n, int npad, int w, T* __restrict__ G, T
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl[kCtlSweeps] = (unsigned)kMaxSweeps;
 }
 
-// FP32 copy of B^T in the Jacobi layout: column c of G32 (ld n) = row c of B,
-// padded columns zero.
-__global__ void jacobi_init_t32_kernel(int n, int npad, const double* __restrict__ B, int64_t ldb,
-                                       float* __restrict__ G) {
-    const int64_t tot = (int64_t)npad * n;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+
+// FP32 copy of B in the Jacobi layout: column c of G32 (ld n) = column c of B
+// (B row-major), padded columns zero; V32 (npad x npad, column-major) = I.
+__global__ void jacobi_init32_kernel(int n, int npad, const double* __restrict__ B, int64_t ldb,
+                                     float* __restrict__ G, float* __restrict__ V) {
+    const int64_t tot = (int64_t)npad * n, totv = (int64_t)npad * npad;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot + totv;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(idx / n), r = (int)(idx % n);
-        G[idx] = c < n ? (float)B[(int64_t)c * ldb + r] : 0.0f;
+        if (idx < tot) {
+            const int c = (int)(idx / n), r = (int)(idx % n);
+            G[idx] = c < n ? (float)B[(int64_t)r * ldb + c] : 0.0f;
+        } else {
+            const int64_t k = idx - tot;
+            V[k] = (k / npad == k % npad) ? 1.0f : 0.0f;
+        }
     }
 }
 
-// V (n x n row-major, FP64): V[:, j] = G32[:, j] / |G32[:, j]| for j < n; a zero
-// column leaves e_j.  Also hands a timeout of the FP32 sweeps to the status words.
-__global__ void __launch_bounds__(128) jacobi_vinit_kernel(int n, const float* __restrict__ G, double* __restrict__ V,
-                                                           const unsigned* ctl32, int* status) {
-    __shared__ double red[4];
-    const int j = blockIdx.x;
-    const float* g = G + (int64_t)j * n;
-    double acc = 0.0;
-    for (int r = threadIdx.x; r < n; r += blockDim.x) acc = fma((double)g[r], (double)g[r], acc);
-    acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    const double nr = sqrt(red[0] + red[1] + red[2] + red[3]);
-    const double inv = nr > 0.0 ? 1.0 / nr : 0.0;
-    for (int r = threadIdx.x; r < n; r += blockDim.x)
-        V[(int64_t)r * n + j] = nr > 0.0 ? (double)g[r] * inv : (r == j ? 1.0 : 0.0);
-    if (j == 0 && threadIdx.x == 0 && ctl32[kCtlErr]) atomicOr(&status[kStTimeout], 1);
+// V (n x n row-major, FP64) = the leading n x n block of the accumulated FP32
+// rotations V32 (the right singular directions of B to FP32 accuracy).  Also hands
+// a timeout of the FP32 sweeps to the status words.
+__global__ void jacobi_vinit_kernel(int n, int npad, const float* __restrict__ V32, double* __restrict__ V,
+                                    const unsigned* ctl32, int* status) {
+    const int64_t tot = (int64_t)n * n;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(idx / n), c = (int)(idx % n);
+        V[idx] = (double)V32[(int64_t)c * npad + r];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && ctl32[kCtlErr]) atomicOr(&status[kStTimeout], 1);
 }
 
 // After the polar iterations: if V^T V (in T) is not the identity to 1e-12, V = I
@@ -596,25 +824,21 @@ __global__ void __launch_bounds__(128) jacobi_vfix_kernel(int n, const double* _
 static int block_width(int n) {
     if (n <= 64 || n > 1024) return 0;
     int w = 1;
-    while (w < kJBlkMaxW && (n + 2 * w - 1) / (2 * w) > 152) w *= 2;
+    while (w < 8 && (n + 2 * w - 1) / (2 * w) > 152) w *= 2;
     return w;
 }
-// Block width of the FP32 preconditioning sweeps: the widest blocks (fewest rounds).
-constexpr int kJW32 = kJBlkMaxW;
+// Block width of the FP32 preconditioning sweeps: the widest blocks (fewest rounds;
+// FP32 work is cheap next to the rounds' latency).
+constexpr int kJW32 = 16;
 
 static int pad_to(int n, int w) { return (n + 2 * w - 1) / (2 * w) * (2 * w); }
-
-template <typename T>
-static size_t block_smem(int n, int w) {
-    return sizeof(T) * ((size_t)2 * w * n + 2 * w);
-}
 
 // Buffers of one small SVD, carved identically by the sizing and the run.
 struct SvdBufs {
     double *G, *V, *nrm, *sig, *part;
     int* perm;
     unsigned *ctl, *ctl32;
-    float *G32, *nrm32;
+    float *G32, *V32;
     double *Vp, *Tm, *Y;  // preconditioner: V, V^T V, B V (n x n row-major)
     void* oz;
     size_t oz_bytes;
@@ -633,7 +857,7 @@ static SvdBufs carve_svd(Arena& ar, int n, int npad, int nv, bool precond) {
         const int np32 = pad_to(n, kJW32);
         b.ctl32 = ar.take<unsigned>(kCtlWords);
         b.G32 = ar.take<float>((size_t)n * np32);
-        b.nrm32 = ar.take<float>(np32);
+        b.V32 = ar.take<float>((size_t)np32 * np32);
         b.Vp = ar.take<double>((size_t)n * n);
         b.Tm = ar.take<double>((size_t)n * n);
         b.Y = ar.take<double>((size_t)n * n);
@@ -677,31 +901,47 @@ static int jacobi_grid(const tsvd_handle* h, int npairs, int& block) {
     return nb;
 }
 
-// Cooperative launch of the block-Jacobi sweeps on G (n x npad, column-major) in T.
-template <typename T>
-static int run_block_sweeps(tsvd_handle* h, int n, int npad, int w, T* G, T* nrm, unsigned* ctl, T tol,
-                            cudaStream_t st) {
-    const int nb = npad / w / 2;
-    const size_t smem = block_smem<T>(n, w);
+// Cooperative launch of the block-Jacobi sweeps on G (n x npad, column-major) in T
+// with blocks of W columns.
+template <typename T, int W>
+static int launch_gram(tsvd_handle* h, int n, int npad, T* G, unsigned* ctl, T tol, cudaStream_t st, T* V) {
+    const int nb = npad / W / 2;
+    const size_t smem = gram_smem<T, W>(n);
     static thread_local int configured = -1;
     if (configured != h->device) {
-        TSVD_TRY_CUDA(cudaFuncSetAttribute(jacobi_block_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)block_smem<double>(1024, kJBlkMaxW)));
-        TSVD_TRY_CUDA(cudaFuncSetAttribute(jacobi_block_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)block_smem<float>(1024, kJBlkMaxW)));
+        TSVD_TRY_CUDA(cudaFuncSetAttribute(jacobi_gram_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)gram_smem<T, W>(1024)));
         configured = h->device;
     }
     int per_sm = 0;
-    TSVD_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_block_kernel<T>, 32 * w * kJGroup,
-                                                                smem));
+    TSVD_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_gram_kernel<T, W>, kJGThreads, smem));
     if (per_sm * h->sm_count < nb) return TSVD_ERR_UNSUPPORTED;
-    int nn = n, np = npad, ww = w;
+    int nn = n, np = npad;
     T t = tol;
-    void* args[] = {(void*)&nn, (void*)&np, (void*)&ww, (void*)&G, (void*)&nrm, (void*)&ctl, (void*)&t};
+    long long mw = h->max_wait;
+    void* args[] = {(void*)&nn, (void*)&np, (void*)&G, (void*)&V, (void*)&ctl, (void*)&t, (void*)&mw};
     h->launches++;
-    TSVD_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_block_kernel<T>, dim3(nb), dim3(32 * w * kJGroup),
-                                              args, smem, st));
+    TSVD_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_gram_kernel<T, W>, dim3(nb), dim3(kJGThreads), args,
+                                              smem, st));
     return TSVD_OK;
+}
+
+template <typename T>
+static int run_block_sweeps(tsvd_handle* h, int n, int npad, int w, T* G, unsigned* ctl, T tol, cudaStream_t st,
+                            T* V = nullptr) {
+    switch (w) {
+        case 1: return launch_gram<T, 1>(h, n, npad, G, ctl, tol, st, V);
+        case 2: return launch_gram<T, 2>(h, n, npad, G, ctl, tol, st, V);
+        case 4: return launch_gram<T, 4>(h, n, npad, G, ctl, tol, st, V);
+        case 8: return launch_gram<T, 8>(h, n, npad, G, ctl, tol, st, V);
+        default: return TSVD_ERR_UNSUPPORTED;
+    }
+}
+template <>
+int run_block_sweeps<float>(tsvd_handle* h, int n, int npad, int w, float* G, unsigned* ctl, float tol,
+                            cudaStream_t st, float* V) {
+    if (w != kJW32) return TSVD_ERR_UNSUPPORTED;
+    return launch_gram<float, kJW32>(h, n, npad, G, ctl, tol, st, V);
 }
 
 int small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* Ubar, double* sigma, double* Vbar, int nv,
@@ -723,17 +963,21 @@ int small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* Ubar,
         const double tol = (double)(n > 16 ? n : 16) * kEps;
         double* Vacc = accumulate ? V : nullptr;
         if (w > 0) {
-            // (1) FP32 block-Jacobi sweeps on B^T: its orthogonalised columns are the right
-            //     singular directions of B to FP32 accuracy
+            // (1) FP32 block-Jacobi sweeps on B with the rotations accumulated in V32: the
+            //     right singular directions of B, orthogonal to FP32 rounding (so B V has
+            //     columns orthogonal to about eps32 sigma_1 / sigma_j, where the right
+            //     vectors from the orthogonalised columns of B^T would leave couplings of
+            //     eps32 (sigma_1 / sigma_j)^2 and more FP64 sweeps)
             const int np32 = pad_to(n, kJW32);
             TSVD_TRY_CUDA(cudaMemsetAsync(bf.ctl32, 0, sizeof(unsigned) * kCtlWords, st));
             h->launches += 2;
-            jacobi_init_t32_kernel<<<(unsigned)std::min<int64_t>(4096, ((int64_t)n * np32 + 255) / 256), 256, 0, st>>>(
-                n, np32, B, ldb, bf.G32);
+            jacobi_init32_kernel<<<(unsigned)std::min<int64_t>(4096, ((int64_t)(n + np32) * np32 + 255) / 256), 256, 0,
+                                   st>>>(n, np32, B, ldb, bf.G32, bf.V32);
             TSVD_TRY_CUDA(cudaGetLastError());
             const float tol32 = (float)(n > 16 ? n : 16) * 5.9604645e-08f;  // n 2^-24
-            TSVD_TRY(run_block_sweeps<float>(h, n, np32, kJW32, bf.G32, bf.nrm32, bf.ctl32, tol32, st));
-            jacobi_vinit_kernel<<<n, 128, 0, st>>>(n, bf.G32, bf.Vp, bf.ctl32, status);
+            TSVD_TRY(run_block_sweeps<float>(h, n, np32, kJW32, bf.G32, bf.ctl32, tol32, st, bf.V32));
+            jacobi_vinit_kernel<<<(unsigned)std::min<int64_t>(4096, ((int64_t)n * n + 255) / 256), 256, 0, st>>>(
+                n, np32, bf.V32, bf.Vp, bf.ctl32, status);
             TSVD_TRY_CUDA(cudaGetLastError());
             // (2) V orthogonal to FP64 rounding: two polar (Newton-Schulz) steps
             //     V <- V (3 I - V^T V) / 2 with FP64-accurate tensor-core products, then a
@@ -754,7 +998,7 @@ int small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* Ubar,
             h->launches++;
             jacobi_init_kernel<<<ib, 256, 0, st>>>(n, npad, bf.Y, n, G, V);
             TSVD_TRY_CUDA(cudaGetLastError());
-            TSVD_TRY(run_block_sweeps<double>(h, n, npad, w, G, bf.nrm, bf.ctl, tol, st));
+            TSVD_TRY(run_block_sweeps<double>(h, n, npad, w, G, bf.ctl, tol, st));
         } else {
             h->launches++;
             jacobi_init_kernel<<<ib, 256, 0, st>>>(n, npad, B, ldb, G, V);
@@ -766,15 +1010,16 @@ int small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* Ubar,
             const int ppb = (npairs + nblocks - 1) / nblocks;
             h->launches++;
             if (nblocks == 1) {
-                jacobi_sweep_kernel<<<1, block, 0, st>>>(n, npad, G, Vacc, bf.nrm, bf.ctl, tol, ppb);
+                jacobi_sweep_kernel<<<1, block, 0, st>>>(n, npad, G, Vacc, bf.nrm, bf.ctl, tol, ppb, h->max_wait);
                 TSVD_TRY_CUDA(cudaGetLastError());
             } else {
                 int nn = n, np = npad, pp = ppb;
                 double t = tol;
                 double* nrm = bf.nrm;
                 unsigned* ctl = bf.ctl;
+                long long mw = h->max_wait;
                 void* args[] = {(void*)&nn, (void*)&np, (void*)&G, (void*)&Vacc, (void*)&nrm, (void*)&ctl, (void*)&t,
-                                (void*)&pp};
+                                (void*)&pp, (void*)&mw};
                 TSVD_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)jacobi_sweep_kernel, dim3(nblocks), dim3(block),
                                                           args, 0, st));
             }

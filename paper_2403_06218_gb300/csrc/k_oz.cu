@@ -42,11 +42,13 @@
 // pipeline of the split-BF16 product: warp 0 loads 3-D boxes (16 K x rows x 7
 // planes, 32-byte swizzle) of both operands into a 5-stage ring, warp 1 owns 512
 // TMEM columns and issues the 10 MMAs of each stage from one thread, warps 2-9
-// drain the accumulators (two warps per 32 TMEM lanes, 32 columns each).  Work units (output tile, 32-wide K block) are split
-// over one wave of CTAs: whole tiles per CTA when there are more tiles than
-// CTAs (the epilogue writes the output itself), an even split of the K blocks
-// otherwise (partial tiles, added by a fix-up kernel in CTA order, so the
-// result is deterministic).  Every mbarrier wait is bounded.
+// drain the accumulators (two warps per 32 TMEM lanes, 32 columns each).  Work
+// units (output tile, 16-wide K block) are split evenly over one wave of CTAs,
+// so no CTA runs a third tile while the others idle (314 tiles on 152 SMs would
+// take three rounds for 2.07 rounds of work): a tile whose K range lies inside
+// one CTA's share is written by its epilogue, the few tiles cut between CTAs
+// leave partial tiles that a fix-up kernel adds in CTA order, so the result is
+// deterministic.  Every mbarrier wait is bounded.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -265,7 +267,7 @@ __global__ void oz_fill_kernel(int64_t n, int v, int* __restrict__ x) {
 // ---- the product kernel ------------------------------------------------------
 struct OzArgs {
     int64_t M, N, KB, tiles, total;
-    int NT, Npad, G, aligned, maxseg;
+    int NT, Npad, G, maxseg;
     const int* ea;
     const int* eb;
     double* out;  // C (direct tiles)
@@ -274,10 +276,11 @@ struct OzArgs {
     int symmetric;
     double* partial;  // [G][maxseg][128][64]
     int* status;
+    long long max_wait;  // limit of one pipeline wait (SM clock cycles)
 };
 
 __host__ __device__ inline int64_t oz_lo(int c, const OzArgs& a) {
-    return a.aligned ? ((int64_t)c * a.tiles / a.G) * a.KB : (int64_t)c * a.total / a.G;
+    return (int64_t)c * a.total / a.G;
 }
 
 // C = 2^(ea + eb - 14) (hi 2^-32 + lo 2^-40) in FP64.
@@ -349,7 +352,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             bool ok = true;
             for (int64_t i = lo; i < hi && ok; ++i, ++it) {
                 const int st = (int)(it % kOzStages);
-                if (it >= kOzStages) ok = mbar_wait(empty(st), (uint32_t)(((it / kOzStages) - 1) & 1), abort_flag);
+                if (it >= kOzStages) ok = mbar_wait(empty(st), (uint32_t)(((it / kOzStages) - 1) & 1), abort_flag, a.max_wait);
                 if (!ok) break;
                 const int64_t t = i / KB;
                 const int kz = (int)((i - t * KB) * kOzDig);  // the 7 planes of K block i - t KB
@@ -380,7 +383,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                     const int64_t ce = min(e, i + kOzChunk);
                     for (int64_t i0 = i; i < ce; ++i, ++it) {
                         const int st = (int)(it % kOzStages);
-                        ok = mbar_wait(full(st), (uint32_t)((it / kOzStages) & 1), abort_flag);
+                        ok = mbar_wait(full(st), (uint32_t)((it / kOzStages) & 1), abort_flag, a.max_wait);
                         if (!ok) break;
                         fence_after();
                         const bool first_kb = (i == i0), last_kb = (i + 1 == ce);
@@ -403,7 +406,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                                 if (first_kb && ch > 0 && p == 0) {
                                     // the epilogue has drained these accumulators of the previous chunk
                                     for (int dd = q0; dd < q0 + cnt && ok; ++dd) {
-                                        ok = mbar_wait(acce(dd), (uint32_t)((ch - 1) & 1), abort_flag);
+                                        ok = mbar_wait(acce(dd), (uint32_t)((ch - 1) & 1), abort_flag, a.max_wait);
                                     }
                                     if (!ok) break;
                                     fence_after();
@@ -460,7 +463,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                 const int64_t ce = min(e, i + kOzChunk);
                 for (int g = 0; g < kOzSlots; ++g) {
                     int w_ok = 1;
-                    if (lane == 0) w_ok = mbar_wait_sleep(accf(g), (uint32_t)(ch & 1), abort_flag) ? 1 : 0;
+                    if (lane == 0) w_ok = mbar_wait_sleep(accf(g), (uint32_t)(ch & 1), abort_flag, a.max_wait) ? 1 : 0;
                     w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
                     if (!w_ok) {
                         if (lane == 0) {
@@ -583,7 +586,6 @@ __global__ void oz_fixup_kernel(OzArgs a) {
 struct OzPlan {
     int64_t M, N, K, KB, tiles, total;
     int MT, NT, Npad, G, maxseg;
-    bool aligned;
 };
 
 OzPlan oz_plan(int64_t M, int64_t N, int64_t K) {
@@ -597,15 +599,13 @@ OzPlan oz_plan(int64_t M, int64_t N, int64_t K) {
     p.KB = std::max<int64_t>(1, (K + kOzBK - 1) / kOzBK);
     p.tiles = (int64_t)p.MT * p.NT;
     p.total = p.tiles * p.KB;
-    p.aligned = p.tiles >= kOzWave;
-    p.G = (int)std::min<int64_t>(kOzWave, p.aligned ? p.tiles : p.total);
+    p.G = (int)std::min<int64_t>(kOzWave, p.total);
     p.maxseg = 1;
     OzArgs a{};
     a.KB = p.KB;
     a.tiles = p.tiles;
     a.total = p.total;
     a.G = p.G;
-    a.aligned = p.aligned ? 1 : 0;
     for (int c = 0; c < p.G; ++c) {
         const int64_t lo = oz_lo(c, a), hi = oz_lo(c + 1, a);
         if (hi > lo) p.maxseg = std::max<int>(p.maxseg, (int)((hi - 1) / p.KB - lo / p.KB + 1));
@@ -631,8 +631,7 @@ bool make_oz_map(CUtensorMap* map, const void* planes, int64_t rows, int64_t Ra,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 inline size_t oz_partial_bytes(const OzPlan& p) {
-    const bool needs = !p.aligned || p.KB > (int64_t)kOzChunk * kOzFlushChunks;
-    return needs ? align256(sizeof(double) * (size_t)p.G * p.maxseg * kOzM * kOzN) : 0;
+    return align256(sizeof(double) * (size_t)p.G * p.maxseg * kOzM * kOzN);
 }
 
 // One operand of the product kernel: `rows` stored rows of K digits each in the
@@ -693,7 +692,6 @@ int oz_run(tsvd_handle* h, const OzPlan& p, const OzView& va, const OzView& vb, 
     a.NT = p.NT;
     a.Npad = p.Npad;
     a.G = p.G;
-    a.aligned = p.aligned ? 1 : 0;
     a.maxseg = p.maxseg;
     a.ea = va.exps;
     a.eb = vb.exps;
@@ -704,6 +702,7 @@ int oz_run(tsvd_handle* h, const OzPlan& p, const OzView& va, const OzView& vb, 
     a.symmetric = symmetric ? 1 : 0;
     a.partial = partial;
     a.status = status;
+    a.max_wait = h->max_wait;
     h->launches++;
     oz_gemm_kernel<<<p.G, kOzThreads, kOzSmem, st>>>(mA, mB, a);
     TSVD_TRY_CUDA(cudaGetLastError());

@@ -73,7 +73,8 @@ __host__ __device__ inline int64_t tc_lo(int64_t c, int64_t total, int G) { retu
 // ---- the product kernel ----------------------------------------------------
 __global__ void __launch_bounds__(kTcThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX, int Npad,
-                   int64_t KB, int64_t total, int G, int maxseg, float* __restrict__ partial, int* status) {
+                   int64_t KB, int64_t total, int G, int maxseg, float* __restrict__ partial, int* status,
+                   long long max_wait) {
     extern __shared__ uint8_t dsm[];
     __shared__ __align__(8) uint64_t bars[2 * kTcStages + 5];
     __shared__ uint32_t s_tmem;
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             bool ok = true;
             for (int64_t i = lo; i < hi && ok; ++i, ++it) {
                 const int st = (int)(it % kTcStages);
-                if (it >= kTcStages) ok = mbar_wait(empty(st), (uint32_t)(((it / kTcStages) - 1) & 1), abort_flag);
+                if (it >= kTcStages) ok = mbar_wait(empty(st), (uint32_t)(((it / kTcStages) - 1) & 1), abort_flag, max_wait);
                 if (!ok) break;
                 const int64_t t = i / KB;
                 const int kx = (int)((i - t * KB) * kTcBK);
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     const int64_t ce = min(e, i + kTcChunk);
                     const int a = (int)(g & 1);
                     if (g >= 2) {
-                        ok = mbar_wait(acce(a), (uint32_t)(((g >> 1) - 1) & 1), abort_flag);
+                        ok = mbar_wait(acce(a), (uint32_t)(((g >> 1) - 1) & 1), abort_flag, max_wait);
                         if (!ok) break;
                         fence_after();
                     }
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     uint32_t acc = 0;
                     for (; i < ce; ++i, ++it) {
                         const int st = (int)(it % kTcStages);
-                        ok = mbar_wait(full(st), (uint32_t)((it / kTcStages) & 1), abort_flag);
+                        ok = mbar_wait(full(st), (uint32_t)((it / kTcStages) & 1), abort_flag, max_wait);
                         if (!ok) break;
                         fence_after();
                         const uint32_t sA = base + (uint32_t)st * kTcStageBytes;
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             for (; i < e; i = min(e, i + kTcChunk), ++g) {
                 const int a = (int)(g & 1);
                 int w_ok = 1;
-                if (lane == 0) w_ok = mbar_wait(accf(a), (uint32_t)((g >> 1) & 1), abort_flag) ? 1 : 0;
+                if (lane == 0) w_ok = mbar_wait(accf(a), (uint32_t)((g >> 1) & 1), abort_flag, max_wait) ? 1 : 0;
                 w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
                 if (!w_ok) {
                     if (lane == 0) {
@@ -437,7 +438,7 @@ cudaError_t tc_mm(tsvd_handle* h, int64_t rows, int64_t cols, const void* pieces
         if (!make_map(&mX, xp, cols, wp, bf16x3_ld(cols), np)) return cudaErrorInvalidValue;
         h->launches += 2;
         tc_gemm_kernel<<<p.ctas, kTcThreads, kTcSmem, st>>>(mA, mX, np, p.kb, p.total, p.ctas, p.maxseg, part,
-                                                            status);
+                                                            status, h->max_wait);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         const dim3 fg((unsigned)((kTcM * wp + 255) / 256), (unsigned)p.tiles);

@@ -174,6 +174,12 @@ int tsvd_destroy(tsvd_handle* h) {
     return TSVD_OK;
 }
 
+int tsvd_set_wait_limit(tsvd_handle* h, long long cycles) {
+    if (!h) return TSVD_ERR_INVALID_ARG;
+    h->max_wait = cycles > 0 ? cycles : tsvd_handle{}.max_wait;
+    return TSVD_OK;
+}
+
 int tsvd_workspace_size(const tsvd_matrix* A, int method, int k, int a, int c, const tsvd_opts* opts, size_t* bytes) {
     if (!bytes) return TSVD_ERR_INVALID_ARG;
     tsvd_opts o;

@@ -54,6 +54,9 @@ struct tsvd_handle {
     int* oz_status = nullptr;
     // operands whose digit planes are kept for the current call (owned by the caller)
     std::vector<const tsvd::OzCache*> oz_caches;
+    // limit, in SM clock cycles, of one bounded wait of the pipelined product kernels
+    // and of the Jacobi grid barrier (2e9, about 1 s; tsvd_set_wait_limit lowers it)
+    long long max_wait = 2000000000LL;
 };
 
 namespace tsvd {

@@ -42,12 +42,28 @@ def test_reference_arm_prints_the_contract_line(capsys, monkeypatch, workload):
         assert str(bench.WORKLOADS[workload]["oracle_cycles"]) in cb["sample"]
 
 
-@pytest.mark.parametrize("workload", ["dense20k-lanczos", "powerlaw2m-lanczos-mixed"])
-def test_reference_arm_is_unavailable_where_the_oracle_is_not_run(capsys, monkeypatch, workload):
+def test_reference_arm_is_unavailable_where_the_oracle_is_not_run(capsys, monkeypatch):
     monkeypatch.delenv("RANK", raising=False)
-    assert bench.main(["--impl", "reference", "--workload", workload, "--steps", "1", "--warmup", "0"]) == 0
+    assert bench.main(["--impl", "reference", "--workload", "powerlaw2m-lanczos-mixed", "--steps", "1",
+                       "--warmup", "0"]) == 0
     line = _one_json_line(capsys)
     assert line["impl"] == "reference" and line["unavailable"]
+
+
+def test_reference_arm_runs_the_whole_oracle_solve_on_the_householder_matrix(capsys, monkeypatch):
+    """The dense workload's reference arm (a miniature of it here): the matrix built on
+    the host with the device generator's formula, the whole oracle solve per step, and
+    the same config dict as the GPU arm's line."""
+    monkeypatch.delenv("RANK", raising=False)
+    small = dict(bench.WORKLOADS["dense20k-lanczos"], m=700, n=500, k=8, b=16, r=4)
+    monkeypatch.setitem(bench.WORKLOADS, "dense20k-lanczos", small)
+    assert bench.main(["--impl", "reference", "--steps", "1", "--warmup", "0"]) == 0
+    line = _one_json_line(capsys)
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert "whole solve" in line["cpu_baseline"]["sample"]
+    assert line["config"] == {"workload": "dense20k-lanczos", **{k: v for k, v in small.items()
+                                                                  if k != "oracle_cycles"},
+                              "parallelism": "replicas1"}
 
 
 def test_every_lanczos_workload_the_oracle_runs_states_its_cycle_count():
@@ -90,6 +106,26 @@ def test_roofline_arithmetic(tsvd):
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert r["achieved"] == pytest.approx(6000.0) and r["peak"] == pytest.approx(hbm)
     assert r["frac"] == pytest.approx(6000.0 / hbm) and r["traffic"] is None
+
+    # dense FP64 A products are sliced products on the tensor cores: 28 BF16 digit-pair
+    # products per FP64 multiply-add, against the measured BF16 peak
+    dense = bench.WORKLOADS["dense20k-lanczos"]
+    bf16 = float(peaks.get("bf16_tflops", 1914.6))
+    r = bench._roofline(dense, ap, *_classes(ap, 10.0, 1e11, 6e9, 2))
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert r["fp64_equiv_tflops"] == pytest.approx(10.0)
+    assert r["achieved"] == pytest.approx(280.0) and r["frac"] == pytest.approx(280.0 / bf16)
+    # and in the mixed form they are the split-BF16 product, bound by HBM
+    r = bench._roofline(bench.WORKLOADS["dense20k-lanczos-mixed"], ap, *_classes(ap, 10.0, 1e11, 6e9, 2))
+    assert r["bound"] == "hbm"
+
+
+def test_default_workload_is_the_dense_20k_solve():
+    src = open(bench.__file__).read()
+    assert 'default="dense20k-lanczos"' in src
+    cfg = bench.WORKLOADS["dense20k-lanczos"]
+    assert (cfg["m"], cfg["n"], cfg["k"], cfg["b"], cfg["r"]) == (20_000, 20_000, 100, 128, 4)
+    assert cfg.get("precision", "fp64") == "fp64" and cfg["tol"] == 1e-6
 
 
 def test_clock_sampler_keeps_only_the_timed_window():

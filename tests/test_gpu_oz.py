@@ -105,7 +105,7 @@ def test_random_data_within_stated_bound(tsvd, torch_cuda, trans):
 
 
 @pytest.mark.parametrize("trans,m,n,w", [
-    (0, 20_000, 600, 64),     # tiles >= one wave: whole tiles per CTA, written by the epilogue
+    (0, 20_000, 600, 64),     # tiles > one wave: most tiles whole in one CTA (direct), the rest cut
     (0, 5_000, 1_100, 128),   # two 64-wide column tiles, split K blocks and the fix-up
     (1, 100_000, 576, 64),    # A^T X with K = 100,000 split over the CTAs (the projection shape)
     (1, 100_000, 64, 64),     # the Gram shape
