@@ -461,6 +461,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             bool stored = false;
             for (; i < e && ok; ++ch) {
                 const int64_t ce = min(e, i + kOzChunk);
+#pragma unroll
                 for (int g = 0; g < kOzSlots; ++g) {
                     int w_ok = 1;
                     if (lane == 0) w_ok = mbar_wait_sleep(accf(g), (uint32_t)(ch & 1), abort_flag, a.max_wait) ? 1 : 0;
@@ -474,30 +475,29 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                         break;
                     }
                     fence_after();
-                    // slot g holds T_g 2^(-8g), T_g an integer below 2^24
-                    const int d = g;
-                    const float mul = oz_digit_scale(-d);
+                    // slot g holds T_g 2^(-8g), T_g an integer below 2^24: read it in one
+                    // load and hand the accumulator back before converting, so the next
+                    // chunk's products into it need not wait for the conversion
                     const uint32_t taddr = tmem + tlane + (uint32_t)(g * a.Npad + cg * ncol);
-#pragma unroll
-                    for (int c0 = 0; c0 < 32; c0 += 16) {
-                        if (c0 < ncol) {
-                            float v[16];
-                            tmem_ld16(taddr + (uint32_t)c0, v);
-                            if (d <= 4) {
-#pragma unroll
-                                for (int q = 0; q < 16; ++q)
-                                    hi[c0 + q] += (long long)__float2int_rn(v[q] * mul) << (8 * (4 - d));
-                            } else if (d == 5) {
-#pragma unroll
-                                for (int q = 0; q < 16; ++q) lo[c0 + q] += __float2int_rn(v[q] * mul);
-                            } else {
-#pragma unroll
-                                for (int q = 0; q < 16; ++q) lo[c0 + q] += (__float2int_rn(v[q] * mul) + 128) >> 8;
-                            }
-                        }
-                    }
+                    float v[32];
+                    if (ncol == 32)
+                        tmem_ld32(taddr, v);
+                    else
+                        tmem_ld16(taddr, v);
                     fence_before();
                     mbar_arrive(acce(g));
+                    const float mul = oz_digit_scale(-g);
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        if (q < ncol) {
+                            if (g <= 4)
+                                hi[q] += (long long)__float2int_rn(v[q] * mul) << (8 * (4 - g));
+                            else if (g == 5)
+                                lo[q] += __float2int_rn(v[q] * mul);
+                            else
+                                lo[q] += (__float2int_rn(v[q] * mul) + 128) >> 8;
+                        }
+                    }
                 }
                 if (!ok) break;
                 i = ce;
