@@ -53,6 +53,7 @@ extern "C" {
 #define TSVD_ERR_WORKSPACE     (-4) /* workspace missing, too small or misaligned       */
 #define TSVD_ERR_TIMEOUT       (-5) /* a bounded device-side wait gave up               */
 #define TSVD_ERR_UNSUPPORTED   (-6) /* a size beyond this build's kernel limits         */
+#define TSVD_ERR_COMM          (-7) /* the row partition's reduction callback failed   */
 
 /* ---- enumerations ------------------------------------------------------ */
 #define TSVD_DENSE   0   /* tsvd_matrix.format: row-major dense                    */
@@ -97,6 +98,8 @@ typedef struct tsvd_matrix {
 
 /* tsvd_opts.flags bits */
 #define TSVD_FLAG_PROFILE  1   /* time every kernel class with CUDA events (tsvd_info.prof_*) */
+#define TSVD_FLAG_ROW_PARTITION 2 /* A is one process's row block (tsvd_set_row_partition):
+                                     never transposed; size the workspace with it too */
 
 /* Kernel classes reported by TSVD_FLAG_PROFILE (index into tsvd_info.prof_*). */
 #define TSVD_K_APROD    0   /* products with A or A^T: CSR SpMM (Table 1 SpMM), dense GEMM
@@ -158,6 +161,11 @@ typedef struct tsvd_info {
 
 typedef struct tsvd_handle tsvd_handle;
 
+/* Sums count doubles at buf (host memory) over the processes of a row partition, in
+ * place; returns 0 on success.  Called by the library on the thread that made the
+ * solver call, in the same order on every process. */
+typedef int (*tsvd_allreduce_fn)(void* ctx, double* buf, int64_t count);
+
 /* ---- lifetime ----------------------------------------------------------- */
 
 /* Fills *opts with the defaults listed above. */
@@ -182,6 +190,30 @@ int tsvd_destroy(tsvd_handle* h);
  * any fault); the paper has no counterpart.  TSVD_ERR_INVALID_ARG for a NULL
  * handle. */
 int tsvd_set_wait_limit(tsvd_handle* h, long long cycles);
+
+/* Row-partitioned LancSVD (Alg. 2 with the rows of A, and of the left basis Pbar,
+ * split over processes; Sec. 3.2's CholeskyQR2 exchanges only b x b Gram matrices).
+ * After this call tsvd_blanczos on this handle treats its matrix argument A (m x n,
+ * CSR or dense, FP64, device) as rows [row0, row0 + m) of a rows_total x n matrix
+ * whose other rows the other processes hold, with rows_total >= n:
+ *   - the right basis P (n-side) is replicated: every process computes it, from the
+ *     sum over processes of A_local^T Qbar_local (one n x b reduction per block);
+ *   - the left blocks stay local; their Gram matrices, projection coefficients and
+ *     norms are summed over the processes (b x b and s x b reductions);
+ *   - B, its SVD and the stopping test are replicated, so every process takes the
+ *     same path; the start block is rows [row0, row0 + m) of the one the whole
+ *     matrix would get with the same seed;
+ *   - outputs: sigma and V (n x k) replicated, U (m x k) this process's rows.
+ * Each reduction is a call fn(ctx, buf, count) on a host buffer (the library copies
+ * the device data to it and back), so any transport serves (MPI, a socket, a
+ * torch.distributed group); every process must make the same solver calls in the
+ * same order.  fn == NULL ends the partition.  Precision FP64 only; tsvd_rsvd and
+ * the mixed form return TSVD_ERR_UNSUPPORTED on a partitioned handle.  The solve and
+ * its tsvd_workspace_size call carry TSVD_FLAG_ROW_PARTITION in tsvd_opts.flags
+ * (TSVD_ERR_INVALID_ARG when the flag and the handle disagree).  A failed
+ * reduction gives TSVD_ERR_COMM.  The paper runs one GPU; this is the data-parallel
+ * split of its method. */
+int tsvd_set_row_partition(tsvd_handle* h, int64_t row0, int64_t rows_total, tsvd_allreduce_fn fn, void* ctx);
 
 /* Static text for a status code. */
 const char* tsvd_status_string(int status);

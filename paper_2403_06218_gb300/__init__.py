@@ -28,10 +28,14 @@ from .api import (  # noqa: F401
     small_svd,
     handle,
     wait_limit,
+    RowPartition,
+    torch_allreduce,
+    row_block,
 )
 
 __all__ = [
     "TsvdError", "CsrMatrix", "SvdResult", "blanczos", "rsvd", "gaussian_block", "csr_transpose", "spmm",
-    "dense_mm", "svd_backward", "truncated_svd", "Bf16x3", "bf16x3_split", "mm_bf16x6", "cholqr2", "cgs_cqr2", "cgs_qr", "small_svd", "handle", "wait_limit", "load",
+    "dense_mm", "svd_backward", "truncated_svd", "Bf16x3", "bf16x3_split", "mm_bf16x6", "cholqr2", "cgs_cqr2", "cgs_qr", "small_svd", "handle", "wait_limit", "RowPartition", "torch_allreduce",
+    "row_block", "load",
     "LIB_PATH",
 ]

@@ -16,6 +16,7 @@ TSVD_ERR_CUDA = -3
 TSVD_ERR_WORKSPACE = -4
 TSVD_ERR_TIMEOUT = -5
 TSVD_ERR_UNSUPPORTED = -6
+TSVD_ERR_COMM = -7
 
 TSVD_DENSE = 0
 TSVD_CSR = 1
@@ -30,6 +31,7 @@ TSVD_METHOD_BLANCZOS = 1
 TSVD_MAX_BLOCK = 128
 TSVD_MAX_SMALL_SVD = 2048
 TSVD_FLAG_PROFILE = 1
+TSVD_FLAG_ROW_PARTITION = 2
 TSVD_NOALLOC_SCRATCH_BYTES = 4 * 1024 * 1024
 KERNEL_CLASSES = ("a_products", "gemm_tn", "gemm_nn", "chol", "svd", "other")
 
@@ -83,6 +85,9 @@ class TsvdBackwardInfo(C.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+# int (*tsvd_allreduce_fn)(void* ctx, double* buf, int64_t count)
+ALLREDUCE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(C.c_double), C.c_int64)
+
 # (name, restype, argtypes); every symbol listed here is declared in include/tsvd.h.
 _P = C.c_void_p
 _I = C.c_int
@@ -95,6 +100,7 @@ SIGNATURES = [
     ("tsvd_create", _I, [C.POINTER(_P), _I]),
     ("tsvd_destroy", _I, [_P]),
     ("tsvd_set_wait_limit", _I, [_P, C.c_longlong]),
+    ("tsvd_set_row_partition", _I, [_P, _I64, _I64, ALLREDUCE_FN, _P]),
     ("tsvd_status_string", C.c_char_p, [_I]),
     ("tsvd_workspace_size", _I, [C.POINTER(TsvdMatrix), _I, _I, _I, _I, C.POINTER(TsvdOpts), _PSZ]),
     ("tsvd_rsvd", _I, [_P, C.POINTER(TsvdMatrix), _I, _I, _I, C.c_uint64, C.POINTER(TsvdOpts), _P, _SZ,

@@ -207,8 +207,49 @@ class SvdResult:
 _PRECISIONS = {"fp64": capi.TSVD_PREC_FP64, "mixed": capi.TSVD_PREC_MIXED}
 
 
+class RowPartition:
+    """This process's share of a row-partitioned LancSVD: its matrix holds rows
+    [row0, row0 + m) of a rows_total x n matrix that other processes hold the rest of.
+    ``allreduce(buf)`` sums a float64 numpy array in place over the processes (see
+    :func:`torch_allreduce`); the library calls it, through the C ABI's callback, for
+    every Gram matrix, projection and A^T product it sums over the rows."""
+
+    def __init__(self, row0: int, rows_total: int, allreduce):
+        if not (0 <= int(row0) < int(rows_total)):
+            raise ValueError("row0 must lie in [0, rows_total)")
+        self.row0, self.rows_total, self.allreduce = int(row0), int(rows_total), allreduce
+        self.error = None
+        self._cb = capi.ALLREDUCE_FN(self._call)
+
+    def _call(self, ctx, buf, count):
+        try:
+            self.allreduce(np.ctypeslib.as_array(buf, shape=(int(count),)))
+            return 0
+        except Exception as e:  # reported to the library as a failed reduction
+            self.error = e
+            return 1
+
+
+def torch_allreduce(group=None):
+    """A RowPartition allreduce over a torch.distributed process group (CPU tensors:
+    a gloo group, or any backend that reduces host memory)."""
+    import torch.distributed as dist
+
+    def allreduce(arr):
+        dist.all_reduce(torch.from_numpy(arr), op=dist.ReduceOp.SUM, group=group)
+
+    return allreduce
+
+
+def row_block(rows_total: int, world: int, rank: int):
+    """[lo, hi) of rank's rows in an even split of rows_total rows over world ranks."""
+    base, extra = divmod(int(rows_total), int(world))
+    lo = rank * base + min(rank, extra)
+    return lo, lo + base + (1 if rank < extra else 0)
+
+
 def _run_driver(fn_name, method, A, k, a, c, seed, tol, max_restarts, qr_block, start_block, output, device,
-                profile=False, precision="fp64", restart_keep=0):
+                profile=False, precision="fp64", restart_keep=0, partition: Optional[RowPartition] = None):
     lib = capi.load()
     desc, keep, dev = _desc(A)
     if dev is None:
@@ -220,6 +261,12 @@ def _run_driver(fn_name, method, A, k, a, c, seed, tol, max_restarts, qr_block, 
     opts.qr_block = int(qr_block)
     opts.output_location = capi.TSVD_HOST if output == "host" else capi.TSVD_DEVICE
     opts.flags = capi.TSVD_FLAG_PROFILE if profile else 0
+    if partition is not None:
+        if start_block is not None:
+            raise ValueError("a row-partitioned solve draws its own start block")
+        if int(desc.m) + partition.row0 > partition.rows_total:
+            raise ValueError("the matrix's rows do not fit in the partition")
+        opts.flags |= capi.TSVD_FLAG_ROW_PARTITION
     if precision not in _PRECISIONS:
         raise ValueError(f"precision must be one of {sorted(_PRECISIONS)}")
     opts.precision = _PRECISIONS[precision]
@@ -252,8 +299,18 @@ def _run_driver(fn_name, method, A, k, a, c, seed, tol, max_restarts, qr_block, 
             U = torch.empty((m, k), dtype=torch.float64, device=dev)
             V = torch.empty((n, k), dtype=torch.float64, device=dev)
         info = capi.TsvdInfo()
-        rc = getattr(lib, fn_name)(handle(dev), C.byref(desc), k, a, c, C.c_uint64(seed), C.byref(opts),
-                                   ws.data_ptr(), ws.numel(), _ptr(sigma), _ptr(U), _ptr(V), C.byref(info))
+        h = handle(dev)
+        if partition is not None:
+            capi.check(lib.tsvd_set_row_partition(h, partition.row0, partition.rows_total, partition._cb, None),
+                       "tsvd_set_row_partition")
+        try:
+            rc = getattr(lib, fn_name)(h, C.byref(desc), k, a, c, C.c_uint64(seed), C.byref(opts),
+                                       ws.data_ptr(), ws.numel(), _ptr(sigma), _ptr(U), _ptr(V), C.byref(info))
+        finally:
+            if partition is not None:
+                lib.tsvd_set_row_partition(h, 0, 0, capi.ALLREDUCE_FN(), None)
+        if partition is not None and partition.error is not None and rc == capi.TSVD_ERR_COMM:
+            raise capi.TsvdError(rc, fn_name) from partition.error
         capi.check(rc, fn_name, allow_not_converged=True)
     del keep
     return SvdResult(sigma, U, V, info.as_dict(), rc)
@@ -261,14 +318,17 @@ def _run_driver(fn_name, method, A, k, a, c, seed, tol, max_restarts, qr_block, 
 
 def blanczos(A, k: int, b: int, r: int, seed: int = 0, tol: float = 1e-6, max_restarts: int = 50,
              start_block: Optional[torch.Tensor] = None, output: str = "device", device=None,
-             profile: bool = False, precision: str = "fp64", restart_keep: int = 0) -> SvdResult:
+             profile: bool = False, precision: str = "fp64", restart_keep: int = 0,
+             partition: Optional[RowPartition] = None) -> SvdResult:
     """LancSVD (Alg. 2): k triplets with blocks of width b, r blocks per restart cycle.
     ``profile`` times every kernel class with CUDA events (``info['prof_*']``);
     ``precision="mixed"`` selects the FP32-product form with FP64 small algebra
     and a final FP64 Rayleigh-Ritz step; ``restart_keep=s > 0`` selects the thick
-    restart that keeps the s leading Ritz pairs (0: the paper's basic restart)."""
+    restart that keeps the s leading Ritz pairs (0: the paper's basic restart).
+    ``partition``: A is this process's row block of a row-partitioned matrix
+    (FP64; sigma and V replicated, U this process's rows)."""
     return _run_driver("tsvd_blanczos", capi.TSVD_METHOD_BLANCZOS, A, k, b, r, seed, tol, max_restarts, 0,
-                       start_block, output, device, profile, precision, restart_keep)
+                       start_block, output, device, profile, precision, restart_keep, partition)
 
 
 def rsvd(A, k: int, p: int, q: int, seed: int = 0, qr_block: int = 0, start_block: Optional[torch.Tensor] = None,

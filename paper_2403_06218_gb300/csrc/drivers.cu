@@ -164,13 +164,13 @@ size_t tn_partial_max(tsvd_handle* h, int64_t q, int64_t s, int wmax) {
 // value conversions between FP64 and FP32, dense split-K scratch.
 template <typename T>
 int setup_op(tsvd_handle* h, const tsvd_matrix* A, int wmax, Arena& ar, Op<T>& op, int* status, cudaStream_t st,
-             bool run, float* ms_transpose, bool oz_planes = false) {
+             bool run, float* ms_transpose, bool oz_planes = false, bool no_transpose = false) {
     constexpr bool kF64 = sizeof(T) == sizeof(double);
     const bool in64 = A->dtype == TSVD_F64;
     const bool host = A->location == TSVD_HOST;
     op.M = A->m;
     op.N = A->n;
-    op.transposed = A->m < A->n;
+    op.transposed = !no_transpose && A->m < A->n;
     op.m = op.transposed ? A->n : A->m;
     op.n = op.transposed ? A->m : A->n;
     op.sparse = A->format == TSVD_CSR;
@@ -442,10 +442,12 @@ int final_triplets(tsvd_handle* h, Op<T>& op, int k, const T* Bm, int64_t ldbm, 
 // method, not after the mixed form's two-sided Rayleigh-Ritz step).
 template <typename T>
 int explicit_residual(tsvd_handle* h, Op<T>& op, int k, const double* U, const double* V, const double* sigma,
-                      Final& f, int* status, cudaStream_t st, double* out) {
+                      Final& f, int* status, cudaStream_t st, double* out, bool part = false) {
     TSVD_TRY(op_mul64(h, op, k, V, k, f.AV, k, status, st));
     TSVD_TRY_CUDA(col_residual_sq(h, op.m, k, f.AV, k, U, k, sigma, f.res, f.cpart, st));
+    if (part) TSVD_TRY(part_sum(h, f.res, 1, k, k, st));  // this process's rows of A V - U S
     TSVD_TRY(op_tmul64(h, op, k, U, k, f.AV, k, status, st));
+    if (part) TSVD_TRY(part_sum(h, f.AV, op.n, k, k, st));  // A^T U over all rows
     TSVD_TRY_CUDA(col_residual_sq(h, op.n, k, f.AV, k, V, k, sigma, f.res + k, f.cpart, st));
     std::vector<double> hres(2 * k), hs(1);
     TSVD_TRY_CUDA(cudaMemcpyAsync(hres.data(), f.res, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, st));
@@ -506,6 +508,7 @@ int rsvd_run(tsvd_handle* h, const tsvd_matrix* A, int k, int p, int q, int bq, 
     } del{total};
     Op<T> op;
     float ms_t = 0.f;
+    if ((o->flags & TSVD_FLAG_ROW_PARTITION) || (run && h->part_fn)) return TSVD_ERR_UNSUPPORTED;
     TSVD_TRY(setup_op<T>(h, A, ell > k ? ell : k, ar, op, status, st, run, A->format == TSVD_CSR ? &ms_t : nullptr,
                          true));
     OzCacheScope ocs(h);
@@ -632,8 +635,14 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
     } del{total};
     Op<T> op;
     float ms_t = 0.f;
+    // row partition: this process's rows of A and of the left basis; sums over the
+    // rows (Gram matrices, projections, A^T Qbar, residual norms) are summed over the
+    // processes, everything n-side and small is replicated
+    const bool part = (o->flags & TSVD_FLAG_ROW_PARTITION) != 0;
+    if (part && (kMixed || (run && !h->part_fn))) return kMixed ? TSVD_ERR_UNSUPPORTED : TSVD_ERR_INVALID_ARG;
+    if (!part && run && h->part_fn) return TSVD_ERR_INVALID_ARG;
     TSVD_TRY(setup_op<T>(h, A, b > k ? b : k, ar, op, status, st, run, A->format == TSVD_CSR ? &ms_t : nullptr,
-                         true));
+                         true, part));
     OzCacheScope ocs(h);
     if (op.oz && run) {
         ocs.add(&op.ozA[0]);
@@ -712,8 +721,12 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
     }
     if (!ar.fits()) return TSVD_ERR_WORKSPACE;
     OzScope oz(h, ozws, ozb, status);
-    OrthCtx ctx;
+    OrthCtx ctx;  // n-side blocks (replicated)
     ctx.seed = seed;
+    OrthCtx mctx;  // m-side blocks (this process's rows when partitioned)
+    mctx.seed = seed;
+    mctx.reduce = part;
+    mctx.row0 = part ? h->part_row0 : 0;
     double* dU = f.oU ? f.oU : (op.transposed ? V : U);
     double* dV = f.oV ? f.oV : (op.transposed ? U : V);
     double* dsig = f.osig ? f.osig : sigma;
@@ -724,9 +737,9 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
         TSVD_TRY_CUDA(gaussian(h, m, b, seed, 2u, g64, b, st));
         TSVD_TRY_CUDA((convert2d<double, T>(h, m, b, g64, b, Pbar, rb, st)));
     } else {
-        TSVD_TRY_CUDA(gaussian(h, m, b, seed, 2u, reinterpret_cast<double*>(Pbar), rb, st));
+        TSVD_TRY_CUDA(gaussian(h, m, b, seed, 2u, reinterpret_cast<double*>(Pbar), rb, st, mctx.row0));
     }
-    TSVD_TRY(cgs_cqr2<T>(h, m, 0, b, nullptr, 0, Pbar, rb, nullptr, Rr, b, false, ctx, ar, status, st));
+    TSVD_TRY(cgs_cqr2<T>(h, m, 0, b, nullptr, 0, Pbar, rb, nullptr, Rr, b, false, mctx, ar, status, st));
     TSVD_TRY(slice_cols(cPb, 0, b));
     int cycles = 0, restarts = 0, sweeps = 0, converged = 0;
     double rho_last = NAN, resid = NAN;
@@ -753,12 +766,14 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
             TSVD_TRY_CUDA(cudaMemcpyAsync(Bsave, B, sizeof(double) * (size_t)rb * rb, cudaMemcpyDeviceToDevice, st));
         for (int pass = 0; pass < 2; ++pass) {
             ctx.deferred = defer && pass == 0;
+            mctx.deferred = ctx.deferred;
             TSVD_TRY(keep_cols(cP, s0));
             TSVD_TRY(keep_cols(cPb, s0 + b));
             for (int i = 0; i < nblk; ++i) {
                 const int c0 = s0 + i * b;
                 T* Qi = P + c0;
                 TSVD_TRY(op_tmul<T>(h, op, b, Pbar + c0, rb, Qi, rb, status, st));                    // S2
+                if (part) TSVD_TRY(part_sum(h, reinterpret_cast<double*>(Qi), n, b, rb, st));
                 double* Lii = B + (int64_t)c0 * rb + c0;
                 const bool couple = (i == 0 && s0 > 0);
                 TSVD_TRY(cgs_cqr2<T>(h, n, c0, b, P, rb, Qi, rb, couple ? Hk : nullptr, Lii, rb, true, ctx, ar, status,
@@ -770,8 +785,8 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
                 const int64_t ldd = last ? b : rb;
                 TSVD_TRY(op_mul<T>(h, op, b, Qi, rb, dst, ldd, status, st));                             // S4
                 double* Ri = last ? Rr : B + (int64_t)(c0 + b) * rb + c0;
-                TSVD_TRY(cgs_cqr2<T>(h, m, c0 + b, b, Pbar, rb, dst, ldd, nullptr, Ri, last ? b : rb, false, ctx, ar,
-                                     status, st));                                                       // S5
+                TSVD_TRY(cgs_cqr2<T>(h, m, c0 + b, b, Pbar, rb, dst, ldd, nullptr, Ri, last ? b : rb, false, mctx,
+                                     ar, status, st));                                                   // S5
                 if (!last) TSVD_TRY(slice_cols(cPb, c0 + b, c0 + 2 * b));
             }
             {
@@ -789,6 +804,7 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
             defer = false;
         }
         ctx.deferred = false;
+        mctx.deferred = false;
         ++cycles;
         TSVD_TRY(status_code(hs));
         sweeps = hs[kStSweeps];
@@ -803,7 +819,7 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
             TSVD_TRY(final_triplets<T>(h, op, k, Pbar, rb, Ub, d, P, rb, Vb, d, d, sig, f, dU, dV, dsig, ctx, ar,
                                        status, st, nullptr, with_masters ? Pbk64[cur] : nullptr, keep,
                                        with_masters ? Pk64[cur] : nullptr, keep, with_masters ? s0 : 0));
-            TSVD_TRY(explicit_residual<T>(h, op, k, dU, dV, dsig, f, status, st, &resid));
+            TSVD_TRY(explicit_residual<T>(h, op, k, dU, dV, dsig, f, status, st, &resid, part));
             if ((done && resid <= o->tol) || restarts >= o->max_restarts) {
                 converged = resid <= o->tol ? 1 : 0;
                 break;
@@ -852,7 +868,7 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
             TSVD_TRY(keep_cols(cP, 0));
             TSVD_TRY(keep_cols(cPb, 0));
             TSVD_TRY_CUDA(copy_block<T>(Qnext, b, Pbar, rb, m, b, st));
-            TSVD_TRY(cgs_cqr2<T>(h, m, 0, b, nullptr, 0, Pbar, rb, nullptr, Rr, b, false, ctx, ar, status, st));
+            TSVD_TRY(cgs_cqr2<T>(h, m, 0, b, nullptr, 0, Pbar, rb, nullptr, Rr, b, false, mctx, ar, status, st));
             TSVD_TRY(slice_cols(cPb, 0, b));
         }
     }
@@ -864,7 +880,7 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
         std::memset(info, 0, sizeof(*info));
         info->iterations = cycles;
         info->restarts = restarts;
-        info->breakdowns = ctx.fallbacks;
+        info->breakdowns = ctx.fallbacks + mctx.fallbacks;
         info->converged = converged;
         info->transposed = op.transposed ? 1 : 0;
         info->svd_sweeps = sweeps;

@@ -374,10 +374,13 @@ __device__ inline void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
 }
 
 __global__ void gaussian_kernel(int64_t rows, int64_t cols, uint32_t k0, uint32_t k1, uint32_t sid,
-                                double* __restrict__ out, int64_t ld) {
+                                double* __restrict__ out, int64_t ld, int64_t e_off) {
+    // elements e_off .. e_off + rows cols - 1 of the row-major global block: element e
+    // is half of Philox counter e / 2, so a slice that starts at an odd element drops
+    // the first half of its first pair
     const int64_t n_el = rows * cols;
-    const int64_t n_pairs = (n_el + 1) / 2;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_pairs;
+    const int64_t t0 = e_off / 2, t1 = (e_off + n_el - 1) / 2;
+    for (int64_t t = t0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t <= t1;
          t += (int64_t)gridDim.x * blockDim.x) {
         uint32_t c[4] = {(uint32_t)(t & 0xffffffffu), (uint32_t)((uint64_t)t >> 32), sid, 0u};
         philox4x32_10(c, k0, k1);
@@ -387,9 +390,9 @@ __global__ void gaussian_kernel(int64_t rows, int64_t cols, uint32_t k0, uint32_
         const double rad = sqrt(-2.0 * log(u1));
         double sn, cs;
         sincospi(2.0 * u2, &sn, &cs);
-        const int64_t e0 = 2 * t, e1 = 2 * t + 1;
-        out[(e0 / cols) * ld + (e0 % cols)] = rad * cs;
-        if (e1 < n_el) out[(e1 / cols) * ld + (e1 % cols)] = rad * sn;
+        const int64_t e0 = 2 * t - e_off, e1 = e0 + 1;
+        if (e0 >= 0 && e0 < n_el) out[(e0 / cols) * ld + (e0 % cols)] = rad * cs;
+        if (e1 >= 0 && e1 < n_el) out[(e1 / cols) * ld + (e1 % cols)] = rad * sn;
     }
 }
 
@@ -632,15 +635,16 @@ cudaError_t trmm_upper(tsvd_handle* h, int b, const double* A, const double* U, 
 }
 
 cudaError_t gaussian(tsvd_handle* h, int64_t rows, int64_t cols, uint64_t seed, uint32_t stream_id, double* out,
-                     int64_t ld, cudaStream_t st) {
-    const int64_t n_pairs = (rows * cols + 1) / 2;
-    if (n_pairs == 0) return cudaSuccess;
+                     int64_t ld, cudaStream_t st, int64_t row0) {
+    if (rows * cols == 0) return cudaSuccess;
+    const int64_t e_off = row0 * cols;
+    const int64_t n_pairs = (e_off + rows * cols - 1) / 2 - e_off / 2 + 1;
     int64_t blocks = (n_pairs + 255) / 256;
     if (blocks > 8LL * h->sm_count * 8) blocks = 8LL * h->sm_count * 8;
     ProfScope prof(h, TSVD_K_OTHER, 0.0, 8.0 * rows * cols, st);
     h->launches++;
     gaussian_kernel<<<(unsigned)blocks, 256, 0, st>>>(rows, cols, (uint32_t)(seed & 0xffffffffu),
-                                                      (uint32_t)(seed >> 32), stream_id, out, ld);
+                                                      (uint32_t)(seed >> 32), stream_id, out, ld, e_off);
     return cudaGetLastError();
 }
 

@@ -101,24 +101,28 @@ OrthWs<T> carve(tsvd_handle* h, Arena& ar, int64_t q, int64_t s, int b) {
     return w;
 }
 
-// One CholeskyQR step (Alg. 4 S1-S3): W = Y^T Y, W = L L^T, Y <- Y L^{-T}.
+// One CholeskyQR step (Alg. 4 S1-S3): W = Y^T Y, W = L L^T, Y <- Y L^{-T}.  With a
+// row partition, W is the sum of the processes' Gram matrices (the communication-
+// avoiding property of Sec. 3.2: one b x b reduction per step).
 template <typename T>
-cudaError_t cholqr_step(tsvd_handle* h, int64_t q, int b, T* Y, int64_t ldy, double* W, double* Lt, double* Mt,
-                        double* partial, int* status, cudaStream_t st) {
-    cudaError_t e = gemm_tn(h, q, b, b, Y, ldy, Y, ldy, W, b, true, partial, st);
-    if (e != cudaSuccess) return e;
-    e = chol_inv(h, b, W, Lt, Mt, status, st);
-    if (e != cudaSuccess) return e;
-    return gemm_nn(h, q, b, b, 1.0, Y, ldy, Mt, b, 0.0, Y, ldy, true, st);
+int cholqr_step(tsvd_handle* h, int64_t q, int b, T* Y, int64_t ldy, double* W, double* Lt, double* Mt,
+                double* partial, int* status, const OrthCtx& ctx, cudaStream_t st) {
+    TSVD_TRY_CUDA(gemm_tn(h, q, b, b, Y, ldy, Y, ldy, W, b, true, partial, st));
+    if (ctx.reduce) TSVD_TRY(part_sum(h, W, b, b, b, st));
+    TSVD_TRY_CUDA(chol_inv(h, b, W, Lt, Mt, status, st));
+    TSVD_TRY_CUDA(gemm_nn(h, q, b, b, 1.0, Y, ldy, Mt, b, 0.0, Y, ldy, true, st));
+    return TSVD_OK;
 }
 
 // v -= [P, Yprev] ([P, Yprev]^T v), twice; accumulating coefficients when asked.
 template <typename T>
 int project_twice(tsvd_handle* h, int64_t q, int64_t s, const T* P, int64_t ldp, int j, const T* Yprev,
-                  int64_t ldy, T* v, int64_t ldv, OrthWs<T>& w, bool accumulate, cudaStream_t st) {
+                  int64_t ldy, T* v, int64_t ldv, OrthWs<T>& w, bool accumulate, const OrthCtx& ctx,
+                  cudaStream_t st) {
     for (int pass = 0; pass < 2; ++pass) {
         if (s > 0) {
             TSVD_TRY_CUDA(gemm_tn(h, q, s, 1, P, ldp, v, ldv, w.fh, 1, false, w.partial, st));
+            if (ctx.reduce) TSVD_TRY(part_sum(h, w.fh, s, 1, 1, st));
             TSVD_TRY_CUDA(gemm_nn(h, q, s, 1, -1.0, P, ldp, w.fh, 1, 1.0, v, ldv, false, st));
             if (accumulate) {
                 h->launches++;
@@ -127,6 +131,7 @@ int project_twice(tsvd_handle* h, int64_t q, int64_t s, const T* P, int64_t ldp,
         }
         if (j > 0) {
             TSVD_TRY_CUDA(gemm_tn(h, q, j, 1, Yprev, ldy, v, ldv, w.fc, 1, false, w.partial, st));
+            if (ctx.reduce) TSVD_TRY(part_sum(h, w.fc, j, 1, 1, st));
             TSVD_TRY_CUDA(gemm_nn(h, q, j, 1, -1.0, Yprev, ldy, w.fc, 1, 1.0, v, ldv, false, st));
             if (accumulate) {
                 h->launches++;
@@ -139,8 +144,10 @@ int project_twice(tsvd_handle* h, int64_t q, int64_t s, const T* P, int64_t ldp,
 }
 
 template <typename T>
-int read_norm(tsvd_handle* h, int64_t q, const T* v, int64_t ldv, OrthWs<T>& w, double* out, cudaStream_t st) {
+int read_norm(tsvd_handle* h, int64_t q, const T* v, int64_t ldv, OrthWs<T>& w, double* out, const OrthCtx& ctx,
+              cudaStream_t st) {
     TSVD_TRY_CUDA(gemm_tn(h, q, 1, 1, v, ldv, v, ldv, w.fnrm, 1, true, w.partial, st));
+    if (ctx.reduce) TSVD_TRY(part_sum(h, w.fnrm, 1, 1, 1, st));
     h->launches++;
     sqrt_kernel<<<1, 1, 0, st>>>(w.fnrm);
     TSVD_TRY_CUDA(cudaGetLastError());
@@ -158,11 +165,11 @@ int cgs2_columns(tsvd_handle* h, int64_t q, int64_t s, int b, const T* P, int64_
     for (int j = 0; j < b; ++j) {
         T* v = Y + j;
         double nrm0 = 0.0, nrm = 0.0;
-        TSVD_TRY(read_norm(h, q, v, ldy, w, &nrm0, st));
+        TSVD_TRY(read_norm(h, q, v, ldy, w, &nrm0, ctx, st));
         if (s > 0) TSVD_TRY_CUDA(cudaMemsetAsync(w.fhacc, 0, sizeof(double) * s, st));
         TSVD_TRY_CUDA(cudaMemsetAsync(w.fcacc, 0, sizeof(double) * b, st));
-        TSVD_TRY(project_twice(h, q, s, P, ldp, j, Y, ldy, v, ldy, w, true, st));
-        TSVD_TRY(read_norm(h, q, v, ldy, w, &nrm, st));
+        TSVD_TRY(project_twice(h, q, s, P, ldp, j, Y, ldy, v, ldy, w, true, ctx, st));
+        TSVD_TRY(read_norm(h, q, v, ldy, w, &nrm, ctx, st));
         if (!std::isfinite(nrm0) || !std::isfinite(nrm)) return TSVD_ERR_NONFINITE;
         h->launches++;
         put_rcol_kernel<<<1, 128, 0, st>>>(j, w.fcacc, nrm, R, ldr, r_trans ? 1 : 0);
@@ -174,13 +181,13 @@ int cgs2_columns(tsvd_handle* h, int64_t q, int64_t s, int b, const T* P, int64_
         TSVD_TRY_CUDA(cudaGetLastError());
         if (!(nrm > 1e-10 * nrm0) || nrm0 == 0.0) {
             // dependent column: replace its direction by a Philox N(0,1) column
-            TSVD_TRY_CUDA(gaussian(h, q, 1, ctx.seed, 0x100u + (uint32_t)ctx.replacements, w.fcol64, 1, st));
+            TSVD_TRY_CUDA(gaussian(h, q, 1, ctx.seed, 0x100u + (uint32_t)ctx.replacements, w.fcol64, 1, st, ctx.row0));
             ctx.replacements++;
             h->launches++;
             d2t_kernel<T><<<(unsigned)((q + 255) / 256), 256, 0, st>>>(q, w.fcol64, w.fcol);
-            TSVD_TRY(project_twice(h, q, s, P, ldp, j, Y, ldy, w.fcol, 1, w, false, st));
+            TSVD_TRY(project_twice(h, q, s, P, ldp, j, Y, ldy, w.fcol, 1, w, false, ctx, st));
             double zn = 0.0;
-            TSVD_TRY(read_norm(h, q, w.fcol, 1, w, &zn, st));
+            TSVD_TRY(read_norm(h, q, w.fcol, 1, w, &zn, ctx, st));
             if (!(zn > 0.0) || !std::isfinite(zn)) return TSVD_ERR_NONFINITE;
             TSVD_TRY_CUDA(copy_block(w.fcol, 1, v, ldy, q, 1, st));
         }
@@ -215,14 +222,16 @@ int cgs_cqr2(tsvd_handle* h, int64_t q, int64_t s, int b, const T* P, int64_t ld
     TSVD_TRY_CUDA(copy_block(Y, ldy, w.save, b, q, b, st));
     if (s > 0) {
         TSVD_TRY_CUDA(gemm_tn(h, q, s, b, P, ldp, Y, ldy, w.H1, b, false, w.partial, st));           // S1
+        if (ctx.reduce) TSVD_TRY(part_sum(h, w.H1, s, b, b, st));
         TSVD_TRY_CUDA(gemm_nn(h, q, s, b, -1.0, P, ldp, w.H1, b, 1.0, Y, ldy, false, st));           // S2
     }
-    TSVD_TRY_CUDA(cholqr_step(h, q, b, Y, ldy, w.W, w.Lt1, w.Mt1, w.partial, status, st));  // S3-S5
+    TSVD_TRY(cholqr_step(h, q, b, Y, ldy, w.W, w.Lt1, w.Mt1, w.partial, status, ctx, st));  // S3-S5
     if (s > 0) {
         TSVD_TRY_CUDA(gemm_tn(h, q, s, b, P, ldp, Y, ldy, w.H2, b, false, w.partial, st));           // S6
+        if (ctx.reduce) TSVD_TRY(part_sum(h, w.H2, s, b, b, st));
         TSVD_TRY_CUDA(gemm_nn(h, q, s, b, -1.0, P, ldp, w.H2, b, 1.0, Y, ldy, false, st));           // S7
     }
-    TSVD_TRY_CUDA(cholqr_step(h, q, b, Y, ldy, w.W, w.Lt2, w.Mt2, w.partial, status, st));  // S8-S10
+    TSVD_TRY(cholqr_step(h, q, b, Y, ldy, w.W, w.Lt2, w.Mt2, w.partial, status, ctx, st));  // S8-S10
     TSVD_TRY_CUDA(trmm_upper(h, b, w.Lt2, w.Lt1, R, ldr, r_trans, st));                         // S11
     if (H != nullptr && s > 0) {                                                                 // S12
         TSVD_TRY_CUDA(copy_block(w.H1, b, H, b, s, b, st));

@@ -23,6 +23,22 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
 
 using namespace tsvd;
 
+int tsvd::part_sum(tsvd_handle* h, double* d, int64_t rows, int64_t cols, int64_t ld, cudaStream_t st) {
+    if (!h->part_fn || rows * cols == 0) return TSVD_OK;
+    const size_t cnt = (size_t)rows * (size_t)cols;
+    h->part_host.resize(cnt);
+    double* hb = h->part_host.data();
+    const size_t w = sizeof(double) * (size_t)cols;
+    TSVD_TRY_CUDA(cudaMemcpy2DAsync(hb, w, d, sizeof(double) * (size_t)ld, w, (size_t)rows, cudaMemcpyDeviceToHost,
+                                    st));
+    TSVD_TRY_CUDA(cudaStreamSynchronize(st));
+    if (h->part_fn(h->part_ctx, hb, (int64_t)cnt) != 0) return TSVD_ERR_COMM;
+    TSVD_TRY_CUDA(cudaMemcpy2DAsync(d, sizeof(double) * (size_t)ld, hb, w, w, (size_t)rows, cudaMemcpyHostToDevice,
+                                    st));
+    TSVD_TRY_CUDA(cudaStreamSynchronize(st));
+    return TSVD_OK;
+}
+
 void tsvd::prof_collect(tsvd_handle* h, tsvd_info* info) {
     for (auto& r : h->recs) {
         float ms = 0.f;
@@ -146,6 +162,7 @@ const char* tsvd_status_string(int s) {
         case TSVD_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
         case TSVD_ERR_TIMEOUT: return "device wait timed out";
         case TSVD_ERR_UNSUPPORTED: return "unsupported size";
+        case TSVD_ERR_COMM: return "row-partition reduction failed";
         default: return "unknown status";
     }
 }
@@ -171,6 +188,16 @@ int tsvd_create(tsvd_handle** out, int device) {
 
 int tsvd_destroy(tsvd_handle* h) {
     delete h;
+    return TSVD_OK;
+}
+
+int tsvd_set_row_partition(tsvd_handle* h, int64_t row0, int64_t rows_total, tsvd_allreduce_fn fn, void* ctx) {
+    if (!h) return TSVD_ERR_INVALID_ARG;
+    if (fn && (row0 < 0 || rows_total < 1 || row0 >= rows_total)) return TSVD_ERR_INVALID_ARG;
+    h->part_fn = fn;
+    h->part_ctx = fn ? ctx : nullptr;
+    h->part_row0 = fn ? row0 : 0;
+    h->part_rows = fn ? rows_total : 0;
     return TSVD_OK;
 }
 

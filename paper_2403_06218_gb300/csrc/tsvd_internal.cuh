@@ -57,6 +57,13 @@ struct tsvd_handle {
     // limit, in SM clock cycles, of one bounded wait of the pipelined product kernels
     // and of the Jacobi grid barrier (2e9, about 1 s; tsvd_set_wait_limit lowers it)
     long long max_wait = 2000000000LL;
+    // row partition (tsvd_set_row_partition): this process holds rows
+    // [part_row0, part_row0 + m) of a part_rows x n matrix; part_fn sums host buffers
+    // over the processes of the partition
+    tsvd_allreduce_fn part_fn = nullptr;
+    void* part_ctx = nullptr;
+    int64_t part_row0 = 0, part_rows = 0;
+    std::vector<double> part_host;
 };
 
 namespace tsvd {
@@ -341,8 +348,10 @@ cudaError_t chol_inv(tsvd_handle* h, int b, const double* W, double* Lt, double*
 cudaError_t trmm_upper(tsvd_handle* h, int b, const double* A, const double* U, double* out,
                        int64_t ldo, bool trans, cudaStream_t st);
 
+// rows x cols of the N(0,1) block of the given seed and stream, starting at global
+// row row0 (a row slice of the same global block, whichever process draws it).
 cudaError_t gaussian(tsvd_handle* h, int64_t rows, int64_t cols, uint64_t seed, uint32_t stream_id,
-                     double* out, int64_t ld, cudaStream_t st);
+                     double* out, int64_t ld, cudaStream_t st, int64_t row0 = 0);
 
 // Small SVD by one-sided Jacobi.  nv == n accumulates every right vector; nv < n
 // recovers only the leading nv right vectors as B^T ubar_j / sigma_j (columns
@@ -417,7 +426,17 @@ struct OrthCtx {
     // leaves the sticky status word set, and the caller redoes the whole cycle
     // with deferred = false so that the fallback runs where it is needed.
     bool deferred = false;
+    // the tall dimension is this process's rows of a row-partitioned block: every
+    // product that sums over it (Gram matrices, projections, norms) is summed over the
+    // partition before use, and replacement columns are drawn at the global rows
+    // starting at row0
+    bool reduce = false;
+    int64_t row0 = 0;
 };
+
+// Sums the rows x cols block d (ld doubles, device) over the row partition of the
+// handle, in place (a no-op without one).  TSVD_ERR_COMM when the exchange fails.
+int part_sum(tsvd_handle* h, double* d, int64_t rows, int64_t cols, int64_t ld, cudaStream_t st);
 
 // Workspace of one orthogonalisation (sized for double blocks, which covers float).
 size_t orth_ws(tsvd_handle* h, int64_t q, int64_t s, int b);
