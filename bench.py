@@ -422,6 +422,12 @@ def run_case(case):
         else:
             H = torch.randn(576, 64, dtype=torch.float64, device="cuda", generator=g)
             call = lambda: tsvd.dense_mm(P, H, tensor_cores=True)  # noqa: E731
+    elif case == "ozd":
+        # dense A X, 10,000 x 10,000 x 128, as an FP64-accurate sliced product (a quarter
+        # of the dense 20k workload's A products, for counter captures)
+        A = torch.randn(10_000, 10_000, dtype=torch.float64, device="cuda", generator=g)
+        X = torch.randn(10_000, 128, dtype=torch.float64, device="cuda", generator=g)
+        call = lambda: tsvd.dense_mm(A, X, tensor_cores=True)  # noqa: E731
     elif case in ("tc", "f32", "f64"):
         # dense A Q of the 20,000 x 20,000 workload with a 128-column block: split-BF16 tensor
         # cores (tc), FP32 CUDA cores (f32) or FP64 (f64)
@@ -474,7 +480,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clock-ms", type=int, default=200, help="nvidia-smi sampling interval in the timed region")
     ap.add_argument("--case", default=None,
-                    choices=("orth", "svd", "tc", "f32", "f64", "backward", "spmm", "ozt", "ozn"),
+                    choices=("orth", "svd", "tc", "f32", "f64", "backward", "spmm", "ozt", "ozn", "ozd"),
                     help="run one building block at its benchmark shape (for profiler captures) and exit")
     args = ap.parse_args(argv)
     cfg = WORKLOADS[args.workload]

@@ -266,8 +266,8 @@ __global__ void oz_fill_kernel(int64_t n, int v, int* __restrict__ x) {
 
 // ---- the product kernel ------------------------------------------------------
 struct OzArgs {
-    int64_t M, N, KB, tiles, total;
-    int NT, Npad, G, maxseg;
+    int64_t M, N, KB, tiles, totalg;  // totalg: (row tile, K block) units of one column tile
+    int NT, Npad, G, Gg, maxseg;       // CTA c: column tile c % NT, unit group c / NT of Gg
     const int* ea;
     const int* eb;
     double* out;  // C (direct tiles)
@@ -279,8 +279,11 @@ struct OzArgs {
     long long max_wait;  // limit of one pipeline wait (SM clock cycles)
 };
 
-__host__ __device__ inline int64_t oz_lo(int c, const OzArgs& a) {
-    return (int64_t)c * a.total / a.G;
+// First unit of group g: the (row tile, K block) units of a column tile are split
+// evenly over Gg groups; the NT CTAs of a group (one per column tile) cover the same
+// units at the same time, so the A planes they all read come from DRAM once.
+__host__ __device__ inline int64_t oz_glo(int g, const OzArgs& a) {
+    return (int64_t)g * a.totalg / a.Gg;
 }
 
 // C = 2^(ea + eb - 14) (hi 2^-32 + lo 2^-40) in FP64.
@@ -322,7 +325,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.x;
-    const int64_t lo = oz_lo(c, a), hi = oz_lo(c + 1, a);
+    const int ntc = c % a.NT, gc = c / a.NT;  // this CTA's column tile and unit group
+    const int64_t lo = oz_glo(gc, a), hi = oz_glo(gc + 1, a);
     const int64_t KB = a.KB;
 
     if (threadIdx.x == 0) {
@@ -354,9 +358,9 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                 const int st = (int)(it % kOzStages);
                 if (it >= kOzStages) ok = mbar_wait(empty(st), (uint32_t)(((it / kOzStages) - 1) & 1), abort_flag, a.max_wait);
                 if (!ok) break;
-                const int64_t t = i / KB;
-                const int kz = (int)((i - t * KB) * kOzDig);  // the 7 planes of K block i - t KB
-                const int mt = (int)(t / a.NT), nt = (int)(t % a.NT);
+                const int64_t mt = i / KB;
+                const int kz = (int)((i - mt * KB) * kOzDig);  // the 7 planes of K block i - mt KB
+                const int nt = ntc;
                 const uint32_t sA = base + (uint32_t)st * kOzStageBytes;
                 mbar_arrive_expect_tx(full(st), stage_tx);
                 tma_load_3d(sA, &tmA, 0, mt * kOzM, kz, full(st));
@@ -377,8 +381,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
             int64_t it = 0, ch = 0;  // K blocks and chunks issued by this CTA
             bool ok = true;
             for (int64_t i = lo; i < hi && ok;) {
-                const int64_t t = i / KB;
-                const int64_t e = min(hi, (t + 1) * KB);
+                const int64_t mt = i / KB;
+                const int64_t e = min(hi, (mt + 1) * KB);
                 for (; i < e && ok; ++ch) {
                     const int64_t ce = min(e, i + kOzChunk);
                     for (int64_t i0 = i; i < ce; ++i, ++it) {
@@ -443,12 +447,12 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         int seg = 0;
         bool ok = true;
         for (int64_t i = lo; i < hi && ok; ++seg) {
-            const int64_t t = i / KB;
-            const int64_t e = min(hi, (t + 1) * KB);
-            const int mt = (int)(t / a.NT), nt = (int)(t % a.NT);
+            const int64_t mt = i / KB;
+            const int64_t e = min(hi, (mt + 1) * KB);
+            const int nt = ntc;
             const int64_t row = (int64_t)mt * kOzM + r;
             const int64_t col0 = (int64_t)nt * kOzN + cg * ncol;
-            const bool direct = (i == t * KB) && (e == (t + 1) * KB) && KB <= (int64_t)kOzChunk * kOzFlushChunks;
+            const bool direct = (i == mt * KB) && (e == (mt + 1) * KB) && KB <= (int64_t)kOzChunk * kOzFlushChunks;
             const int ea = row < a.M ? a.ea[row] : 0;
             double* slot = a.partial + (((int64_t)c * a.maxseg + seg) * kOzM + r) * kOzN + cg * ncol;
             // integer sums of the digit products: hi in units of 2^-32 (p + q <= 4, exact),
@@ -538,34 +542,35 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 // Tiles whose K range is split over CTAs (or longer than one 64-bit
 // accumulation): the parts are added in CTA order and the output rule applied.
 __global__ void oz_fixup_kernel(OzArgs a) {
-    __shared__ int s_c0, s_c1;
+    __shared__ int s_g0, s_g1;
     const int64_t t = blockIdx.y;
     const int64_t KB = a.KB;
+    const int mt = (int)(t / a.NT), nt = (int)(t % a.NT);
     if (threadIdx.x == 0) {
-        auto cta_of = [&](int64_t u) {
-            int cc = (int)(u * a.G / a.total);
-            while (cc + 1 < a.G && oz_lo(cc + 1, a) <= u) ++cc;
-            while (cc > 0 && oz_lo(cc, a) > u) --cc;
-            return cc;
+        auto group_of = [&](int64_t u) {
+            int g = (int)(u * a.Gg / a.totalg);
+            while (g + 1 < a.Gg && oz_glo(g + 1, a) <= u) ++g;
+            while (g > 0 && oz_glo(g, a) > u) --g;
+            return g;
         };
-        s_c0 = cta_of(t * KB);
-        s_c1 = cta_of((t + 1) * KB - 1);
+        s_g0 = group_of((int64_t)mt * KB);
+        s_g1 = group_of((int64_t)(mt + 1) * KB - 1);
     }
     __syncthreads();
-    if (s_c0 == s_c1 && KB <= (int64_t)kOzChunk * kOzFlushChunks) return;  // written by its CTA
-    // the partial tile of each contributing CTA (in CTA order)
+    if (s_g0 == s_g1 && KB <= (int64_t)kOzChunk * kOzFlushChunks) return;  // written by its CTA
+    // the partial tile of each contributing CTA (column tile nt of groups g0..g1, in order)
     __shared__ int64_t s_slot[kOzWave];
-    const int nc = s_c1 - s_c0 + 1;
+    const int nc = s_g1 - s_g0 + 1;
     for (int j = threadIdx.x; j < nc; j += blockDim.x) {
-        const int cc = s_c0 + j;
-        const int seg = (int)(t - oz_lo(cc, a) / KB);
+        const int g = s_g0 + j;
+        const int cc = g * a.NT + nt;
+        const int seg = (int)(mt - oz_glo(g, a) / KB);
         s_slot[j] = ((int64_t)cc * a.maxseg + seg) * kOzM * kOzN;
     }
     __syncthreads();
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= kOzM * kOzN) return;
     const int r = idx / kOzN, cl = idx % kOzN;
-    const int mt = (int)(t / a.NT), nt = (int)(t % a.NT);
     const int64_t row = (int64_t)mt * kOzM + r, col = (int64_t)nt * kOzN + cl;
     if (row >= a.M || col >= a.N) return;
     // eight loads in flight, added in CTA order (the same sum as a sequential loop)
@@ -584,8 +589,8 @@ __global__ void oz_fixup_kernel(OzArgs a) {
 
 // ---- host side -------------------------------------------------------------------
 struct OzPlan {
-    int64_t M, N, K, KB, tiles, total;
-    int MT, NT, Npad, G, maxseg;
+    int64_t M, N, K, KB, tiles, totalg;
+    int MT, NT, Npad, G, Gg, maxseg;
 };
 
 OzPlan oz_plan(int64_t M, int64_t N, int64_t K) {
@@ -598,16 +603,18 @@ OzPlan oz_plan(int64_t M, int64_t N, int64_t K) {
     p.Npad = N <= 32 ? 32 : kOzN;
     p.KB = std::max<int64_t>(1, (K + kOzBK - 1) / kOzBK);
     p.tiles = (int64_t)p.MT * p.NT;
-    p.total = p.tiles * p.KB;
-    p.G = (int)std::min<int64_t>(kOzWave, p.total);
+    p.totalg = (int64_t)p.MT * p.KB;
+    p.Gg = (int)std::max<int64_t>(1, std::min<int64_t>(kOzWave / p.NT, p.totalg));
+    p.G = p.Gg * p.NT;
     p.maxseg = 1;
     OzArgs a{};
     a.KB = p.KB;
     a.tiles = p.tiles;
-    a.total = p.total;
+    a.totalg = p.totalg;
     a.G = p.G;
-    for (int c = 0; c < p.G; ++c) {
-        const int64_t lo = oz_lo(c, a), hi = oz_lo(c + 1, a);
+    a.Gg = p.Gg;
+    for (int g = 0; g < p.Gg; ++g) {
+        const int64_t lo = oz_glo(g, a), hi = oz_glo(g + 1, a);
         if (hi > lo) p.maxseg = std::max<int>(p.maxseg, (int)((hi - 1) / p.KB - lo / p.KB + 1));
     }
     return p;
@@ -688,10 +695,11 @@ int oz_run(tsvd_handle* h, const OzPlan& p, const OzView& va, const OzView& vb, 
     a.N = p.N;
     a.KB = p.KB;
     a.tiles = p.tiles;
-    a.total = p.total;
+    a.totalg = p.totalg;
     a.NT = p.NT;
     a.Npad = p.Npad;
     a.G = p.G;
+    a.Gg = p.Gg;
     a.maxseg = p.maxseg;
     a.ea = va.exps;
     a.eb = vb.exps;
