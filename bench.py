@@ -77,6 +77,10 @@ SM_COUNT = 152
 FP64_FLOPS_PER_CLK_PER_SM = 4  # 2 DFMA lanes per SM (measured 2.06 DFMA/clk/SM), 2 flops each
 FP32_FLOPS_PER_CLK_PER_SM = 256  # 128 FFMA lanes per SM, 2 flops each
 OZ_PAIRS = 28  # BF16 digit-pair products per FP64 multiply-add in the sliced product
+# DRAM bytes (read + write) of one sliced A-product launch, from an ncu capture of the
+# same kernel: (m, n, b) -> (bytes, how); profiles/oz_gemm_dense_a_products.md
+SLICED_TRAFFIC = {(20_000, 20_000, 128): (5.94e9, "ncu dram__bytes of the 10,000^2 x 128 launch (1.486 GB) x 4, "
+                                                  "the A entries of the 20,000^2 launch")}
 
 
 def replica_env():
@@ -126,6 +130,9 @@ def _roofline(cfg, dom, ms_cls, fl_cls, by_cls, ln_cls):
         # side, pairs p + q <= 6) per FP64 multiply-add, all on the tensor cores
         bf16 = float(peaks.get("bf16_tflops", 1914.6))
         ach = OZ_PAIRS * fl_cls[dom] / t / 1e12 if t > 0 else 0.0
+        tr = SLICED_TRAFFIC.get((cfg["m"], cfg["n"], cfg.get("b", 0)))
+        if tr is not None:
+            out.update(traffic=tr[0], traffic_note=tr[1])
         out.update(bound="tensor", achieved=ach, peak=bf16, unit="TFLOP/s", frac=ach / bf16,
                    fp64_equiv_tflops=fl_cls[dom] / t / 1e12 if t > 0 else 0.0,
                    peak_note="MEASURED_PEAKS.json bf16_tflops, burst (of measured); achieved counts the "
@@ -445,10 +452,16 @@ def run_case(case):
         else:
             call = lambda: tsvd.dense_mm(A, X)  # noqa: E731
     else:
-        # projected matrix of one restart cycle: 1024 x 1024 lower block bidiagonal (b = 64)
-        B = torch.tril(torch.randn(1024, 1024, dtype=torch.float64, device="cuda", generator=g))
-        B = (B - torch.tril(B, -65) + 24.0 * torch.eye(1024, dtype=torch.float64, device="cuda")).contiguous()
-        call = lambda: tsvd.small_svd(B, nv=64)  # noqa: E731
+        # the small SVD of the dense 20k solve's cycle: order r b = 512 with its spectrum
+        # sigma_i = 1/(1+i)^1.5, seeded orthogonal factors, the leading 128 right vectors
+        import numpy as np
+        n = 512
+        rng = np.random.default_rng(0)
+        Q1 = np.linalg.qr(rng.standard_normal((n, n)))[0]
+        Q2 = np.linalg.qr(rng.standard_normal((n, n)))[0]
+        sv = 1.0 / (1.0 + np.arange(n)) ** 1.5
+        B = torch.from_numpy(np.ascontiguousarray((Q1 * sv) @ Q2.T)).cuda()
+        call = lambda: tsvd.small_svd(B, nv=128)  # noqa: E731
     times = []
     for _ in range(3):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
