@@ -1,27 +1,38 @@
-"""The paper's dense experiment (Sec. 4.2) at its smallest shape on the GPU:
-A 100,000 x 10,000 FP64 with singular values falling from 10 to 1e-14 over the
-first 5,000 (reading of the garbled formula) and Householder-product factors;
+"""The paper's dense experiment (Sec. 4.2) on the GPU: A m x 10,000 FP64 with
+m = 100,000 and 250,000 (the two smallest of the paper's four shapes), singular
+values falling from 10 to 1e-14 over the first 5,000 (reading of the garbled
+formula) and Householder-product factors;
 LancSVD with b = 16, 4 blocks (Krylov dimension 64), p = 1 and 4 cycles, against
 RandSVD with block width 16 after 6 and 24 iterations.  The claim: LancSVD
 reaches RandSVD's accuracy with about 6x fewer iterations (the paper: RandSVD
 p = 6 ~ LancSVD p = 1, RandSVD p = 24 ~ LancSVD p = 4).  Checked as: after p
 cycles LancSVD's R_1 and R_10 (R_j = ||A v_j - s_j u_j|| / s_j) are within 3x of
 RandSVD's after 6p iterations (measured at p = 1: 6.8e-2 vs 6.0e-2 and 1.2e-1 vs
-9.3e-2), with 8p instead of 12p products of width 16."""
+9.3e-2), with 8p instead of 12p products of width 16.
+
+At m = 100,000 both methods are also compared with the FP64 oracle on the same
+matrix and Philox start blocks (one LancSVD cycle, six RandSVD iterations): sigma
+to 1e-10 relative and the singular subspaces to sin-angle 1e-8, the bar of the
+FP64 path.  The two larger shapes (750,000 and 1,000,000 rows) are not run: with
+the digit-plane caches of A (28 bytes an entry, both layouts) they exceed the
+GPU's memory."""
 
 import numpy as np
 import pytest
 
+import oracle
 import workloads
+from helpers import subspace_sin
 
 pytestmark = pytest.mark.gpu
 
 
-def test_paper_dense_experiment_iteration_ratio(tsvd):
+@pytest.mark.parametrize("m", [100_000, 250_000])
+def test_paper_dense_experiment_iteration_ratio(tsvd, m):
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    m, n, k = 100_000, 10_000, 10
+    n, k = 10_000, 10
     A, sig = workloads.dense_householder_spectrum_torch(m, n, seed=6, sigma=workloads.spectrum_paper_dense(n),
                                                         device="cuda")
 
@@ -34,8 +45,32 @@ def test_paper_dense_experiment_iteration_ratio(tsvd):
         rl = tsvd.blanczos(A, k, 16, 4, seed=6, tol=0.0, max_restarts=p - 1)
         rr = tsvd.rsvd(A, k, 6, 6 * p - 1, seed=6)
         Rl, Rr = R(rl), R(rr)
-        lines.append(f"p={p}: LancSVD R1 {Rl[0]:.1e} R10 {Rl[9]:.1e} ({rl.info['ms_total']:.0f} ms, {8 * p} products) | "
+        lines.append(f"m={m} p={p}: LancSVD R1 {Rl[0]:.1e} R10 {Rl[9]:.1e} ({rl.info['ms_total']:.0f} ms, {8 * p} products) | "
                      f"RandSVD {6 * p} iterations R1 {Rr[0]:.1e} R10 {Rr[9]:.1e} ({rr.info['ms_total']:.0f} ms, "
                      f"{12 * p} products)")
         assert Rl[0] <= 3 * max(Rr[0], 1e-13) and Rl[9] <= 3 * max(Rr[9], 1e-13), lines[-1]
     print("\n".join(lines))
+    del A
+    torch.cuda.empty_cache()
+
+
+def test_paper_dense_experiment_matches_oracle(tsvd):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    m, n, k = 100_000, 10_000, 10
+    A, _ = workloads.dense_householder_spectrum_torch(m, n, seed=6, sigma=workloads.spectrum_paper_dense(n),
+                                                      device="cuda")
+    rl = tsvd.blanczos(A, k, 16, 4, seed=6, tol=0.0, max_restarts=0)
+    rr = tsvd.rsvd(A, k, 6, 5, seed=6)
+    An = A.cpu().numpy()
+    del A
+    torch.cuda.empty_cache()
+    outs = {"LancSVD 1 cycle": (rl, oracle.blanczos(An, k, 16, 4, seed=6, tol=0.0, max_restarts=0)),
+            "RandSVD 6 iterations": (rr, oracle.rsvd(An, k, 6, 5, seed=6))}
+    for name, (res, (so, Uo, Vo, info)) in outs.items():
+        s, U, V = (t.detach().cpu().numpy() for t in (res.sigma, res.U, res.V))
+        su, sv = subspace_sin(U, Uo), subspace_sin(V, Vo)
+        print(f"{name}: max rel sigma diff {np.max(np.abs(s - so) / so):.1e}, sin U {su:.1e}, sin V {sv:.1e}")
+        np.testing.assert_allclose(s, so, rtol=1e-10)
+        assert su < 1e-8 and sv < 1e-8, (name, su, sv)
