@@ -137,7 +137,7 @@ def _roofline(cfg, dom, ms_cls, fl_cls, by_cls, ln_cls):
                    fp64_equiv_tflops=fl_cls[dom] / t / 1e12 if t > 0 else 0.0,
                    peak_note="MEASURED_PEAKS.json bf16_tflops, burst (of measured); achieved counts the "
                              f"{OZ_PAIRS} BF16 digit-pair products executed per FP64 multiply-add")
-    elif mixed and name in ("gemm_tn", "gemm_nn"):
+    elif mixed and name in ("gemm_tn", "gemm_nn", "upd_gram"):
         ach = fl_cls[dom] / t / 1e12 if t > 0 else 0.0
         out.update(bound="alu", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak,
                    peak_note="FP32 pipe: 152 SMs x 256 flop/clk x max SM clock (derived)")
@@ -429,6 +429,13 @@ def run_case(case):
         else:
             H = torch.randn(576, 64, dtype=torch.float64, device="cuda", generator=g)
             call = lambda: tsvd.dense_mm(P, H, tensor_cores=True)  # noqa: E731
+    elif case == "updgram":
+        # fused FP32 update + Gram (mixed form's CGS-CQR2) at the power-law solve's left
+        # side: Y - P H and its Gram matrix, q = 2,000,000, s = 512 (mid-cycle), b = 128
+        P = torch.randn(2_000_000, 512, dtype=torch.float32, device="cuda", generator=g)
+        H = torch.randn(512, 128, dtype=torch.float64, device="cuda", generator=g)
+        Y = torch.randn(2_000_000, 128, dtype=torch.float32, device="cuda", generator=g)
+        call = lambda: tsvd.update_gram_f32(P, H, Y, alpha=-1.0, beta=1.0, overwrite_y=True)  # noqa: E731
     elif case == "ozd":
         # dense A X, 10,000 x 10,000 x 128, as an FP64-accurate sliced product (a quarter
         # of the dense 20k workload's A products, for counter captures)
@@ -475,6 +482,11 @@ def run_case(case):
         best = min(times) * 1e-3
         flops = 2.0 * 100_000 * 576 * 64
         info = {"fp64_equiv_tflops": flops / best / 1e12, "bf16_tflops_issued": 28 * flops / best / 1e12}
+    if case == "updgram":
+        best = min(times) * 1e-3
+        q, s_, b = 2_000_000, 512, 128
+        info = {"tflops": (2.0 * q * s_ * b + q * b * (b + 1)) / best / 1e12,
+                "gbs": (4.0 * q * s_ + 8.0 * q * b) / best / 1e9}
     if case in ("tc", "f32", "f64"):
         best = min(times) * 1e-3
         info = {"tflops": 2.0 * 20_000 * 20_000 * 128 / best / 1e12,
@@ -493,7 +505,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clock-ms", type=int, default=200, help="nvidia-smi sampling interval in the timed region")
     ap.add_argument("--case", default=None,
-                    choices=("orth", "svd", "tc", "f32", "f64", "backward", "spmm", "ozt", "ozn", "ozd"),
+                    choices=("orth", "svd", "tc", "f32", "f64", "backward", "spmm", "ozt", "ozn", "ozd", "updgram"),
                     help="run one building block at its benchmark shape (for profiler captures) and exit")
     args = ap.parse_args(argv)
     cfg = WORKLOADS[args.workload]
@@ -588,12 +600,14 @@ def main(argv=None):
 
     # ---- roofline of the dominant kernel class (CUDA events on the launching stream) ----
     from paper_2403_06218_gb300._capi import KERNEL_CLASSES
-    ms_cls = [sum(i["prof_ms"][c] for i in pinfos) for c in range(6)]
-    fl_cls = [sum(i["prof_flops"][c] for i in pinfos) for c in range(6)]
-    by_cls = [sum(i["prof_bytes"][c] for i in pinfos) for c in range(6)]
-    ln_cls = [sum(i["prof_launches"][c] for i in pinfos) for c in range(6)]
+    ncls = len(KERNEL_CLASSES)
+    ms_cls = [sum(i["prof_ms"][c] for i in pinfos) for c in range(ncls)]
+    fl_cls = [sum(i["prof_flops"][c] for i in pinfos) for c in range(ncls)]
+    by_cls = [sum(i["prof_bytes"][c] for i in pinfos) for c in range(ncls)]
+    ln_cls = [sum(i["prof_launches"][c] for i in pinfos) for c in range(ncls)]
     ms_prof = sum(i["ms_total"] for i in pinfos)
-    dom = max(range(5), key=lambda c: ms_cls[c])
+    # the dominant class among the method's kernels ("other" collects copies and set-up)
+    dom = max((c for c in range(ncls) if KERNEL_CLASSES[c] != "other"), key=lambda c: ms_cls[c])
     roofline = _roofline(cfg, dom, ms_cls, fl_cls, by_cls, ln_cls)
     roofline["share_of_step"] = ms_cls[dom] / ms_prof if ms_prof > 0 else None
     roofline["profiled_steps"] = len(pinfos)
@@ -601,7 +615,7 @@ def main(argv=None):
         KERNEL_CLASSES[c]: {"launches": ln_cls[c], "ms": ms_cls[c],
                             "tflops": fl_cls[c] / (ms_cls[c] * 1e-3) / 1e12 if ms_cls[c] > 0 else None,
                             "gbs": by_cls[c] / (ms_cls[c] * 1e-3) / 1e9 if ms_cls[c] > 0 else None}
-        for c in range(6)}
+        for c in range(ncls)}
 
     line = {
         "metric": METRIC, "value": ms_step / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,

@@ -111,7 +111,9 @@ typedef struct tsvd_matrix {
 #define TSVD_K_SVD      4   /* small Jacobi SVD (flops: 12 n per rotation, 18 n with V,
                                n(n-1)/2 rotations a sweep, times the sweeps it took)    */
 #define TSVD_K_OTHER    5   /* start block, transpose build, residuals, copies            */
-#define TSVD_K_COUNT    6
+#define TSVD_K_UPD_GRAM 6   /* fused update + Gram of FP32 blocks (mixed form): Q - P H or
+                               Q L^{-T} together with the Gram matrix of the result       */
+#define TSVD_K_COUNT    7
 
 /* Options; fill with tsvd_default_opts() and override fields. */
 typedef struct tsvd_opts {
@@ -431,6 +433,37 @@ int tsvd_cgs_cqr2(tsvd_handle* h, int64_t q, int64_t s, int b, const double* P, 
                   double* Y, int64_t ldy, double* H, double* R,
                   uint64_t seed, int* replacements, int* breakdowns,
                   void* ws, size_t ws_bytes, void* stream);
+
+/* CGS-CQR2 (Alg. 5; s = 0: CholeskyQR2, Alg. 4) on FP32 blocks, as the
+ * mixed-precision form runs it: P (q x s, ldp) and Y (q x b, ldy) FP32 (device);
+ * H (s x b, ld = b, may be NULL) and R (b x b, ld = b) FP64, with the meaning,
+ * breakdown fallback and seed/replacement rules of tsvd_cgs_cqr2.  The products
+ * read FP32 blocks and accumulate in FP32 within a row slab; Gram matrices,
+ * projection coefficients, Cholesky factors, H and R are FP64.  Each update
+ * (Y - P H, and with s = 0 the first Y L^{-T}) runs as one fused pass with the
+ * Gram matrix of its result (tsvd_update_gram_f32).  Workspace:
+ * tsvd_orth_workspace(q, s, b).  Synchronises `stream` before returning. */
+int tsvd_cgs_cqr2_f32(tsvd_handle* h, int64_t q, int64_t s, int b, const float* P, int64_t ldp,
+                      float* Y, int64_t ldy, double* H, double* R,
+                      uint64_t seed, int* replacements, int* breakdowns,
+                      void* ws, size_t ws_bytes, void* stream);
+
+/* Fused update + Gram of an FP32 block (the update of Alg. 5 S2/S7, Y - P H, or
+ * the Y L^{-T} of Alg. 4, together with the Gram matrix that the next CholeskyQR
+ * step factors, Sec. 3.2-3.3), in one pass over the rows of Y:
+ *   Y (q x b, ldy, FP32) <- beta Y + alpha X M,   X (q x s, ldx, FP32),
+ *                                                  M (s x b, ldm, FP64, rounded to FP32),
+ *   W (b x b, ld = b, FP64, both halves) = Y^T Y of the updated Y.
+ * upper != 0: M is upper triangular (entries below its diagonal are not read).
+ * Y may be X itself (s == b, ldx == ldy): the update is done in place.  Y gets the
+ * same bits as the unfused FP32 product; W sums FP32 products over a row slab and
+ * the slabs in FP64 in a fixed order (bitwise reproducible).  1 <= b <= 128,
+ * s >= 1.  All pointers are device memory owned by the caller; ws holds
+ * tsvd_update_gram_f32_workspace(q, b) bytes.  Asynchronous on `stream`. */
+int tsvd_update_gram_f32_workspace(int64_t q, int b, size_t* bytes);
+int tsvd_update_gram_f32(tsvd_handle* h, int64_t q, int64_t s, int b, double alpha, const float* X, int64_t ldx,
+                         const double* M, int64_t ldm, double beta, float* Y, int64_t ldy, int upper,
+                         double* W, void* ws, size_t ws_bytes, void* stream);
 
 /* CGS-QR, Alg. 3 (Sec. 3.1): QR of Y (q x r) by column blocks of width b
  * (the last one narrower if b does not divide r): Y <- Q in place, R (r x r,

@@ -24,6 +24,7 @@ from .api import (  # noqa: F401
     mm_bf16x6,
     cholqr2,
     cgs_cqr2,
+    update_gram_f32,
     cgs_qr,
     small_svd,
     handle,
@@ -35,7 +36,7 @@ from .api import (  # noqa: F401
 
 __all__ = [
     "TsvdError", "CsrMatrix", "SvdResult", "blanczos", "rsvd", "gaussian_block", "csr_transpose", "spmm",
-    "dense_mm", "svd_backward", "truncated_svd", "Bf16x3", "bf16x3_split", "mm_bf16x6", "cholqr2", "cgs_cqr2", "cgs_qr", "small_svd", "handle", "wait_limit", "RowPartition", "torch_allreduce",
+    "dense_mm", "svd_backward", "truncated_svd", "Bf16x3", "bf16x3_split", "mm_bf16x6", "cholqr2", "cgs_cqr2", "update_gram_f32", "cgs_qr", "small_svd", "handle", "wait_limit", "RowPartition", "torch_allreduce",
     "row_block", "load",
     "LIB_PATH",
 ]

@@ -33,7 +33,7 @@ TSVD_MAX_SMALL_SVD = 2048
 TSVD_FLAG_PROFILE = 1
 TSVD_FLAG_ROW_PARTITION = 2
 TSVD_NOALLOC_SCRATCH_BYTES = 4 * 1024 * 1024
-KERNEL_CLASSES = ("a_products", "gemm_tn", "gemm_nn", "chol", "svd", "other")
+KERNEL_CLASSES = ("a_products", "gemm_tn", "gemm_nn", "chol", "svd", "other", "upd_gram")
 
 
 class TsvdMatrix(C.Structure):
@@ -60,8 +60,8 @@ class TsvdInfo(C.Structure):
         ("converged", C.c_int32), ("transposed", C.c_int32), ("svd_sweeps", C.c_int32),
         ("resid_max", C.c_double), ("rho_last", C.c_double),
         ("ms_total", C.c_double), ("ms_transpose", C.c_double), ("kernel_launches", C.c_int64),
-        ("prof_launches", C.c_int64 * 6), ("prof_ms", C.c_double * 6),
-        ("prof_flops", C.c_double * 6), ("prof_bytes", C.c_double * 6),
+        ("prof_launches", C.c_int64 * 7), ("prof_ms", C.c_double * 7),
+        ("prof_flops", C.c_double * 7), ("prof_bytes", C.c_double * 7),
     ]
 
     def as_dict(self):
@@ -128,6 +128,11 @@ SIGNATURES = [
     ("tsvd_orth_workspace", _I, [_I64, _I64, _I, _PSZ]),
     ("tsvd_cholqr2", _I, [_P, _I64, _I, _P, _I64, _P, C.c_uint64, _PI, _PI, _P, _SZ, _P]),
     ("tsvd_cgs_cqr2", _I, [_P, _I64, _I64, _I, _P, _I64, _P, _I64, _P, _P, C.c_uint64, _PI, _PI, _P, _SZ, _P]),
+    ("tsvd_cgs_cqr2_f32", _I, [_P, _I64, _I64, _I, _P, _I64, _P, _I64, _P, _P, C.c_uint64, _PI, _PI, _P, _SZ,
+                               _P]),
+    ("tsvd_update_gram_f32_workspace", _I, [_I64, _I, _PSZ]),
+    ("tsvd_update_gram_f32", _I, [_P, _I64, _I64, _I, C.c_double, _P, _I64, _P, _I64, C.c_double, _P, _I64, _I,
+                                  _P, _P, _SZ, _P]),
     ("tsvd_cgs_qr", _I, [_P, _I64, _I, _I, _P, _I64, _P, C.c_uint64, _PI, _PI, _P, _SZ, _P]),
     ("tsvd_small_svd_workspace", _I, [_I, _PSZ]),
     ("tsvd_small_svd", _I, [_P, _I, _P, _I64, _I, _P, _P, _P, _PI, _P, _SZ, _P]),

@@ -613,14 +613,28 @@ def cholqr2(Y: torch.Tensor, seed: int = 0):
     return Q, R, bd.value
 
 
+def _cuda_f32(t: torch.Tensor, name: str):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.dim() == 2
+            and t.stride(1) == 1):
+        raise TypeError(f"{name} must be a row-major float32 CUDA matrix")
+
+
 def cgs_cqr2(Y: torch.Tensor, P: torch.Tensor, seed: int = 0):
-    """CGS-CQR2 (Alg. 5) of a copy of Y against P: returns (Q, H, R, breakdowns)."""
+    """CGS-CQR2 (Alg. 5) of a copy of Y against P: returns (Q, H, R, breakdowns).
+    float32 Y and P run the mixed form's FP32-block variant (tsvd_cgs_cqr2_f32;
+    H and R are float64 either way); P may have 0 columns (CholeskyQR2)."""
     lib = capi.load()
     if not (isinstance(Y, torch.Tensor) and Y.dim() == 2):
         raise TypeError("Y must be a 2-D tensor")
     _check_rows(P, Y.shape[0], "P")
-    _cuda_f64(Y, "Y")
-    _cuda_f64(P, "P")
+    if Y.dtype == torch.float32:
+        _cuda_f32(Y, "Y")
+        _cuda_f32(P, "P")
+        fn, name = lib.tsvd_cgs_cqr2_f32, "tsvd_cgs_cqr2_f32"
+    else:
+        _cuda_f64(Y, "Y")
+        _cuda_f64(P, "P")
+        fn, name = lib.tsvd_cgs_cqr2, "tsvd_cgs_cqr2"
     dev = Y.device
     _same_device(dev, (P, "P"))
     Q = Y.clone()
@@ -631,10 +645,49 @@ def cgs_cqr2(Y: torch.Tensor, P: torch.Tensor, seed: int = 0):
     rep, bd = C.c_int(0), C.c_int(0)
     with torch.cuda.device(dev):
         ws = _orth_ws(q, s, b, dev)
-        capi.check(lib.tsvd_cgs_cqr2(handle(dev), q, s, b, P.data_ptr(), P.stride(0), Q.data_ptr(), Q.stride(0),
-                                     H.data_ptr(), R.data_ptr(), C.c_uint64(seed), C.byref(rep), C.byref(bd),
-                                     ws.data_ptr(), ws.numel(), _stream_ptr(dev)), "tsvd_cgs_cqr2")
+        capi.check(fn(handle(dev), q, s, b, P.data_ptr(), max(P.stride(0), s), Q.data_ptr(), Q.stride(0),
+                      H.data_ptr(), R.data_ptr(), C.c_uint64(seed), C.byref(rep), C.byref(bd),
+                      ws.data_ptr(), ws.numel(), _stream_ptr(dev)), name)
     return Q, H[:s], R, bd.value
+
+
+def update_gram_f32(X: torch.Tensor, M: torch.Tensor, Y: Optional[torch.Tensor] = None, alpha: float = 1.0,
+                    beta: float = 0.0, upper: bool = False, in_place: bool = False, overwrite_y: bool = False):
+    """Fused update + Gram of FP32 blocks (tsvd_update_gram_f32): returns (Y', W) with
+    Y' = beta Y + alpha X M (FP32) and W = Y'^T Y' (float64).  Y' is a new tensor
+    (a copy of Y, or zeros when Y is None) unless ``overwrite_y`` (Y itself is updated)
+    or ``in_place`` (X itself is updated; M square, Y unused)."""
+    lib = capi.load()
+    _cuda_f32(X, "X")
+    _cuda_f64(M, "M")
+    dev = X.device
+    _same_device(dev, (M, "M"))
+    q, s = X.shape
+    if M.shape[0] != s:
+        raise ValueError(f"M must have {s} rows")
+    b = M.shape[1]
+    if in_place:
+        if s != b:
+            raise ValueError("an in-place update needs a square M")
+        Yo = X
+    elif Y is None:
+        Yo = torch.zeros((q, b), dtype=torch.float32, device=dev)
+    else:
+        _cuda_f32(Y, "Y")
+        _check_rows(Y, q, "Y")
+        if Y.shape[1] != b:
+            raise ValueError(f"Y must have {b} columns")
+        Yo = Y if overwrite_y else Y.clone()
+    W = torch.empty((b, b), dtype=torch.float64, device=dev)
+    nb = C.c_size_t()
+    capi.check(lib.tsvd_update_gram_f32_workspace(q, b, C.byref(nb)), "tsvd_update_gram_f32_workspace")
+    with torch.cuda.device(dev):
+        ws = _ws(nb.value, dev)
+        capi.check(lib.tsvd_update_gram_f32(handle(dev), q, s, b, float(alpha), X.data_ptr(), X.stride(0),
+                                            M.data_ptr(), M.stride(0), float(beta), Yo.data_ptr(), Yo.stride(0),
+                                            int(bool(upper)), W.data_ptr(), ws.data_ptr(), ws.numel(),
+                                            _stream_ptr(dev)), "tsvd_update_gram_f32")
+    return Yo, W
 
 
 def cgs_qr(Y: torch.Tensor, b: int, seed: int = 0):

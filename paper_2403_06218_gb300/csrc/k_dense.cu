@@ -132,10 +132,9 @@ struct TnPlan {
 };
 
 // One full wave of the kernel on a 152-SM GB300: 7 resident CTAs per SM for the
-// FP64 kernel (its 72 registers x 128 threads and 16 KB of shared memory allow 7).
-// The FP32 target assumes 16 CTAs of the 64-thread FP32 kernel; at its 72
-// registers only 14 are resident, so the last eighth of that split runs as a
-// short second wave.  Splitting K so that regions x slabs fills
+// FP64 kernel (its 72 registers x 128 threads and 16 KB of shared memory allow 7),
+// 16 for the 64-thread FP32 kernel (bounded to 64 registers, which it fits without
+// spilling).  Splitting K so that regions x slabs fills
 // exactly one wave keeps every SM equally busy; a fixed target (rather than the
 // device's SM count) keeps the split, the workspace size and the summation order
 // independent of the device.
@@ -556,6 +555,55 @@ cudaError_t gemm_tn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, const TI* X
     const int64_t tot = s * b;
     gemm_tn_reduce_kernel<TC><<<(unsigned)((tot + 31) / 32), dim3(32, 8), 0, st>>>(s, b, p.slabs, partial, stride, C,
                                                                                   ldc, symmetric ? 1 : 0);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Fused update + Gram of FP32 blocks.  One CTA per slab of consecutive 64-row
+// tiles; the split targets one wave of the kernel's resident 256-thread CTAs on
+// 152 SMs: 4 per SM for b <= 64, 2 for b <= 128 (a fixed target, so the split, the
+// workspace and the summation order do not depend on the device).
+struct UgPlan {
+    int slabs;
+    int64_t slab_rows;
+};
+
+static UgPlan ug_plan(int64_t q, int64_t b) {
+    UgPlan p;
+    const int64_t wave = 152 * (b <= 64 ? 4 : 2);
+    int64_t tiles = (q + 63) / 64;
+    if (tiles < 1) tiles = 1;
+    const int64_t slabs = tiles < wave ? tiles : wave;
+    p.slab_rows = (tiles + slabs - 1) / slabs * 64;
+    p.slabs = (int)((q + p.slab_rows - 1) / p.slab_rows);
+    if (p.slabs < 1) p.slabs = 1;
+    return p;
+}
+
+size_t update_gram_ws(int64_t q, int64_t b) {
+    return align256(sizeof(double) * (size_t)ug_plan(q, b).slabs * (size_t)b * (size_t)b);
+}
+
+cudaError_t update_gram(tsvd_handle* h, int64_t q, int64_t s, int64_t b, double alpha, const float* X, int64_t ldx,
+                        const double* M, int64_t ldm, double beta, float* Y, int64_t ldy, bool upper, double* W,
+                        double* partial, cudaStream_t st) {
+    if (b < 1 || b > 128 || s < 1) return cudaErrorInvalidValue;
+    if (q == 0) return cudaMemsetAsync(W, 0, sizeof(double) * (size_t)b * b, st);
+    const UgPlan p = ug_plan(q, b);
+    // algorithmic work: the update (2qsb, or q b (b+1) for a triangular M) plus the
+    // upper half of the Gram matrix, q b (b+1); compulsory traffic: X and M read,
+    // Y read (beta != 0, unless it is X) and written, W written
+    const bool alias = (const void*)X == (const void*)Y;
+    const double upd = upper ? (double)q * b * (b + 1) : 2.0 * q * s * b;
+    const double bytes = 4.0 * q * s + ((beta != 0.0 && !alias) ? 4.0 * q * b : 0.0) + 4.0 * q * b +
+                         8.0 * s * b + 8.0 * b * b;
+    ProfScope prof(h, TSVD_K_UPD_GRAM, upd + (double)q * b * (b + 1), bytes, st);
+    h->launches += 2;
+    cudaError_t e = launch_update_gram_f32<double>(st, p.slabs, p.slab_rows, q, s, b, alpha, X, ldx, M, ldm, beta, Y,
+                                                   ldy, upper, partial);
+    if (e != cudaSuccess) return e;
+    gemm_tn_reduce_kernel<double><<<(unsigned)((b * b + 31) / 32), dim3(32, 8), 0, st>>>(b, b, p.slabs, partial,
+                                                                                         b * b, W, b, 1);
     return cudaGetLastError();
 }
 

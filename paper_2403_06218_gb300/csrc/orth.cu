@@ -14,6 +14,7 @@
 // FP32 blocks but every Gram matrix, projection coefficient, Cholesky factor and R
 // stays FP64 (split-K partial sums are reduced in FP64).
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "tsvd_internal.cuh"
@@ -89,6 +90,7 @@ OrthWs<T> carve(tsvd_handle* h, Arena& ar, int64_t q, int64_t s, int b) {
     }
     for (int j = 1; j <= b; ++j) upd(gemm_tn_ws(h, q, j, 1, false, eb));
     upd(gemm_tn_ws(h, q, 1, 1, true, eb));
+    if (eb == 4) upd(update_gram_ws(q, b));
     w.partial = ar.take<double>(pbytes / sizeof(double) + 1);
     w.save = ar.take<T>((size_t)q * b);
     w.fcol = ar.take<T>((size_t)q);
@@ -112,6 +114,49 @@ int cholqr_step(tsvd_handle* h, int64_t q, int b, T* Y, int64_t ldy, double* W, 
     TSVD_TRY_CUDA(chol_inv(h, b, W, Lt, Mt, status, st));
     TSVD_TRY_CUDA(gemm_nn(h, q, b, b, 1.0, Y, ldy, Mt, b, 0.0, Y, ldy, true, st));
     return TSVD_OK;
+}
+
+// CGS-CQR2 (Alg. 5) on FP32 blocks with the fused update + Gram pass: per CGS
+// pass, the projection H = P^T Y is its own pass (split-K over the rows), then one
+// pass forms Y - P H and the Gram matrix of the result, whose Cholesky factor
+// normalises the block.  Without P (s = 0: CholeskyQR2, Alg. 4) the first step's
+// Y L^{-T} is fused with the second step's Gram matrix instead.
+//
+// The second projection is not folded into the first pass (P^T of the unnormalised
+// Y - P H, then multiplied by L^{-T}): that product misses the rounding committed
+// when Y L^{-T} is formed, which is of order eps cond(Y - P H), so the result would be
+// orthogonal to P only to that level instead of to eps.  Alg. 5 projects the
+// normalised block, and so does this sequence.
+template <typename T>
+int fused_cgs_cqr2_f32(tsvd_handle* h, int64_t q, int64_t s, int b, const T* P, int64_t ldp, T* Y, int64_t ldy,
+                       OrthWs<T>& w, int* status, const OrthCtx& ctx, cudaStream_t st) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (s > 0) {
+            TSVD_TRY_CUDA(gemm_tn(h, q, s, b, P, ldp, Y, ldy, w.H1, b, false, w.partial, st));        // S1
+            if (ctx.reduce) TSVD_TRY(part_sum(h, w.H1, s, b, b, st));
+            TSVD_TRY_CUDA(update_gram(h, q, s, b, -1.0, P, ldp, w.H1, b, 1.0, Y, ldy, false, w.W, w.partial,
+                                      st));                                                             // S2, S3
+            if (ctx.reduce) TSVD_TRY(part_sum(h, w.W, b, b, b, st));
+            TSVD_TRY_CUDA(chol_inv(h, b, w.W, w.Lt1, w.Mt1, status, st));                              // S4
+            TSVD_TRY_CUDA(gemm_nn(h, q, b, b, 1.0, Y, ldy, w.Mt1, b, 0.0, Y, ldy, true, st));          // S5
+            TSVD_TRY_CUDA(gemm_tn(h, q, s, b, P, ldp, Y, ldy, w.H2, b, false, w.partial, st));        // S6
+            if (ctx.reduce) TSVD_TRY(part_sum(h, w.H2, s, b, b, st));
+            TSVD_TRY_CUDA(update_gram(h, q, s, b, -1.0, P, ldp, w.H2, b, 1.0, Y, ldy, false, w.W, w.partial,
+                                      st));                                                             // S7, S8
+        } else {
+            TSVD_TRY_CUDA(gemm_tn(h, q, b, b, Y, ldy, Y, ldy, w.W, b, true, w.partial, st));          // S3
+            if (ctx.reduce) TSVD_TRY(part_sum(h, w.W, b, b, b, st));
+            TSVD_TRY_CUDA(chol_inv(h, b, w.W, w.Lt1, w.Mt1, status, st));                              // S4
+            TSVD_TRY_CUDA(update_gram(h, q, b, b, 1.0, Y, ldy, w.Mt1, b, 0.0, Y, ldy, true, w.W, w.partial,
+                                      st));                                                             // S5, S8
+        }
+        if (ctx.reduce) TSVD_TRY(part_sum(h, w.W, b, b, b, st));
+        TSVD_TRY_CUDA(chol_inv(h, b, w.W, w.Lt2, w.Mt2, status, st));                                  // S9
+        TSVD_TRY_CUDA(gemm_nn(h, q, b, b, 1.0, Y, ldy, w.Mt2, b, 0.0, Y, ldy, true, st));              // S10
+        return TSVD_OK;
+    } else {
+        return TSVD_ERR_UNSUPPORTED;
+    }
 }
 
 // v -= [P, Yprev] ([P, Yprev]^T v), twice; accumulating coefficients when asked.
@@ -206,10 +251,13 @@ int read_status(cudaStream_t st, const int* d_status, int* h_status) {
     return TSVD_OK;
 }
 
+// Covers both block types: FP32 blocks take half the copies but a wider split-K
+// plan and the fused update + Gram partials.
 size_t orth_ws(tsvd_handle* h, int64_t q, int64_t s, int b) {
-    Arena ar;
-    carve<double>(h, ar, q, s, b);
-    return ar.off;
+    Arena a64, a32;
+    carve<double>(h, a64, q, s, b);
+    carve<float>(h, a32, q, s, b);
+    return a64.off > a32.off ? a64.off : a32.off;
 }
 
 template <typename T>
@@ -220,18 +268,25 @@ int cgs_cqr2(tsvd_handle* h, int64_t q, int64_t s, int b, const T* P, int64_t ld
     OrthWs<T> w = carve<T>(h, ar, q, s, b);
     if (!ar.fits()) return TSVD_ERR_WORKSPACE;
     TSVD_TRY_CUDA(copy_block(Y, ldy, w.save, b, q, b, st));
-    if (s > 0) {
-        TSVD_TRY_CUDA(gemm_tn(h, q, s, b, P, ldp, Y, ldy, w.H1, b, false, w.partial, st));           // S1
-        if (ctx.reduce) TSVD_TRY(part_sum(h, w.H1, s, b, b, st));
-        TSVD_TRY_CUDA(gemm_nn(h, q, s, b, -1.0, P, ldp, w.H1, b, 1.0, Y, ldy, false, st));           // S2
+    if constexpr (std::is_same<T, float>::value) {
+        // FP32 blocks: each update is fused with the Gram matrix of its result (one
+        // pass over the rows; update_gram).  The projections stay separate passes: the
+        // second one must see the normalised block (see fused_cgs_cqr2_f32).
+        TSVD_TRY(fused_cgs_cqr2_f32(h, q, s, b, P, ldp, Y, ldy, w, status, ctx, st));
+    } else {
+        if (s > 0) {
+            TSVD_TRY_CUDA(gemm_tn(h, q, s, b, P, ldp, Y, ldy, w.H1, b, false, w.partial, st));       // S1
+            if (ctx.reduce) TSVD_TRY(part_sum(h, w.H1, s, b, b, st));
+            TSVD_TRY_CUDA(gemm_nn(h, q, s, b, -1.0, P, ldp, w.H1, b, 1.0, Y, ldy, false, st));       // S2
+        }
+        TSVD_TRY(cholqr_step(h, q, b, Y, ldy, w.W, w.Lt1, w.Mt1, w.partial, status, ctx, st));  // S3-S5
+        if (s > 0) {
+            TSVD_TRY_CUDA(gemm_tn(h, q, s, b, P, ldp, Y, ldy, w.H2, b, false, w.partial, st));       // S6
+            if (ctx.reduce) TSVD_TRY(part_sum(h, w.H2, s, b, b, st));
+            TSVD_TRY_CUDA(gemm_nn(h, q, s, b, -1.0, P, ldp, w.H2, b, 1.0, Y, ldy, false, st));       // S7
+        }
+        TSVD_TRY(cholqr_step(h, q, b, Y, ldy, w.W, w.Lt2, w.Mt2, w.partial, status, ctx, st));  // S8-S10
     }
-    TSVD_TRY(cholqr_step(h, q, b, Y, ldy, w.W, w.Lt1, w.Mt1, w.partial, status, ctx, st));  // S3-S5
-    if (s > 0) {
-        TSVD_TRY_CUDA(gemm_tn(h, q, s, b, P, ldp, Y, ldy, w.H2, b, false, w.partial, st));           // S6
-        if (ctx.reduce) TSVD_TRY(part_sum(h, w.H2, s, b, b, st));
-        TSVD_TRY_CUDA(gemm_nn(h, q, s, b, -1.0, P, ldp, w.H2, b, 1.0, Y, ldy, false, st));           // S7
-    }
-    TSVD_TRY(cholqr_step(h, q, b, Y, ldy, w.W, w.Lt2, w.Mt2, w.partial, status, ctx, st));  // S8-S10
     TSVD_TRY_CUDA(trmm_upper(h, b, w.Lt2, w.Lt1, R, ldr, r_trans, st));                         // S11
     if (H != nullptr && s > 0) {                                                                 // S12
         TSVD_TRY_CUDA(copy_block(w.H1, b, H, b, s, b, st));

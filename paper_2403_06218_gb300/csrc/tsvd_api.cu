@@ -526,7 +526,9 @@ int tsvd_orth_workspace(int64_t q, int64_t s, int b, size_t* bytes) {
     return TSVD_OK;
 }
 
-static int orth_entry(tsvd_handle* h, int64_t q, int64_t s, int b, const double* P, int64_t ldp, double* Y,
+extern "C++" {
+template <typename T>
+int orth_entry(tsvd_handle* h, int64_t q, int64_t s, int b, const T* P, int64_t ldp, T* Y,
                       int64_t ldy, double* H, double* R, uint64_t seed, int* replacements, int* breakdowns, void* ws,
                       size_t ws_bytes, void* stream) {
     if (!h || b < 1 || q < b || s < 0 || !Y || !R || ldy < b) return TSVD_ERR_INVALID_ARG;
@@ -544,23 +546,54 @@ static int orth_entry(tsvd_handle* h, int64_t q, int64_t s, int b, const double*
     ctx.seed = seed;
     ctx.replacements = replacements ? *replacements : 0;
     TSVD_TRY_CUDA(cudaMemsetAsync(R, 0, sizeof(double) * (size_t)b * b, st));
-    int rc = cgs_cqr2<double>(h, q, s, b, P, ldp, Y, ldy, H, R, b, false, ctx, ar, status, st);
+    int rc = cgs_cqr2<T>(h, q, s, b, P, ldp, Y, ldy, H, R, b, false, ctx, ar, status, st);
     TSVD_TRY_CUDA(cudaStreamSynchronize(st));
     if (replacements) *replacements = ctx.replacements;
     if (breakdowns) *breakdowns += ctx.fallbacks;
     return rc;
 }
+}  // extern "C++"
 
 int tsvd_cholqr2(tsvd_handle* h, int64_t q, int b, double* Y, int64_t ldy, double* R, uint64_t seed,
                  int* replacements, int* breakdowns, void* ws, size_t ws_bytes, void* stream) {
-    return orth_entry(h, q, 0, b, nullptr, 0, Y, ldy, nullptr, R, seed, replacements, breakdowns, ws, ws_bytes,
-                      stream);
+    return orth_entry(h, q, 0, b, (const double*)nullptr, 0, Y, ldy, nullptr, R, seed, replacements, breakdowns, ws,
+                      ws_bytes, stream);
 }
 
 int tsvd_cgs_cqr2(tsvd_handle* h, int64_t q, int64_t s, int b, const double* P, int64_t ldp, double* Y, int64_t ldy,
                   double* H, double* R, uint64_t seed, int* replacements, int* breakdowns, void* ws,
                   size_t ws_bytes, void* stream) {
     return orth_entry(h, q, s, b, P, ldp, Y, ldy, H, R, seed, replacements, breakdowns, ws, ws_bytes, stream);
+}
+
+int tsvd_cgs_cqr2_f32(tsvd_handle* h, int64_t q, int64_t s, int b, const float* P, int64_t ldp, float* Y,
+                      int64_t ldy, double* H, double* R, uint64_t seed, int* replacements, int* breakdowns, void* ws,
+                      size_t ws_bytes, void* stream) {
+    return orth_entry(h, q, s, b, P, ldp, Y, ldy, H, R, seed, replacements, breakdowns, ws, ws_bytes, stream);
+}
+
+int tsvd_update_gram_f32_workspace(int64_t q, int b, size_t* bytes) {
+    if (!bytes || q < 0 || b < 1) return TSVD_ERR_INVALID_ARG;
+    if (b > 128) return TSVD_ERR_UNSUPPORTED;
+    *bytes = update_gram_ws(q, b);
+    return TSVD_OK;
+}
+
+int tsvd_update_gram_f32(tsvd_handle* h, int64_t q, int64_t s, int b, double alpha, const float* X, int64_t ldx,
+                         const double* M, int64_t ldm, double beta, float* Y, int64_t ldy, int upper, double* W,
+                         void* ws, size_t ws_bytes, void* stream) {
+    if (!h || q < 0 || s < 1 || b < 1 || !X || !M || !Y || !W || ldx < s || ldm < b || ldy < b)
+        return TSVD_ERR_INVALID_ARG;
+    if (b > 128) return TSVD_ERR_UNSUPPORTED;
+    if ((const void*)X == (const void*)Y && (s != b || ldx != ldy)) return TSVD_ERR_INVALID_ARG;
+    size_t need = 0;
+    TSVD_TRY(tsvd_update_gram_f32_workspace(q, b, &need));
+    TSVD_TRY(check_ws(ws, ws_bytes, need));
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    TSVD_TRY_CUDA(update_gram(h, q, s, b, alpha, X, ldx, M, ldm, beta, Y, ldy, upper != 0, W,
+                              static_cast<double*>(ws), st));
+    return TSVD_OK;
 }
 
 int tsvd_cgs_qr(tsvd_handle* h, int64_t q, int r, int b, double* Y, int64_t ldy, double* R, uint64_t seed,

@@ -265,6 +265,20 @@ cudaError_t tc_mm(tsvd_handle* h, int64_t rows, int64_t cols, const void* pieces
 template <typename TM, typename TY>
 cudaError_t launch_gemm_nn_f32(cudaStream_t st, int64_t q, int64_t s, int64_t b, double alpha, const float* X,
                                int64_t ldx, const TM* M, int64_t ldm, double beta, TY* Y, int64_t ldy, bool upper);
+// Fused update + Gram of FP32 blocks (k_f32.cu kernel, k_dense.cu host side):
+//   Y (q x b, ldy) = beta Y + alpha X M  (X q x s FP32, M s x b FP64; upper as in gemm_nn),
+//   W (b x b, ld b, FP64, both halves) = Y^T Y of the updated Y,
+// in one pass over the rows; Y may alias X (s == b, ldx == ldy).  b <= 128.
+// Partial Gram sums per row slab go to `partial` (update_gram_ws bytes) and are
+// reduced in a fixed order.
+size_t update_gram_ws(int64_t q, int64_t b);
+cudaError_t update_gram(tsvd_handle* h, int64_t q, int64_t s, int64_t b, double alpha, const float* X, int64_t ldx,
+                        const double* M, int64_t ldm, double beta, float* Y, int64_t ldy, bool upper, double* W,
+                        double* partial, cudaStream_t st);
+template <typename TM>
+cudaError_t launch_update_gram_f32(cudaStream_t st, int slabs, int64_t slab_rows, int64_t q, int64_t s, int64_t b,
+                                   double alpha, const float* X, int64_t ldx, const TM* M, int64_t ldm, double beta,
+                                   float* Y, int64_t ldy, bool upper, double* partial);
 template <typename TI, typename TC>
 cudaError_t gemm_tn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, const TI* X, int64_t ldx,
                     const TI* Z, int64_t ldz, TC* C, int64_t ldc, bool symmetric,

@@ -2,8 +2,10 @@
 ptxas's resource report (nvcc -Xptxas -v, the flags of the library build).
 
 * No kernel spills registers to local memory.
-* The FP64 split-K Gram/projection kernel fits 7 CTAs per SM: its split is sized
-  to one wave of 152 x 7 CTAs.
+* The FP64 split-K Gram/projection kernel fits 7 CTAs per SM and the FP32 one 16:
+  their splits are sized to one wave of 152 x 7 (152 x 16) CTAs.
+* The fused FP32 update + Gram kernel fits 4 CTAs of 256 threads per SM for
+  blocks of up to 64 columns and 2 for up to 128, as its slab plan assumes.
 * The tensor-core product kernel's 320 threads fit its registers in one SM.
 """
 
@@ -89,6 +91,21 @@ def test_no_kernel_spills(kernels):
 def test_fp64_split_k_kernel_fits_its_wave(kernels):
     k = _one(kernels, r"gemm_tn_kernelIddE")
     assert _resident_ctas(k["regs"], 128, k["smem"]) >= 7, k
+
+
+def test_fp32_split_k_kernel_fits_its_wave(kernels):
+    # the FP32 split plan targets one wave of 152 x 16 CTAs of 64 threads
+    for name in (r"gemm_tn_f32_kernelIdE", r"gemm_tn_f32_kernelIfE"):
+        k = _one(kernels, name)
+        assert _resident_ctas(k["regs"], 64, k["smem"]) >= 16, k
+
+
+def test_fused_update_gram_kernel_fits_its_wave(kernels):
+    # its slab plan targets one wave of 152 x 4 CTAs of 256 threads for b <= 64 and
+    # 152 x 2 for b <= 128
+    for name, ctas in ((r"update_gram_f32_kernelILi1E", 4), (r"update_gram_f32_kernelILi2E", 2)):
+        k = _one(kernels, name)
+        assert _resident_ctas(k["regs"], 256, k["smem"]) >= ctas, k
 
 
 def test_tensor_core_kernel_fits_one_sm(kernels):
