@@ -791,7 +791,7 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
             }
             {
                 Arena sv = ar;
-                TSVD_TRY(small_svd(h, d, B, rb, Ub, sig, Vb, nv, sv, status, st, ctx.deferred));        // S6
+                TSVD_TRY(small_svd(h, d, B, rb, Ub, sig, Vb, nv, sv, status, st, ctx.deferred, o->tol));  // S6
             }
             TSVD_TRY_CUDA(lanczos_rho(h, b, k, Rr, Vb + (int64_t)(d - b) * d, d, rho, st));
             TSVD_TRY_CUDA(cudaMemcpyAsync(hrho.data(), rho, sizeof(double) * k, cudaMemcpyDeviceToHost, st));

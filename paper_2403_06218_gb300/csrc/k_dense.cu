@@ -4,7 +4,8 @@
 //   gemm_nn   Y = b Y + a X M  update Q - P H (Alg. 5 S2/S7), TRSM applied as the
 //                              product with L^{-T} (Alg. 4 S3/S6, Alg. 5 S5/S10),
 //                              Ritz/restart products (Alg. 1 S6/S7, Alg. 2 S7-S9), A X;
-//   chol_inv  W = L L^T and L^{-T} of the b x b Gram matrix (POTRF of Table 1);
+//   chol_inv  W = L L^T and L^{-T} of the b x b Gram matrix (POTRF of Table 1; one
+//             CTA, or a cluster of 8 CTAs for b >= 64);
 //   trmm      R = Lbar^T L^T (Alg. 4 S7, Alg. 5 S11);
 // plus the Philox/Box-Muller start block, residual column norms, the Lanczos
 // residual estimate and the output sign convention.
@@ -15,6 +16,8 @@
 // traffic.  Symmetric Gram matrices compute only their upper half, triangular
 // factors skip their zero half at warp granularity, and split-K partial sums
 // are reduced in a fixed order so results are bitwise reproducible.
+#include <cooperative_groups.h>
+
 #include "tsvd_internal.cuh"
 
 namespace tsvd {
@@ -336,6 +339,178 @@ __global__ void __launch_bounds__(256) chol_inv_kernel(int b, const double* __re
         const int i = idx / b, j = idx % b;
         Lt[idx] = (j >= i) ? A[j * ld + i] : 0.0;
         Mt[idx] = (j > i) ? A[i * ld + j] : (j == i ? dinv[i] : 0.0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// chol_inv on a cluster of kCholCluster CTAs (b >= kCholClusterMin): the same
+// factorisation and inverse with the FP64 work spread over 8 SMs (one SM's FP64
+// pipe, 2 DFMA/clk, bounds the single-CTA kernel above).  Every CTA keeps a full
+// b x b copy in its shared memory; row i belongs to CTA i mod 8.  Per panel of 16
+// columns:
+//   1. every CTA factors the 16 x 16 diagonal block (warp 0; the same numbers and
+//      code in every CTA, so every CTA takes the same breakdown decision);
+//   2. each CTA solves its rows of the panel, L[i][P] = A[i][P] L11^{-T}, and writes
+//      them into every CTA's copy (distributed shared memory); cluster barrier;
+//   3. each CTA applies the rank-16 update A[i][k] -= L[i][P] L[k][P]^T to its rows
+//      (k <= i), then writes its rows of the next diagonal block into every copy;
+//      cluster barrier.
+// Afterwards every copy holds all of L; the inverse is split by columns (column c of
+// L^{-1} on CTA c mod 8, no exchange), and each CTA writes its rows of Lt and Mt.
+// The trailing updates sum 16 products per panel before subtracting (the one-CTA
+// kernel subtracts them one at a time), so results agree to rounding, not bits.
+// ---------------------------------------------------------------------------
+constexpr int kCholCluster = 8;
+constexpr int kCholPanel = 16;
+constexpr int kCholClusterMin = 64;
+
+__global__ void __cluster_dims__(kCholCluster, 1, 1) __launch_bounds__(256)
+    chol_inv_cluster_kernel(int b, const double* __restrict__ W, double* __restrict__ Lt, double* __restrict__ Mt,
+                            int* status) {
+    namespace cg = cooperative_groups;
+    constexpr int C = kCholCluster;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    extern __shared__ double sm[];
+    const int ld = b + 1;
+    double* A = sm;                     // lower: L; upper (transposed): own columns of L^{-1}
+    double* dinv = sm + (size_t)b * ld;  // 1 / L_jj
+    __shared__ double s_thresh;
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    for (int idx = tid; idx < b * b; idx += nt) {
+        const int i = idx / b, j = idx % b;
+        A[i * ld + j] = (j <= i) ? W[idx] : 0.0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double wmax = 0.0;
+        int bad = 0;
+        for (int i = 0; i < b; ++i) {
+            const double d = A[i * ld + i];
+            if (!isfinite(d)) bad = 2;
+            if (d > wmax) wmax = d;
+        }
+        if (bad == 0 && !(wmax > 0.0)) bad = 1;
+        s_bad = bad;
+        s_thresh = (double)b * kEps * wmax;
+    }
+    __syncthreads();
+    cl.sync();  // every copy is loaded before any CTA writes into another's
+    for (int p0 = 0; p0 < b; p0 += kCholPanel) {
+        if (s_bad) break;  // the same in every CTA
+        const int p1 = min(b, p0 + kCholPanel), pw = p1 - p0;
+        // 1. the diagonal block
+        if (tid < 32) {
+            for (int j = p0; j < p1; ++j) {
+                if (lane == 0) {
+                    const double d = A[j * ld + j];
+                    if (!isfinite(d) || !(d > s_thresh)) {
+                        s_bad = isfinite(d) ? 1 : 2;
+                    } else {
+                        const double y = rsqrt_fp64(d);
+                        A[j * ld + j] = d * y;
+                        dinv[j] = y;
+                    }
+                }
+                __syncwarp();
+                if (s_bad) break;
+                const double inv = dinv[j];
+                for (int i = j + 1 + lane; i < p1; i += 32) A[i * ld + j] *= inv;
+                __syncwarp();
+                const int nn = p1 - j - 1;
+                for (int idx = lane; idx < nn * (nn + 1) / 2; idx += 32) {
+                    int ii, kk;
+                    tri_decode(idx, ii, kk);
+                    const int i = j + 1 + ii, k = j + 1 + kk;
+                    A[i * ld + k] = fma(-A[i * ld + j], A[k * ld + j], A[i * ld + k]);
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        if (s_bad) break;
+        // 2. this CTA's rows below the block (one thread a row), into every copy
+        const int first = p1 + ((rank - p1 % C) % C + C) % C;
+        for (int i = first + C * tid; i < b; i += C * nt) {
+            double x[kCholPanel];
+#pragma unroll
+            for (int l = 0; l < kCholPanel; ++l) {
+                if (l < pw) {
+                    double a = A[i * ld + p0 + l];
+#pragma unroll
+                    for (int m = 0; m < l; ++m) a = fma(-x[m], A[(p0 + l) * ld + p0 + m], a);
+                    x[l] = a * dinv[p0 + l];
+                }
+            }
+            for (int r = 0; r < C; ++r) {
+                double* Ar = cl.map_shared_rank(A, r);
+#pragma unroll
+                for (int l = 0; l < kCholPanel; ++l)
+                    if (l < pw) Ar[i * ld + p0 + l] = x[l];
+            }
+        }
+        cl.sync();
+        // 3. rank-pw update of this CTA's rows i >= p1, columns p1 <= k <= i: 16
+        //    threads a row, each over k = p1 + (tid % 16) + 16 m
+        const int nown = first < b ? (b - first + C - 1) / C : 0;
+        for (int t = tid / 16; t < nown; t += nt / 16) {
+            const int i = first + C * t;
+            double li[kCholPanel];
+#pragma unroll
+            for (int l = 0; l < kCholPanel; ++l) li[l] = l < pw ? A[i * ld + p0 + l] : 0.0;
+            for (int k = p1 + (tid % 16); k <= i; k += 16) {
+                double acc = 0.0;
+#pragma unroll
+                for (int l = 0; l < kCholPanel; ++l)
+                    if (l < pw) acc = fma(li[l], A[k * ld + p0 + l], acc);
+                A[i * ld + k] -= acc;
+            }
+        }
+        __syncthreads();
+        const int p2 = min(b, p1 + kCholPanel);
+        for (int i = first + C * tid; i < p2; i += C * nt) {
+            for (int r = 0; r < C; ++r) {
+                double* Ar = cl.map_shared_rank(A, r);
+                for (int k = p1; k <= i; ++k) Ar[i * ld + k] = A[i * ld + k];
+            }
+        }
+        cl.sync();
+    }
+    if (s_bad) {
+        if (rank == 0 && tid == 0) atomicOr(&status[s_bad == 2 ? kStNonfinite : kStBreakdown], 1);
+        for (int idx = rank * nt + tid; idx < b * b; idx += C * nt) {
+            const double v = (idx / b == idx % b) ? 1.0 : 0.0;
+            Lt[idx] = v;
+            Mt[idx] = v;
+        }
+        return;
+    }
+    // X = L^{-1} for this CTA's columns c = rank + C u (as in the one-CTA kernel: row k
+    // of X is final once scaled by 1/L_kk, rows i > k take X[i][c] -= L[i][k] X[k][c];
+    // X[i][c] (c < i) is held at A[c][i])
+    for (int k = 0; k < b; ++k) {
+        const double ik = dinv[k];
+        const int ncol = k >= rank ? (k - rank) / C + 1 : 0;  // own c <= k
+        for (int u = tid; u < ncol; u += nt) {
+            const int c = rank + C * u;
+            if (c < k) A[c * ld + k] *= ik;
+        }
+        __syncthreads();
+        const int rows = b - k - 1;
+        for (int idx = tid; idx < rows * ncol; idx += nt) {
+            const int i = k + 1 + idx / ncol, c = rank + C * (idx % ncol);
+            const double xkc = (c == k) ? ik : A[c * ld + k];
+            A[c * ld + i] = fma(-A[i * ld + k], xkc, A[c * ld + i]);
+        }
+        __syncthreads();
+    }
+    // Lt = L^T (rows i = rank + C u) and Mt = L^{-T} = X^T (rows c = rank + C u), upper
+    for (int row = rank; row < b; row += C) {
+        for (int j = tid; j < b; j += nt) {
+            Lt[(size_t)row * b + j] = (j >= row) ? A[j * ld + row] : 0.0;
+            Mt[(size_t)row * b + j] = (j > row) ? A[row * ld + j] : (j == row ? dinv[row] : 0.0);
+        }
     }
 }
 
@@ -666,11 +841,17 @@ cudaError_t chol_inv(tsvd_handle* h, int b, const double* W, double* Lt, double*
         cudaError_t e = cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)chol_smem(TSVD_MAX_BLOCK));
         if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(chol_inv_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)chol_smem(TSVD_MAX_BLOCK));
+        if (e != cudaSuccess) return e;
         configured_device = h->device;
     }
     ProfScope prof(h, TSVD_K_CHOL, 2.0 * b * b * (double)b / 3.0, 24.0 * b * b, st);
     h->launches++;
-    chol_inv_kernel<<<1, 256, smem, st>>>(b, W, Lt, Mt, status);
+    if (b >= kCholClusterMin)
+        chol_inv_cluster_kernel<<<kCholCluster, 256, smem, st>>>(b, W, Lt, Mt, status);
+    else
+        chol_inv_kernel<<<1, 256, smem, st>>>(b, W, Lt, Mt, status);
     return cudaGetLastError();
 }
 

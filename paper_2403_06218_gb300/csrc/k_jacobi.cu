@@ -945,7 +945,7 @@ int run_block_sweeps<float>(tsvd_handle* h, int n, int npad, int w, float* G, un
 }
 
 int small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* Ubar, double* sigma, double* Vbar, int nv,
-              Arena& ar, int* status, cudaStream_t st, bool deferred) {
+              Arena& ar, int* status, cudaStream_t st, bool deferred, double target) {
     if (n < 1 || n > TSVD_MAX_SMALL_SVD) return TSVD_ERR_UNSUPPORTED;
     if (nv < 0 || nv > n) return TSVD_ERR_INVALID_ARG;
     const bool accumulate = (nv == n);
@@ -960,7 +960,17 @@ int small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* Ubar,
         TSVD_TRY_CUDA(cudaMemsetAsync(bf.ctl, 0, sizeof(unsigned) * kCtlWords, st));
         const int64_t tot = (int64_t)npad * npad;
         const unsigned ib = (unsigned)((tot + 255) / 256 < 4096 ? (tot + 255) / 256 : 4096);
-        const double tol = (double)(n > 16 ? n : 16) * kEps;
+        // Sweep tolerance tau (columns p, q count as orthogonal once |g_p.g_q| <=
+        // tau |g_p||g_q|): max(n, 16) eps by default.  Ritz pairs built on the result
+        // have residuals of a small multiple of tau sigma_1: couplings below tau are
+        // never rotated away, and with thick restart the converged kept Ritz vectors
+        // enter B with exactly such couplings (their columns are then not rotated at
+        // all, and the last block rows of their singular vectors stay zero).  A caller
+        // that needs residuals below 1e3 n eps (or as small as they get, target 0)
+        // gets tau = sqrt(n) eps, the level to which a computed coupling (an n-term
+        // FP64 dot product) is itself known.
+        double tol = (double)(n > 16 ? n : 16) * kEps;
+        if (target >= 0.0 && target < 1e3 * tol) tol = std::sqrt((double)(n > 16 ? n : 16)) * kEps;
         double* Vacc = accumulate ? V : nullptr;
         if (w > 0) {
             // (1) FP32 block-Jacobi sweeps on B with the rotations accumulated in V32: the

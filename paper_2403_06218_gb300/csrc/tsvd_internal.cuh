@@ -373,8 +373,12 @@ cudaError_t gaussian(tsvd_handle* h, int64_t rows, int64_t cols, uint64_t seed, 
 size_t small_svd_ws(int n);
 // deferred: the re-orthonormalisation of the recovered right vectors runs unsynchronised
 // and a breakdown there only sets the caller's breakdown flag.
+// target >= 0: the relative residual the caller needs from Ritz pairs built on the
+// result (0: as small as it gets); a small target tightens the sweep tolerance (see
+// k_jacobi.cu).  target < 0: the default tolerance.
 int small_svd(tsvd_handle* h, int n, const double* B, int64_t ldb, double* Ubar, double* sigma,
-              double* Vbar, int nv, Arena& ar, int* status, cudaStream_t st, bool deferred = false);
+              double* Vbar, int nv, Arena& ar, int* status, cudaStream_t st, bool deferred = false,
+              double target = -1.0);
 
 // out[j] = sum_i (Y[i,j] - U[i,j] * sigma[j])^2 for j < k  (deterministic).
 size_t colres_ws(int64_t q, int k);
