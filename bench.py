@@ -590,6 +590,9 @@ def main(argv=None):
 
     # ---- end to end through the C ABI with host buffers ----
     e2e_steps = max(1, min(args.steps, 2))
+    # one untimed call first: it sizes the larger workspace of host inputs (the first
+    # allocation of that size would otherwise land in the first timed step)
+    _solve(tsvd, cfg, A_pinned, seed, output="host")
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()

@@ -402,6 +402,7 @@ int final_triplets(tsvd_handle* h, Op<T>& op, int k, const T* Bm, int64_t ldbm, 
     constexpr bool kF64 = sizeof(T) == sizeof(double);
     const int64_t m = op.m, n = op.n;
     if (kF64) {
+        OzFreshRows fresh(h);  // the returned vectors to full FP64 accuracy
         TSVD_TRY_CUDA((gemm_nn<T, double, double>(h, m, wdim, k, 1.0, Bm, ldbm, Wm, ldwm, 0.0, dU, k, false, st)));
         TSVD_TRY_CUDA((gemm_nn<T, double, double>(h, n, wdim, k, 1.0, Bn, ldbn, Wn, ldwn, 0.0, dV, k, false, st)));
         TSVD_TRY_CUDA(cudaMemcpyAsync(dsig, sig, sizeof(double) * k, cudaMemcpyDeviceToDevice, st));
@@ -848,6 +849,7 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
                 TSVD_TRY_CUDA((convert2d<double, T>(h, n, keep, Pk64[cur], keep, P, rb, st)));
                 TSVD_TRY_CUDA((convert2d<double, T>(h, m, keep, Pbk64[cur], keep, Pbar, rb, st)));
             } else {
+                OzFreshRows fresh(h);  // the kept Ritz vectors to full FP64 accuracy
                 TSVD_TRY_CUDA((gemm_nn<T, double, T>(h, n, d, keep, 1.0, P, rb, Vb, d, 0.0, Pk, keep, false, st)));
                 TSVD_TRY_CUDA((gemm_nn<T, double, T>(h, m, d, keep, 1.0, Pbar, rb, Ub, d, 0.0, Pbk, keep, false, st)));
                 TSVD_TRY(keep_cols(cP, 0));
@@ -864,7 +866,10 @@ int blanczos_run(tsvd_handle* h, const tsvd_matrix* A, int k, int b, int r, uint
             s0 = keep;
         } else {
             // S7: Qbar_1 = Pbar Ubar_1, re-orthonormalised by CholeskyQR2
-            TSVD_TRY_CUDA((gemm_nn<T, double, T>(h, m, rb, b, 1.0, Pbar, rb, Ub, rb, 0.0, Qnext, b, false, st)));
+            {
+                OzFreshRows fresh(h);
+                TSVD_TRY_CUDA((gemm_nn<T, double, T>(h, m, rb, b, 1.0, Pbar, rb, Ub, rb, 0.0, Qnext, b, false, st)));
+            }
             TSVD_TRY(keep_cols(cP, 0));
             TSVD_TRY(keep_cols(cPb, 0));
             TSVD_TRY_CUDA(copy_block<T>(Qnext, b, Pbar, rb, m, b, st));

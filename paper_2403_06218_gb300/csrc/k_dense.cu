@@ -799,7 +799,7 @@ cudaError_t gemm_nn(tsvd_handle* h, int64_t q, int64_t s, int64_t b, double alph
                        (double)sizeof(TY) * q * b * (beta != 0.0 ? 2 : 1), st);
     if constexpr (std::is_same<TX, double>::value && std::is_same<TM, double>::value &&
                   std::is_same<TY, double>::value) {
-        const OzCache* xc = h->oz_ws ? oz_find_cache(h, X, ldx, q, s, false) : nullptr;
+        const OzCache* xc = (h->oz_ws && !h->oz_fresh_rows) ? oz_find_cache(h, X, ldx, q, s, false) : nullptr;
         if (h->oz_ws && s > 0 && oz_worth(q, b, s) && oz_nn_ws(q, s, b, xc != nullptr) <= h->oz_bytes) {
             const int rc = oz_gemm_nn(h, q, s, b, alpha, X, ldx, M, ldm, beta, Y, ldy, upper, h->oz_ws, h->oz_bytes,
                                       h->oz_status, st, xc);

@@ -54,6 +54,9 @@ struct tsvd_handle {
     int* oz_status = nullptr;
     // operands whose digit planes are kept for the current call (owned by the caller)
     std::vector<const tsvd::OzCache*> oz_caches;
+    // set by OzFreshRows: products slice their left operand afresh instead of
+    // reading a rows-layout basis cache
+    bool oz_fresh_rows = false;
     // limit, in SM clock cycles, of one bounded wait of the pipelined product kernels
     // and of the Jacobi grid barrier (2e9, about 1 s; tsvd_set_wait_limit lowers it)
     long long max_wait = 2000000000LL;
@@ -321,6 +324,20 @@ struct OzCacheScope {
     explicit OzCacheScope(tsvd_handle* hh) : h(hh), n0(hh->oz_caches.size()) {}
     void add(const OzCache* c) { h->oz_caches.push_back(c); }
     ~OzCacheScope() { h->oz_caches.resize(n0); }
+};
+
+// Within its lifetime the FP64 products slice their left operand afresh, with one
+// exponent per row, instead of reading the rows-layout planes of a basis cache.
+// Those planes give every row the fixed exponent of an orthonormal basis (entries
+// below 2), so a basis of n rows, with entries near n^-1/2, keeps about log2(n)/2
+// bits fewer than FP64 there.  The cache serves the CGS-CQR2 updates, whose
+// coefficients are computed from the same planes; the restart and Ritz products,
+// whose results the next cycle takes as exact Ritz vectors, slice afresh.
+struct OzFreshRows {
+    tsvd_handle* h;
+    bool prev;
+    explicit OzFreshRows(tsvd_handle* hh) : h(hh), prev(hh->oz_fresh_rows) { h->oz_fresh_rows = true; }
+    ~OzFreshRows() { h->oz_fresh_rows = prev; }
 };
 
 // Makes the FP64 products of one call run on the tensor cores with `bytes` of
