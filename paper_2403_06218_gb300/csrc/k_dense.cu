@@ -383,17 +383,24 @@ __global__ void __cluster_dims__(kCholCluster, 1, 1) __launch_bounds__(256)
         A[i * ld + j] = (j <= i) ? W[idx] : 0.0;
     }
     __syncthreads();
-    if (tid == 0) {
+    if (tid < 32) {  // max of the diagonal and a non-finite flag, over warp 0
         double wmax = 0.0;
         int bad = 0;
-        for (int i = 0; i < b; ++i) {
+        for (int i = lane; i < b; i += 32) {
             const double d = A[i * ld + i];
             if (!isfinite(d)) bad = 2;
             if (d > wmax) wmax = d;
         }
-        if (bad == 0 && !(wmax > 0.0)) bad = 1;
-        s_bad = bad;
-        s_thresh = (double)b * kEps * wmax;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+            bad = max(bad, __shfl_xor_sync(0xffffffffu, bad, o));
+        }
+        if (lane == 0) {
+            if (bad == 0 && !(wmax > 0.0)) bad = 1;
+            s_bad = bad;
+            s_thresh = (double)b * kEps * wmax;
+        }
     }
     __syncthreads();
     cl.sync();  // every copy is loaded before any CTA writes into another's
@@ -430,8 +437,10 @@ __global__ void __cluster_dims__(kCholCluster, 1, 1) __launch_bounds__(256)
         }
         __syncthreads();
         if (s_bad) break;
-        // 2. this CTA's rows below the block (one thread a row), into every copy
+        // 2. this CTA's rows below the block (one thread a row), then every CTA's
+        //    copy of them (all threads, one remote store each)
         const int first = p1 + ((rank - p1 % C) % C + C) % C;
+        const int nown = first < b ? (b - first + C - 1) / C : 0;
         for (int i = first + C * tid; i < b; i += C * nt) {
             double x[kCholPanel];
 #pragma unroll
@@ -443,17 +452,19 @@ __global__ void __cluster_dims__(kCholCluster, 1, 1) __launch_bounds__(256)
                     x[l] = a * dinv[p0 + l];
                 }
             }
-            for (int r = 0; r < C; ++r) {
-                double* Ar = cl.map_shared_rank(A, r);
 #pragma unroll
-                for (int l = 0; l < kCholPanel; ++l)
-                    if (l < pw) Ar[i * ld + p0 + l] = x[l];
-            }
+            for (int l = 0; l < kCholPanel; ++l)
+                if (l < pw) A[i * ld + p0 + l] = x[l];
+        }
+        __syncthreads();
+        for (int idx = tid; idx < nown * pw * (C - 1); idx += nt) {
+            const int r = (rank + 1 + idx % (C - 1)) % C, rest = idx / (C - 1);
+            const int i = first + C * (rest / pw), col = p0 + rest % pw;
+            cl.map_shared_rank(A, r)[i * ld + col] = A[i * ld + col];
         }
         cl.sync();
         // 3. rank-pw update of this CTA's rows i >= p1, columns p1 <= k <= i: 16
         //    threads a row, each over k = p1 + (tid % 16) + 16 m
-        const int nown = first < b ? (b - first + C - 1) / C : 0;
         for (int t = tid / 16; t < nown; t += nt / 16) {
             const int i = first + C * t;
             double li[kCholPanel];
@@ -468,12 +479,14 @@ __global__ void __cluster_dims__(kCholCluster, 1, 1) __launch_bounds__(256)
             }
         }
         __syncthreads();
+        // this CTA's rows of the next diagonal block into every other copy, one remote
+        // store per thread: (row t, column p1 + kk <= row, rank)
         const int p2 = min(b, p1 + kCholPanel);
-        for (int i = first + C * tid; i < p2; i += C * nt) {
-            for (int r = 0; r < C; ++r) {
-                double* Ar = cl.map_shared_rank(A, r);
-                for (int k = p1; k <= i; ++k) Ar[i * ld + k] = A[i * ld + k];
-            }
+        const int nnext = first < p2 ? (p2 - first + C - 1) / C : 0;
+        for (int idx = tid; idx < nnext * kCholPanel * (C - 1); idx += nt) {
+            const int r = (rank + 1 + idx % (C - 1)) % C, rest = idx / (C - 1);
+            const int i = first + C * (rest / kCholPanel), k = p1 + rest % kCholPanel;
+            if (k <= i) cl.map_shared_rank(A, r)[i * ld + k] = A[i * ld + k];
         }
         cl.sync();
     }
@@ -486,30 +499,34 @@ __global__ void __cluster_dims__(kCholCluster, 1, 1) __launch_bounds__(256)
         }
         return;
     }
-    // X = L^{-1} for this CTA's columns c = rank + C u (as in the one-CTA kernel: row k
-    // of X is final once scaled by 1/L_kk, rows i > k take X[i][c] -= L[i][k] X[k][c];
-    // X[i][c] (c < i) is held at A[c][i])
-    for (int k = 0; k < b; ++k) {
-        const double ik = dinv[k];
-        const int ncol = k >= rank ? (k - rank) / C + 1 : 0;  // own c <= k
-        for (int u = tid; u < ncol; u += nt) {
-            const int c = rank + C * u;
-            if (c < k) A[c * ld + k] *= ik;
-        }
-        __syncthreads();
-        const int rows = b - k - 1;
-        for (int idx = tid; idx < rows * ncol; idx += nt) {
-            const int i = k + 1 + idx / ncol, c = rank + C * (idx % ncol);
-            const double xkc = (c == k) ? ik : A[c * ld + k];
-            A[c * ld + i] = fma(-A[i * ld + k], xkc, A[c * ld + i]);
-        }
-        __syncthreads();
-    }
-    // Lt = L^T (rows i = rank + C u) and Mt = L^{-T} = X^T (rows c = rank + C u), upper
-    for (int row = rank; row < b; row += C) {
-        for (int j = tid; j < b; j += nt) {
-            Lt[(size_t)row * b + j] = (j >= row) ? A[j * ld + row] : 0.0;
-            Mt[(size_t)row * b + j] = (j > row) ? A[row * ld + j] : (j == row ? dinv[row] : 0.0);
+    // Lt = L^T (rows i = rank + C u)
+    for (int row = rank; row < b; row += C)
+        for (int j = tid; j < b; j += nt) Lt[(size_t)row * b + j] = (j >= row) ? A[j * ld + row] : 0.0;
+    // X = L^{-1}, column c = rank + C u by one warp (no barriers): forward substitution
+    // L x = e_c with the running sums of rows c + lane + 32 t in registers; x_k =
+    // acc_k / L_kk comes from the lane holding row k, then rows i > k take
+    // acc_i -= L[i][k] x_k.  Row c of Mt = L^{-T} is x (zero left of c).
+    constexpr int kRowsPerLane = TSVD_MAX_BLOCK / 32;
+    const int warp = tid >> 5, nwarps = nt >> 5;
+    for (int c = rank + C * warp; c < b; c += C * nwarps) {
+        double acc[kRowsPerLane];
+#pragma unroll
+        for (int t = 0; t < kRowsPerLane; ++t) acc[t] = (c + lane + 32 * t == c) ? 1.0 : 0.0;
+        double* mrow = Mt + (size_t)c * b;
+        for (int j = lane; j < c; j += 32) mrow[j] = 0.0;
+#pragma unroll
+        for (int tt = 0; tt < kRowsPerLane; ++tt) {
+            for (int ll = 0; ll < 32; ++ll) {
+                const int k = c + 32 * tt + ll;
+                if (k >= b) break;  // uniform over the warp
+                const double xk = __shfl_sync(0xffffffffu, acc[tt], ll) * dinv[k];
+                if (lane == 0) mrow[k] = xk;
+#pragma unroll
+                for (int t = tt; t < kRowsPerLane; ++t) {
+                    const int i = c + lane + 32 * t;
+                    if (i > k && i < b) acc[t] = fma(-A[i * ld + k], xk, acc[t]);
+                }
+            }
         }
     }
 }
