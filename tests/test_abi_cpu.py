@@ -113,6 +113,39 @@ def test_validation_of_the_newer_entry_points_without_gpu(tsvd):
     assert lib.tsvd_spmm_workspace(100, 10 ** 7, 64, C.byref(nb)) == _capi.TSVD_OK and nb.value > small.value
 
 
+def test_fused_update_gram_and_fp32_orthogonalisation_entry_points_without_gpu(tsvd):
+    """The fused update + Gram pass and the FP32-block CGS-CQR2 reject bad arguments
+    before any device work; the fused pass's workspace holds one b x b FP64 partial
+    Gram matrix per row slab (at most one wave of slabs, so it stops growing with q),
+    and the orthogonalisation workspace covers it."""
+    from paper_2403_06218_gb300 import _capi
+    lib = tsvd.load()
+    nb = C.c_size_t()
+    assert lib.tsvd_update_gram_f32_workspace(-1, 64, C.byref(nb)) == _capi.TSVD_ERR_INVALID_ARG
+    assert lib.tsvd_update_gram_f32_workspace(1000, 0, C.byref(nb)) == _capi.TSVD_ERR_INVALID_ARG
+    assert lib.tsvd_update_gram_f32_workspace(1000, 129, C.byref(nb)) == _capi.TSVD_ERR_UNSUPPORTED
+    sizes = {}
+    for q, b in ((64, 64), (10 ** 5, 64), (10 ** 6, 64), (10 ** 7, 64), (10 ** 7, 128)):
+        assert lib.tsvd_update_gram_f32_workspace(q, b, C.byref(nb)) == _capi.TSVD_OK
+        sizes[q, b] = nb.value
+        assert nb.value % 256 == 0 and nb.value >= 8 * b * b
+    assert sizes[64, 64] < sizes[10 ** 5, 64] <= sizes[10 ** 6, 64]
+    # at most one wave of slabs: 4 CTAs an SM for b <= 64, 2 for b = 128 (152 SMs)
+    for (q, b), v in sizes.items():
+        assert v <= 8 * b * b * 152 * (4 if b <= 64 else 2) + 256, (q, b, v)
+    assert sizes[10 ** 7, 64] > 0.95 * 8 * 64 * 64 * 152 * 4
+    orth = C.c_size_t()
+    for q, s_, b in ((10 ** 5, 576, 64), (2 * 10 ** 6, 1024, 128)):
+        assert lib.tsvd_orth_workspace(q, s_, b, C.byref(orth)) == _capi.TSVD_OK
+        assert lib.tsvd_update_gram_f32_workspace(q, b, C.byref(nb)) == _capi.TSVD_OK
+        assert orth.value > nb.value
+    # no handle
+    assert lib.tsvd_update_gram_f32(None, 100, 10, 8, 1.0, 1, 10, 1, 8, 0.0, 1, 8, 0, 1, None, 0, None) == \
+        _capi.TSVD_ERR_INVALID_ARG
+    assert lib.tsvd_cgs_cqr2_f32(None, 100, 10, 8, 1, 10, 1, 8, None, 1, 0, None, None, None, 0, None) == \
+        _capi.TSVD_ERR_INVALID_ARG
+
+
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     from paper_2403_06218_gb300 import _capi
     monkeypatch.setattr(_capi, "LIB_PATH", tmp_path / "libtsvd.so")
