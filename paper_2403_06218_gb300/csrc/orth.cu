@@ -12,7 +12,8 @@
 // The routines are templated on the storage type T of the tall blocks: double for
 // the FP64 method, float for the mixed-precision form, where the products read
 // FP32 blocks but every Gram matrix, projection coefficient, Cholesky factor and R
-// stays FP64 (split-K partial sums are reduced in FP64).
+// stays FP64 (split-K partial sums are reduced in FP64).  With FP32 blocks each
+// update runs as one pass with the Gram matrix of its result (fused_cgs_cqr2_f32).
 #include <cmath>
 #include <type_traits>
 #include <vector>
