@@ -7,6 +7,7 @@ ptxas's resource report (nvcc -Xptxas -v, the flags of the library build).
 * The fused FP32 update + Gram kernel fits 4 CTAs of 256 threads per SM for
   blocks of up to 64 columns and 2 for up to 128, as its slab plan assumes.
 * The tensor-core product kernel's 320 threads fit its registers in one SM.
+* The cluster Cholesky fits one CTA (256 threads, 133 KB matrix copy) on an SM.
 """
 
 import concurrent.futures as cf
@@ -106,6 +107,15 @@ def test_fused_update_gram_kernel_fits_its_wave(kernels):
     for name, ctas in ((r"update_gram_f32_kernelILi1E", 4), (r"update_gram_f32_kernelILi2E", 2)):
         k = _one(kernels, name)
         assert _resident_ctas(k["regs"], 256, k["smem"]) >= ctas, k
+
+
+def test_cluster_cholesky_fits_one_cta_per_sm(kernels):
+    # 256 threads and the b x (b + 1) + b doubles of its matrix copy at b = 128 (133 KB
+    # of dynamic shared memory): one CTA on each of the cluster's 8 SMs
+    k = _one(kernels, r"chol_inv_cluster_kernel")
+    dyn = 8 * (128 * 129 + 128)
+    assert k["regs"] * 256 <= REGS_PER_SM, k
+    assert k["smem"] + dyn + 1024 <= SMEM_PER_SM, k
 
 
 def test_tensor_core_kernel_fits_one_sm(kernels):
